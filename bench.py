@@ -1,0 +1,314 @@
+"""Benchmark: sketch-pass throughput of the single-pass randomized PCA on one GB300.
+
+A step is one whole pass of the method over the 100000 x 10000 FP32
+low-rank-plus-noise workload (k = 50, p = 10, 4096-row blocks, column centring):
+Omega regenerated (spca_reset), 25 row blocks folded in (spca_update) and the
+FP64 finalisation (spca_finalize). The data (4.0 GB) is larger than L2, so no
+L2 flush is needed between steps.
+
+Prints one JSON line. `value` is GB/s of A (as stored) per second of device
+time; `e2e` is the same metric through the C ABI with host (pinned) buffers and
+the host-to-device copies inside the timed region. `--impl reference` times the
+FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sketch-pass GB/s of A + roofline %, FP32 vs tensor-core at ≤1e-3 σ error; p99"
+WORKLOAD = "100000x10000 f32 low-rank+noise (sigma_i=10^(-i/20), i<=200; noise 1e-4 sigma_1; column means N(0,1)), " \
+           "k=50 p=10 (l=60), 4096-row blocks, column-centred"
+M, N, K, P, BLOCK = 100_000, 10_000, 50, 10, 4096
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0,
+                "source": "fallback"}
+
+
+# ------------------------------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", str(self.gpu_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------ CPU oracle
+
+def oracle_pass_seconds(A_rows_f32, seed):
+    """Time the FP64 oracle (sketch loop + Alg. 4 finalisation) on the given rows."""
+    from oracle import spca as O
+    A64 = np.asarray(A_rows_f32, dtype=np.float64)
+    t0 = time.perf_counter()
+    O.single_pass_pca(A64, K, P, seed, BLOCK, finalize="blocked", omega_form="f32")
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(A_sample_f32, seed, what):
+    secs = oracle_pass_seconds(A_sample_f32, seed)
+    gb = A_sample_f32.shape[0] * A_sample_f32.shape[1] * 4 / 1e9
+    return {"value": gb / secs, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{what}: {A_sample_f32.shape[0]} of {M} rows x {N} (f32 stored, FP64 compute), "
+                      f"Alg. 4 sketch loop + blocked finalisation, {secs:.2f} s"}
+
+
+# ------------------------------------------------------------------------------------------ arms
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args):
+    # the oracle runs on rank 0's host cores only; other ranks exit without work
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    from paper_1704_07669_gb300 import synth
+    rows = 8192
+    w = synth.workload_c2(m=rows, n=N, device="cpu")
+    A = w["A"].numpy()
+    for _ in range(args.warmup):
+        oracle_pass_seconds(A, w["seed"])
+    times = [oracle_pass_seconds(A, w["seed"]) for _ in range(args.steps)]
+    gb = rows * N * 4 / 1e9
+    t = float(np.sum(times))
+    value = gb * args.steps / t
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD + f"; each step a {rows}-row sample of the same recipe",
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{rows} rows x {N} per step, FP64 numpy oracle (Alg. 4)"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import paper_1704_07669_gb300 as spca
+    from paper_1704_07669_gb300 import build as spca_build
+    from paper_1704_07669_gb300 import synth
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spca_build.build()
+    spca.lib()
+    pk = peaks()
+
+    w = synth.workload_c2(device=dev, seed=synth.SEED_BASE + 1 + rank)
+    A = w["A"]
+    seed = w["seed"]
+    stream = torch.cuda.Stream(device=dev)
+    sess = spca.Session(N, K, P, seed, math=args.math, stream=stream)
+    sigma_d = torch.zeros(K, dtype=torch.float64, device=dev)
+    V_d = torch.zeros((K, N), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        spca.spca_reset(sess.handle, seed)
+        for r0 in range(0, M, BLOCK):
+            spca.spca_update(sess.handle, A[r0:r0 + BLOCK])
+        spca.spca_finalize(sess.handle, sigma_d, V_d, out_on_device=True)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    steps = args.steps
+    if steps is None:
+        t0 = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        steps = max(10, int(math.ceil(3.0 / max(dt, 1e-4))))
+
+    spca.spca_clear_profile(sess.handle)
+    spca.spca_set_profiling(sess.handle, True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        time.sleep(0.3)
+        barrier(ws)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+    spca.spca_set_profiling(sess.handle, False)
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ms, ws)
+    prof = sess.profile()
+    launches = int(sum(v[1] for v in prof.values()))
+    bytes_A = M * N * 4
+    value = ws * bytes_A * steps / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (FP32 FMA pipe for the plain path)
+    dom = max(("g_partial", "h_partial"), key=lambda k_: prof[k_][0])
+    dom_ms, dom_launches = prof[dom]
+    l = K + P
+    flops_total = 2.0 * M * N * l * steps          # each contraction: 2 m n l per pass
+    achieved = flops_total / (dom_ms * 1e-3) / 1e12
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": None, "kernel": dom,
+                "kernel_avg_ms": dom_ms / max(dom_launches, 1),
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"}
+    kernels = {k_: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps} for k_, v in prof.items()}
+
+    # end to end through the C ABI: pinned host rows copied inside the timed region, results read back
+    A_host = torch.empty((M, N), dtype=torch.float32, pin_memory=True)
+    A_host.copy_(A)
+    sig_h = np.zeros(K)
+    V_h = np.zeros((K, N))
+    e2e_steps = 2
+    rows_np = A_host.numpy()
+
+    def e2e_step():
+        spca.spca_reset(sess.handle, seed)
+        for r0 in range(0, M, BLOCK):
+            spca.spca_update(sess.handle, rows_np[r0:r0 + BLOCK])
+        spca.spca_finalize(sess.handle, sig_h, V_h, out_on_device=False)
+
+    e2e_step()
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e = {"value": ws * bytes_A * e2e_steps / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": bytes_A,
+           "d2h_bytes_per_step": 8 * (K + K * N)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sample_rows = 8 * BLOCK
+        cpu = cpu_baseline(A[:sample_rows].cpu().numpy(), seed, "first 8 row blocks of the timed matrix")
+
+    sess.close()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "math": args.math, "l2": "inputs larger than L2 (4.0 GB), no flush",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks.summary(), "kernels": kernels, "peaks_source": pk["source"],
+            "tflops": 4.0 * M * N * l * steps * ws / (ms * 1e-3) / 1e12}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--math", default="fp32", choices=["fp32", "bf16", "bf16x2", "fp8"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        if args.steps is None:
+            args.steps = 3
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

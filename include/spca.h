@@ -1,0 +1,228 @@
+/*
+ * spca.h - C ABI of the GB300 single-pass randomized PCA library.
+ *
+ * The method is Alg. 4 of Yu, Gu, Li, Liu, Li, "Single-Pass PCA of Large
+ * High-Dimensional Data" (IJCAI 2017): one streaming pass over the rows of an
+ * m x n data matrix A forms G = A Omega with an n x l Gaussian test matrix Omega
+ * (Alg. 4 steps 3-6) and accumulates H = A^T G row block by row block (Alg. 4
+ * step 7, Eq. 11); a small finalisation turns (G, H, Omega) into the leading k
+ * singular values and right singular vectors (Alg. 4 steps 9-20). Here G is not
+ * kept: the pass also accumulates the Gram matrix G^T G, the column sums of the
+ * (shifted) data and of G, and the finalisation takes R from the Gram matrix
+ * (Thm 1: Q = G R^-1 is orthonormal and B = Q^T A = R^-T H^T).
+ *
+ * Conventions for every call:
+ *  - Every function returns an spca_status; none aborts or exits. On failure
+ *    spca_last_error() describes the cause. A CUDA error puts the session in an
+ *    error state; later calls on it return SPCA_E_STATE.
+ *  - All matrices are row-major unless stated. "device" pointers are CUDA
+ *    device addresses on the session's device; "host" pointers are ordinary
+ *    (pageable or pinned) host memory.
+ *  - The caller owns every buffer it passes in; the library owns the session
+ *    and everything reachable from it.
+ *  - Sizes: n >= 1, k >= 1, p >= 0, l = k + p with l <= min(n, 256).
+ *  - Work is issued on the session's CUDA stream (the one given in the options,
+ *    or a stream the library creates). Calls on one session must not overlap in
+ *    time from several host threads.
+ */
+#ifndef SPCA_H_
+#define SPCA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spca_session spca_session;
+
+typedef enum {
+  SPCA_OK = 0,
+  SPCA_E_INVALID = 1,     /* bad argument (shape, dtype, pointer, size)        */
+  SPCA_E_NOMEM = 2,       /* device or pinned-host allocation failed           */
+  SPCA_E_CUDA = 3,        /* a CUDA runtime call or kernel launch failed       */
+  SPCA_E_STATE = 4,       /* call not valid in the session's state             */
+  SPCA_E_NUMERIC = 5,     /* NaN/Inf seen in the data, or no rows accumulated  */
+  SPCA_E_TIMEOUT = 6,     /* a bounded device wait gave up                     */
+  SPCA_E_UNSUPPORTED = 7  /* valid request this build or device cannot serve   */
+} spca_status;
+
+/* Storage type of the rows handed to spca_update. */
+typedef enum {
+  SPCA_F32 = 0,
+  SPCA_BF16 = 1,
+  SPCA_F8E4M3 = 2,        /* OCP E4M3 ("fn"): value = code * block_scale       */
+  SPCA_F64 = 3
+} spca_dtype;
+
+/* Arithmetic of the two contractions of the pass (a3: G = A Omega, a4: H += A^T G). */
+typedef enum {
+  SPCA_MATH_FP32 = 0,     /* FP32 CUDA-core FMA, FP32 accumulate               */
+  SPCA_MATH_BF16 = 1,     /* BF16 tensor-core operands, FP32 accumulate        */
+  SPCA_MATH_BF16X2 = 2,   /* split BF16 (hi + lo) operands, FP32 accumulate    */
+  SPCA_MATH_FP8 = 3       /* FP8 E4M3 operands, FP32 accumulate                */
+} spca_math;
+
+typedef struct {
+  int32_t math;           /* spca_math; default SPCA_MATH_FP32                 */
+  int32_t center;         /* 1 (default): principal components of the column-
+                             centred data; 0: of the raw rows                   */
+  int32_t max_block_rows; /* largest row count one internal launch handles;
+                             0 = library default (8192). Bigger updates are
+                             processed in pieces of this many rows.            */
+  int32_t reserved;       /* must be 0                                         */
+  void* cuda_stream;      /* cudaStream_t to work on; NULL = library-owned     */
+} spca_options;
+
+/* Fill *opt with the defaults. */
+void spca_default_options(spca_options* opt);
+
+/*
+ * spca_create - start a streaming PCA session (Alg. 4 steps 1-3).
+ *   n     number of features (columns of A)
+ *   k     number of principal components wanted
+ *   p     oversampling (the paper's s): l = k + p columns of Omega
+ *   seed  64-bit key of the Philox4x32-10 stream that defines Omega:
+ *         Omega[j, 4q + t] is normal t of the Box-Muller transform of the four
+ *         words of Philox(counter = (j mod 2^32, j div 2^32, q, 0),
+ *         key = (seed mod 2^32, seed div 2^32)), uniforms u = (x + 1/2) 2^-32
+ *   opt   options or NULL for defaults
+ *   out   receives the session handle (owned by the library; free it with
+ *         spca_destroy)
+ * Allocates the session's device state (H: n x l FP32, Omega, the Gram matrix,
+ * the sums and a workspace of O((n + max_block_rows) l) floats): constant in m.
+ * Errors: SPCA_E_INVALID (sizes), SPCA_E_NOMEM, SPCA_E_CUDA, SPCA_E_UNSUPPORTED
+ * (math form not available on this device).
+ */
+spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed,
+                        const spca_options* opt, spca_session** out);
+
+/*
+ * spca_update - fold the next rows of A into the sketch (Alg. 4 steps 5-7,
+ * Eq. 11; row order does not change the result in exact arithmetic).
+ *   rows            m_i x n block, row-major with leading dimension ld >= n
+ *                   elements, of type dtype
+ *   block_scale     SPCA_F8E4M3 only: one FP32 scale for the whole block
+ *                   (host pointer); ignored otherwise (may be NULL)
+ *   rows_on_device  1: rows is a device pointer, read in place on the session
+ *                   stream (the caller keeps it valid and unmodified until the
+ *                   stream has passed this work, e.g. until spca_sync);
+ *                   0: rows is host memory, copied through the session's pinned
+ *                   staging buffers; the call returns once the copy of the last
+ *                   piece has been issued and the caller's buffer is no longer
+ *                   read.
+ *   G_out           optional device pointer (NULL = none) receiving the m_i x l
+ *                   sketch rows G_i = (A_i - 1 c^T) Omega (row-major, ld = l)
+ *                   as this pass computes them, c being the session's shift
+ *                   (the FP32 column mean of the first rows seen when centering
+ *                   is on, else 0).
+ * m_i = 0 is a no-op. Errors: SPCA_E_INVALID, SPCA_E_CUDA, SPCA_E_STATE.
+ */
+spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t ld,
+                        int32_t dtype, const float* block_scale, int32_t rows_on_device,
+                        float* G_out);
+
+/*
+ * spca_finalize - leading k singular values and right singular vectors of the
+ * (centred) rows seen so far (Alg. 4 steps 9-20, FP64 on the device).
+ *   sigma  k doubles, descending; entries beyond the numerical rank are 0
+ *   V      n x k doubles, COLUMN-major (column i at V + i*n); column i is
+ *          scaled by +-1 so that its entry of largest magnitude (lowest index
+ *          on ties) is positive; columns for zero sigma are 0
+ *   out_on_device  1: sigma and V are device pointers; 0: host pointers
+ * Synchronises the session stream. Non-destructive: updates may continue.
+ * Errors: SPCA_E_INVALID, SPCA_E_NUMERIC (no rows yet, or NaN/Inf in the
+ * accumulated state), SPCA_E_CUDA, SPCA_E_STATE.
+ */
+spca_status spca_finalize(spca_session* s, double* sigma, double* V, int32_t out_on_device);
+
+/*
+ * spca_get_state - the centred accumulators, for inspection and parity tests.
+ *   H_bar    n x l doubles, row-major: A_bar^T G_bar (NULL = skip)
+ *   gram_bar l x l doubles: G_bar^T G_bar (NULL = skip)
+ *   colsum   n doubles: column sums of the shifted rows A - 1 c^T (NULL = skip)
+ *   shift    n floats: the shift c (NULL = skip)
+ *   m        receives the number of rows seen (NULL = skip)
+ * with A_bar, G_bar the column-centred data and sketch (or the raw ones when
+ * centering is off). All output pointers are host memory. Synchronises.
+ */
+spca_status spca_get_state(spca_session* s, double* H_bar, double* gram_bar,
+                           double* colsum, float* shift, int64_t* m);
+
+/*
+ * spca_merge - dst += src for two sessions that saw disjoint row sets of the
+ * same data stream (same n, k, p, seed, centering and shift). The sketch is a
+ * sum over rows (Eq. 11), so the merged session equals one session that saw
+ * both row sets. Both sessions must be on the same device. Synchronises src.
+ * Errors: SPCA_E_INVALID (mismatch), SPCA_E_CUDA, SPCA_E_STATE.
+ */
+spca_status spca_merge(spca_session* dst, const spca_session* src);
+
+/* Wait until all work issued on the session's stream is done. */
+spca_status spca_sync(spca_session* s);
+
+/* Release the session and its device memory (after synchronising). NULL is ok. */
+spca_status spca_destroy(spca_session* s);
+
+/* Text of the last error on s (or of the calling thread when s is NULL). */
+const char* spca_last_error(const spca_session* s);
+
+/* Number of rows of A seen so far, or -1 for a NULL session. */
+int64_t spca_rows_seen(const spca_session* s);
+
+/*
+ * spca_reset - start a new pass on the same session: zero H, the Gram matrix,
+ * the sums and the row count, forget the shift, and regenerate Omega for
+ * `seed` (Alg. 4 steps 1-3 again, without reallocating). Stream-ordered.
+ */
+spca_status spca_reset(spca_session* s, uint64_t seed);
+
+/* Kernel classes reported by spca_get_profile. */
+typedef enum {
+  SPCA_K_OMEGA = 0,       /* a1: Omega generation                          */
+  SPCA_K_SHIFT = 1,       /* a2: shift (column mean of the first rows)     */
+  SPCA_K_G_PARTIAL = 2,   /* a3: G = A_hat Omega contraction               */
+  SPCA_K_G_FINISH = 3,    /* a3/a5: split reduction, Gram and sum partials */
+  SPCA_K_GRAM_ACCUM = 4,  /* a5: FP64 Gram and sum accumulation            */
+  SPCA_K_H_PARTIAL = 5,   /* a4: H += A_hat^T G contraction (+ col sums)   */
+  SPCA_K_H_FINISH = 6,    /* a4/a5: split reduction into H and col sums    */
+  SPCA_K_FINALIZE = 7,    /* a7: all FP64 finalisation kernels together    */
+  SPCA_K_COUNT = 8
+} spca_kernel_id;
+
+/*
+ * spca_set_profiling - when on (1), every kernel launch of the session is
+ * bracketed by CUDA events on the session stream, so that spca_get_profile can
+ * report per-class device time. Launch counts are kept either way.
+ */
+spca_status spca_set_profiling(spca_session* s, int32_t on);
+
+/*
+ * spca_get_profile - for kernel class `kernel` (spca_kernel_id): total device
+ * milliseconds of the launches timed since the last spca_clear_profile (0 when
+ * profiling was off) and the number of launches. Synchronises the stream.
+ */
+spca_status spca_get_profile(spca_session* s, int32_t kernel, double* total_ms, int64_t* launches);
+
+/* Forget the recorded launches and times. */
+spca_status spca_clear_profile(spca_session* s);
+
+/*
+ * spca_omega_words - the raw Philox4x32-10 words behind Omega (a1), for
+ * bit-exact checks: out (device, uint32) receives n x 4*ceil(l/4) words, row j
+ * holding the words of counters (j, q = 0..ceil(l/4)-1) in order. Synchronous.
+ */
+spca_status spca_omega_words(uint64_t seed, int64_t n, int32_t l, uint32_t* out);
+
+/*
+ * spca_omega - Omega itself (a1) as FP32, n x l row-major, into device memory
+ * out (ld = l): the FP64 Box-Muller normals rounded to FP32. Synchronous.
+ */
+spca_status spca_omega(uint64_t seed, int64_t n, int32_t l, float* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPCA_H_ */

@@ -1,0 +1,269 @@
+"""GB300 single-pass randomized PCA (Yu et al., IJCAI 2017, Alg. 4) - Python binding.
+
+A thin ctypes layer over the C ABI in include/spca.h: every function here has
+the name of the C function it calls and only marshals arguments (torch tensors
+or numpy arrays to pointers, sizes, dtype codes). All arithmetic of the method
+runs in the CUDA library ``libspca.so``, built in-tree by ``build.build()``.
+There is no fallback: if the library is missing or cannot load, every call
+raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SPCA_OK = 0
+STATUS_NAMES = {0: "SPCA_OK", 1: "SPCA_E_INVALID", 2: "SPCA_E_NOMEM", 3: "SPCA_E_CUDA", 4: "SPCA_E_STATE",
+                5: "SPCA_E_NUMERIC", 6: "SPCA_E_TIMEOUT", 7: "SPCA_E_UNSUPPORTED"}
+SPCA_F32, SPCA_BF16, SPCA_F8E4M3, SPCA_F64 = 0, 1, 2, 3
+SPCA_MATH_FP32, SPCA_MATH_BF16, SPCA_MATH_BF16X2, SPCA_MATH_FP8 = 0, 1, 2, 3
+MATH_NAMES = {"fp32": SPCA_MATH_FP32, "bf16": SPCA_MATH_BF16, "bf16x2": SPCA_MATH_BF16X2, "fp8": SPCA_MATH_FP8}
+
+
+class SpcaError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("math", ctypes.c_int32), ("center", ctypes.c_int32), ("max_block_rows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+
+
+_LIB = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """The loaded libspca.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_1704_07669_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        vp, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+        sig = {
+            "spca_default_options": (None, [ctypes.POINTER(Options)]),
+            "spca_create": (i32, [i64, i32, i32, u64, ctypes.POINTER(Options), ctypes.POINTER(vp)]),
+            "spca_update": (i32, [vp, vp, i64, i64, i32, vp, i32, vp]),
+            "spca_finalize": (i32, [vp, vp, vp, i32]),
+            "spca_get_state": (i32, [vp, vp, vp, vp, vp, vp]),
+            "spca_merge": (i32, [vp, vp]),
+            "spca_sync": (i32, [vp]),
+            "spca_destroy": (i32, [vp]),
+            "spca_last_error": (ctypes.c_char_p, [vp]),
+            "spca_rows_seen": (i64, [vp]),
+            "spca_reset": (i32, [vp, u64]),
+            "spca_set_profiling": (i32, [vp, i32]),
+            "spca_get_profile": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
+            "spca_clear_profile": (i32, [vp]),
+            "spca_omega_words": (i32, [u64, i64, i32, vp]),
+            "spca_omega": (i32, [u64, i64, i32, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(status, handle=None):
+    if status != SPCA_OK:
+        msg = lib().spca_last_error(handle)
+        raise SpcaError(status, msg.decode() if msg else "")
+
+
+def _ptr(x):
+    """(address, on_device) of a torch tensor or numpy array, or (x, None) for an int."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data, False
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr(), bool(x.is_cuda)
+    return int(x), None
+
+
+def _dtype_code(x):
+    name = str(getattr(x, "dtype", ""))
+    if name.endswith("float32"):
+        return SPCA_F32
+    if name.endswith("float64"):
+        return SPCA_F64
+    if name.endswith("bfloat16"):
+        return SPCA_BF16
+    if name.endswith("float8_e4m3fn") or name.endswith("uint8"):
+        return SPCA_F8E4M3
+    raise ValueError(f"unsupported row dtype {name}")
+
+
+# ---------------------------------------------------------------- C ABI, one function each
+
+def spca_create(n, k, p, seed, math=SPCA_MATH_FP32, center=1, max_block_rows=0, stream=None):
+    opt = Options()
+    lib().spca_default_options(ctypes.byref(opt))
+    opt.math = MATH_NAMES[math] if isinstance(math, str) else int(math)
+    opt.center = int(center)
+    opt.max_block_rows = int(max_block_rows)
+    opt.cuda_stream = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    out = ctypes.c_void_p()
+    _check(lib().spca_create(int(n), int(k), int(p), int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(opt),
+                             ctypes.byref(out)))
+    return out.value
+
+
+def spca_update(handle, rows, m_i=None, ld=None, dtype=None, block_scale=None, rows_on_device=None, G_out=None):
+    addr, on_dev = _ptr(rows)
+    if m_i is None:
+        m_i = rows.shape[0]
+    if ld is None:
+        ld = (rows.stride(0) if hasattr(rows, "stride") and callable(rows.stride)
+              else rows.strides[0] // rows.itemsize)
+    if dtype is None:
+        dtype = _dtype_code(rows)
+    if rows_on_device is None:
+        rows_on_device = bool(on_dev)
+    scale = None
+    if block_scale is not None:
+        scale = ctypes.c_float(float(block_scale))
+    g_addr, _ = _ptr(G_out)
+    _check(lib().spca_update(handle, addr, int(m_i), int(ld), int(dtype),
+                             ctypes.cast(ctypes.byref(scale), ctypes.c_void_p) if scale is not None else None,
+                             int(rows_on_device), g_addr), handle)
+
+
+def spca_finalize(handle, sigma, V, out_on_device=None):
+    """Fill sigma (k doubles) and V (n x k doubles, column-major) - tensors or arrays."""
+    sa, sdev = _ptr(sigma)
+    va, vdev = _ptr(V)
+    on = bool(sdev) if out_on_device is None else bool(out_on_device)
+    _check(lib().spca_finalize(handle, sa, va, int(on)), handle)
+
+
+def spca_get_state(handle, H_bar=None, gram_bar=None, colsum=None, shift=None):
+    m = ctypes.c_int64(0)
+    _check(lib().spca_get_state(handle, _ptr(H_bar)[0], _ptr(gram_bar)[0], _ptr(colsum)[0], _ptr(shift)[0],
+                                ctypes.byref(m)), handle)
+    return m.value
+
+
+def spca_merge(dst, src):
+    _check(lib().spca_merge(dst, src), dst)
+
+
+def spca_sync(handle):
+    _check(lib().spca_sync(handle), handle)
+
+
+def spca_destroy(handle):
+    _check(lib().spca_destroy(handle))
+
+
+def spca_last_error(handle=None):
+    msg = lib().spca_last_error(handle)
+    return msg.decode() if msg else ""
+
+
+def spca_rows_seen(handle):
+    return lib().spca_rows_seen(handle)
+
+
+def spca_reset(handle, seed):
+    _check(lib().spca_reset(handle, int(seed) & 0xFFFFFFFFFFFFFFFF), handle)
+
+
+KERNEL_NAMES = ["omega", "shift", "g_partial", "g_finish", "gram_accum", "h_partial", "h_finish", "finalize"]
+
+
+def spca_set_profiling(handle, on):
+    _check(lib().spca_set_profiling(handle, int(bool(on))), handle)
+
+
+def spca_get_profile(handle, kernel):
+    """(total_ms, launches) for one kernel class (index or name)."""
+    kid = KERNEL_NAMES.index(kernel) if isinstance(kernel, str) else int(kernel)
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(lib().spca_get_profile(handle, kid, ctypes.byref(ms), ctypes.byref(n)), handle)
+    return ms.value, n.value
+
+
+def spca_clear_profile(handle):
+    _check(lib().spca_clear_profile(handle), handle)
+
+
+def spca_omega_words(seed, n, l, out):
+    _check(lib().spca_omega_words(int(seed) & 0xFFFFFFFFFFFFFFFF, int(n), int(l), _ptr(out)[0]))
+
+
+def spca_omega(seed, n, l, out):
+    _check(lib().spca_omega(int(seed) & 0xFFFFFFFFFFFFFFFF, int(n), int(l), _ptr(out)[0]))
+
+
+# ---------------------------------------------------------------- convenience wrapper
+
+class Session:
+    """RAII wrapper: Session(n, k, p, seed, math='fp32') with update/finalize/state."""
+
+    def __init__(self, n, k, p, seed, math=SPCA_MATH_FP32, center=True, max_block_rows=0, stream=None):
+        self.n, self.k, self.p = int(n), int(k), int(p)
+        self.l = self.k + self.p
+        self.handle = spca_create(n, k, p, seed, math=math, center=int(center), max_block_rows=max_block_rows,
+                                  stream=stream)
+
+    def update(self, rows, G_out=None, block_scale=None):
+        spca_update(self.handle, rows, G_out=G_out, block_scale=block_scale)
+
+    def finalize(self):
+        """(sigma, V) as float64 numpy arrays, V of shape (n, k)."""
+        sigma = np.zeros(self.k)
+        Vc = np.zeros((self.k, self.n))      # column-major n x k == row-major k x n
+        spca_finalize(self.handle, sigma, Vc, out_on_device=False)
+        return sigma, Vc.T.copy()
+
+    def state(self):
+        H = np.zeros((self.n, self.l))
+        g = np.zeros((self.l, self.l))
+        cs = np.zeros(self.n)
+        sh = np.zeros(self.n, dtype=np.float32)
+        m = spca_get_state(self.handle, H, g, cs, sh)
+        return {"H_bar": H, "gram_bar": g, "colsum": cs, "shift": sh, "m": m}
+
+    def reset(self, seed):
+        spca_reset(self.handle, seed)
+
+    def profile(self):
+        """{kernel name: (total_ms, launches)} since the last clear."""
+        return {name: spca_get_profile(self.handle, i) for i, name in enumerate(KERNEL_NAMES)}
+
+    @property
+    def rows_seen(self):
+        return spca_rows_seen(self.handle)
+
+    def sync(self):
+        spca_sync(self.handle)
+
+    def close(self):
+        if self.handle:
+            spca_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

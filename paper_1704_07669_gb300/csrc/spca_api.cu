@@ -1,0 +1,559 @@
+// C ABI of the library (include/spca.h): sessions, argument checks, streams,
+// host staging, and the order of the launches that make up the pass.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "spca.h"
+#include "spca_internal.cuh"
+
+using namespace spca;
+
+namespace {
+
+thread_local char g_thread_err[512] = "";
+
+constexpr size_t kStageBytes = size_t(256) << 20;   // per staging buffer (two of them)
+
+size_t dtype_size(int dtype) {
+  switch (dtype) {
+    case SPCA_F32: return 4;
+    case SPCA_BF16: return 2;
+    case SPCA_F8E4M3: return 1;
+    case SPCA_F64: return 8;
+    default: return 0;
+  }
+}
+
+}  // namespace
+
+namespace spca {
+
+void Prof::begin(int id, cudaStream_t st) {
+  launches[id] += 1;
+  if (!timing) return;
+  if (nmarks == cap) {
+    const int ncap = cap ? 2 * cap : 256;
+    Mark* nm = static_cast<Mark*>(realloc(marks, sizeof(Mark) * ncap));
+    if (!nm) { timing = false; return; }
+    for (int i = cap; i < ncap; ++i) {
+      nm[i].a = nullptr;
+      nm[i].b = nullptr;
+    }
+    marks = nm;
+    cap = ncap;
+  }
+  Mark& mk = marks[nmarks];
+  if (!mk.a) cudaEventCreate(&mk.a);
+  if (!mk.b) cudaEventCreate(&mk.b);
+  mk.id = id;
+  cudaEventRecord(mk.a, st);
+}
+
+void Prof::end(int id, cudaStream_t st) {
+  if (!timing || nmarks >= cap || marks[nmarks].id != id) return;
+  cudaEventRecord(marks[nmarks].b, st);
+  ++nmarks;
+}
+
+void Prof::release() {
+  for (int i = 0; i < cap; ++i) {
+    if (marks[i].a) cudaEventDestroy(marks[i].a);
+    if (marks[i].b) cudaEventDestroy(marks[i].b);
+  }
+  free(marks);
+  marks = nullptr;
+  cap = nmarks = 0;
+}
+
+}  // namespace spca
+
+struct spca_session {
+  int device = 0;
+  int64_t n = 0;
+  int k = 0, p = 0, l = 0, L = 0;
+  uint64_t seed = 0;
+  spca_options opt{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  bool own_stream = false;
+  bool failed = false;
+  int64_t m = 0;
+  bool shift_set = false;
+  char err[512] = "";
+
+  // state
+  float* omega32 = nullptr;
+  float* H = nullptr;
+  float* shift = nullptr;
+  double* colsum = nullptr;
+  double* sG = nullptr;
+  double* gram = nullptr;
+  int* flags = nullptr;
+  int* host_flags = nullptr;   // pinned mirror of flags[0..3]
+
+  // workspace
+  SimtWork simt{};
+  int64_t gp_rows = 0;
+  double* shift_part = nullptr;
+  FinalWork fin{};
+  double* fin_sigma = nullptr;
+  double* fin_V = nullptr;
+
+  // host staging
+  void* pinned[2] = {nullptr, nullptr};
+  void* dstage[2] = {nullptr, nullptr};
+  size_t stage_bytes = 0;
+  cudaEvent_t copied[2] = {nullptr, nullptr};
+  cudaEvent_t consumed[2] = {nullptr, nullptr};
+  int next_stage = 0;
+
+  Prof prof;
+
+  State state() const {
+    State s;
+    s.n = n; s.l = l; s.L = L;
+    s.omega32 = omega32; s.H = H; s.shift = shift; s.colsum = colsum; s.sG = sG; s.gram = gram; s.flags = flags;
+    return s;
+  }
+};
+
+namespace {
+
+spca_status fail(spca_session* s, spca_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (s) {
+    std::strncpy(s->err, buf, sizeof(s->err) - 1);
+    if (st == SPCA_E_CUDA) s->failed = true;
+  }
+  std::strncpy(g_thread_err, buf, sizeof(g_thread_err) - 1);
+  return st;
+}
+
+#define CU(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(s, SPCA_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+void free_all(spca_session* s) {
+  void* bufs[] = {s->omega32, s->H, s->shift, s->colsum, s->sG, s->gram, s->flags, s->simt.Gpart, s->simt.G,
+                  s->simt.gram_part, s->simt.sG_part, s->simt.Hpart, s->simt.cs_part, s->shift_part, s->fin.Hbar,
+                  s->fin.gbar, s->fin.T, s->fin.X, s->fin.W, s->fin.lam, s->fin.Bt, s->fin.Cpart, s->fin.C,
+                  s->fin.sig, s->fin.info, s->fin_sigma, s->fin_V, s->dstage[0], s->dstage[1]};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (int i = 0; i < 2; ++i) {
+    if (s->pinned[i]) cudaFreeHost(s->pinned[i]);
+    if (s->copied[i]) cudaEventDestroy(s->copied[i]);
+    if (s->consumed[i]) cudaEventDestroy(s->consumed[i]);
+  }
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  if (s->host_flags) cudaFreeHost(s->host_flags);
+  s->prof.release();
+}
+
+spca_status check_usable(spca_session* s) {
+  if (!s) return fail(nullptr, SPCA_E_INVALID, "NULL session");
+  if (s->failed) return fail(s, SPCA_E_STATE, "session is in an error state after a CUDA failure: %s", s->err);
+  return SPCA_OK;
+}
+
+// One piece of at most max_block_rows rows, resident on the device.
+spca_status run_piece(spca_session* s, const void* rows, int64_t m, int64_t ld, int dtype, float scale,
+                      float* G_out) {
+  if (s->opt.center && !s->shift_set) {
+    CU(launch_shift(rows, dtype, m, s->n, ld, scale, s->shift, s->shift_part, s->stream, &s->prof));
+    s->shift_set = true;
+  }
+  SimtWork w = s->simt;
+  CU(simt_pass(s->state(), w, rows, dtype, scale, m, ld, G_out, s->stream, &s->prof));
+  s->m += m;
+  return SPCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void spca_default_options(spca_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->math = SPCA_MATH_FP32;
+  opt->center = 1;
+  opt->max_block_rows = 0;
+  opt->cuda_stream = nullptr;
+}
+
+spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const spca_options* opt,
+                        spca_session** out) {
+  spca_session* s = nullptr;
+  if (!out) return fail(nullptr, SPCA_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || k < 1 || p < 0) return fail(nullptr, SPCA_E_INVALID, "need n >= 1, k >= 1, p >= 0 (n=%lld k=%d p=%d)",
+                                           (long long)n, k, p);
+  const int64_t l = static_cast<int64_t>(k) + p;
+  if (l > kMaxL || l > n)
+    return fail(nullptr, SPCA_E_INVALID, "l = k + p = %lld must be <= min(n, %d)", (long long)l, kMaxL);
+  spca_options o;
+  spca_default_options(&o);
+  if (opt) o = *opt;
+  if (o.reserved != 0 || (o.center != 0 && o.center != 1) || o.max_block_rows < 0)
+    return fail(nullptr, SPCA_E_INVALID, "invalid options");
+  if (o.math != SPCA_MATH_FP32)
+    return fail(nullptr, SPCA_E_UNSUPPORTED, "math form %d is not available in this build", o.math);
+
+  s = new (std::nothrow) spca_session();
+  if (!s) return fail(nullptr, SPCA_E_NOMEM, "host allocation failed");
+  s->n = n; s->k = k; s->p = p; s->l = static_cast<int>(l); s->L = pad_l(static_cast<int>(l)); s->seed = seed;
+  s->opt = o;
+  const int64_t mb = o.max_block_rows > 0 ? o.max_block_rows : kDefaultBlockRows;
+  const int L = s->L;
+
+#define CC(call)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      spca_status st_ = (e_ == cudaErrorMemoryAllocation) ? SPCA_E_NOMEM : SPCA_E_CUDA; \
+      fail(nullptr, st_, "%s: %s", #call, cudaGetErrorString(e_));                  \
+      free_all(s);                                                                  \
+      delete s;                                                                     \
+      return st_;                                                                   \
+    }                                                                               \
+  } while (0)
+
+  CC(cudaGetDevice(&s->device));
+  if (o.cuda_stream) {
+    s->stream = static_cast<cudaStream_t>(o.cuda_stream);
+  } else {
+    CC(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    s->own_stream = true;
+  }
+  CC(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
+  CC(dalloc(&s->omega32, n * L));
+  CC(dalloc(&s->H, n * L));
+  CC(dalloc(&s->shift, n));
+  CC(dalloc(&s->colsum, n));
+  CC(dalloc(&s->sG, L));
+  CC(dalloc(&s->gram, size_t(L) * L));
+  CC(dalloc(&s->flags, 4));
+  CC(cudaMallocHost(&s->host_flags, sizeof(int) * 4));
+
+  SimtWork& w = s->simt;
+  w.mb = mb;
+  const int64_t mb_pad = ((mb + 127) / 128) * 128;
+  w.gp_rows = mb_pad > 65536 ? mb_pad : 65536;
+  s->gp_rows = w.gp_rows;
+  int64_t tmax = (int64_t(16) << 20) / (n * L);
+  w.T = static_cast<int>(tmax < 1 ? 1 : (tmax > 16 ? 16 : tmax));
+  CC(dalloc(&w.Gpart, size_t(s->gp_rows) * L));
+  CC(dalloc(&w.G, size_t(mb) * L));
+  const int64_t groups = (mb + 31) / 32;
+  CC(dalloc(&w.gram_part, size_t(groups) * L * L));
+  CC(dalloc(&w.sG_part, size_t(groups) * L));
+  CC(dalloc(&w.Hpart, size_t(w.T) * n * L));
+  CC(dalloc(&w.cs_part, size_t(w.T) * n));
+  CC(dalloc(&s->shift_part, size_t(kShiftParts) * n));
+
+  FinalWork& f = s->fin;
+  f.nparts = 64;
+  CC(dalloc(&f.Hbar, size_t(n) * L));
+  CC(dalloc(&f.gbar, size_t(L) * L));
+  CC(dalloc(&f.T, size_t(L) * L));
+  CC(dalloc(&f.X, size_t(L) * L));
+  CC(dalloc(&f.W, size_t(L) * L));
+  CC(dalloc(&f.lam, L));
+  CC(dalloc(&f.Bt, size_t(n) * L));
+  CC(dalloc(&f.Cpart, size_t(f.nparts) * L * L));
+  CC(dalloc(&f.C, size_t(L) * L));
+  CC(dalloc(&f.sig, L));
+  CC(dalloc(&f.info, 8));
+  CC(dalloc(&s->fin_sigma, k));
+  CC(dalloc(&s->fin_V, size_t(n) * k));
+
+  CC(cudaMemsetAsync(s->H, 0, sizeof(float) * n * L, s->stream));
+  CC(cudaMemsetAsync(s->shift, 0, sizeof(float) * n, s->stream));
+  CC(cudaMemsetAsync(s->colsum, 0, sizeof(double) * n, s->stream));
+  CC(cudaMemsetAsync(s->sG, 0, sizeof(double) * L, s->stream));
+  CC(cudaMemsetAsync(s->gram, 0, sizeof(double) * L * L, s->stream));
+  CC(cudaMemsetAsync(s->flags, 0, sizeof(int) * 4, s->stream));
+  CC(launch_omega_f32(seed, n, s->l, L, s->omega32, L, s->stream));
+  CC(cudaStreamSynchronize(s->stream));
+#undef CC
+  *out = s;
+  return SPCA_OK;
+}
+
+spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t ld, int32_t dtype,
+                        const float* block_scale, int32_t rows_on_device, float* G_out) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  if (m_i < 0) return fail(s, SPCA_E_INVALID, "m_i < 0");
+  if (m_i == 0) return SPCA_OK;
+  if (!rows) return fail(s, SPCA_E_INVALID, "rows is NULL");
+  if (ld < s->n) return fail(s, SPCA_E_INVALID, "ld (%lld) < n (%lld)", (long long)ld, (long long)s->n);
+  const size_t es = dtype_size(dtype);
+  if (es == 0) return fail(s, SPCA_E_INVALID, "unknown dtype %d", dtype);
+  float scale = 1.0f;
+  if (dtype == SPCA_F8E4M3) {
+    if (!block_scale) return fail(s, SPCA_E_INVALID, "FP8 rows need a block_scale");
+    scale = *block_scale;
+    if (!(scale > 0.0f) || scale != scale) return fail(s, SPCA_E_INVALID, "block_scale must be positive");
+  }
+  if (rows_on_device != 0 && rows_on_device != 1) return fail(s, SPCA_E_INVALID, "rows_on_device must be 0 or 1");
+  CU(cudaSetDevice(s->device));
+  const int64_t mb = s->simt.mb;
+  if (rows_on_device) {
+    cudaPointerAttributes attr;
+    std::memset(&attr, 0, sizeof(attr));
+    const bool ok_attr = cudaPointerGetAttributes(&attr, rows) == cudaSuccess;
+    cudaGetLastError();
+    if (!ok_attr || (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged))
+      return fail(s, SPCA_E_INVALID, "rows_on_device=1 but rows is not a device pointer");
+    for (int64_t r0 = 0; r0 < m_i; r0 += mb) {
+      const int64_t mr = (m_i - r0) < mb ? (m_i - r0) : mb;
+      const char* base = static_cast<const char*>(rows) + size_t(r0) * ld * es;
+      st = run_piece(s, base, mr, ld, dtype, scale, G_out ? G_out + r0 * s->l : nullptr);
+      if (st != SPCA_OK) return st;
+    }
+    return SPCA_OK;
+  }
+  // Host rows: copy pieces through two staging buffers so the copy of piece i+1
+  // overlaps the kernels of piece i.
+  const size_t row_bytes = size_t(s->n) * es;
+  if (!s->pinned[0]) {
+    size_t want = kStageBytes;
+    if (want < row_bytes) want = row_bytes;
+    s->stage_bytes = want;
+    for (int i = 0; i < 2; ++i) {
+      if (cudaMallocHost(&s->pinned[i], want) != cudaSuccess || cudaMalloc(&s->dstage[i], want) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(s, SPCA_E_NOMEM, "staging allocation of %zu bytes failed", want);
+      }
+      CU(cudaEventCreateWithFlags(&s->copied[i], cudaEventDisableTiming));
+      CU(cudaEventCreateWithFlags(&s->consumed[i], cudaEventDisableTiming));
+      CU(cudaEventRecord(s->consumed[i], s->stream));
+      CU(cudaEventRecord(s->copied[i], s->copy_stream));
+    }
+  }
+  int64_t piece = static_cast<int64_t>(s->stage_bytes / row_bytes);
+  if (piece > mb) piece = mb;
+  cudaPointerAttributes attr;
+  std::memset(&attr, 0, sizeof(attr));
+  bool host_pinned = false;
+  if (cudaPointerGetAttributes(&attr, rows) == cudaSuccess) host_pinned = (attr.type == cudaMemoryTypeHost);
+  cudaGetLastError();
+  for (int64_t r0 = 0; r0 < m_i; r0 += piece) {
+    const int64_t mr = (m_i - r0) < piece ? (m_i - r0) : piece;
+    const int b = s->next_stage;
+    s->next_stage ^= 1;
+    const char* src = static_cast<const char*>(rows) + size_t(r0) * ld * es;
+    CU(cudaStreamWaitEvent(s->copy_stream, s->consumed[b], 0));
+    if (host_pinned) {
+      CU(cudaMemcpy2DAsync(s->dstage[b], row_bytes, src, size_t(ld) * es, row_bytes, mr, cudaMemcpyHostToDevice,
+                           s->copy_stream));
+    } else {
+      CU(cudaEventSynchronize(s->copied[b]));   // pinned[b] free again
+      char* dst = static_cast<char*>(s->pinned[b]);
+      if (ld == s->n) {
+        std::memcpy(dst, src, row_bytes * mr);
+      } else {
+        for (int64_t r = 0; r < mr; ++r) std::memcpy(dst + r * row_bytes, src + size_t(r) * ld * es, row_bytes);
+      }
+      CU(cudaMemcpyAsync(s->dstage[b], dst, row_bytes * mr, cudaMemcpyHostToDevice, s->copy_stream));
+    }
+    CU(cudaEventRecord(s->copied[b], s->copy_stream));
+    CU(cudaStreamWaitEvent(s->stream, s->copied[b], 0));
+    st = run_piece(s, s->dstage[b], mr, s->n, dtype, scale, G_out ? G_out + r0 * s->l : nullptr);
+    if (st != SPCA_OK) return st;
+    CU(cudaEventRecord(s->consumed[b], s->stream));
+  }
+  if (!host_pinned) {
+    // the caller's buffer has been copied into pinned memory already; nothing more to wait for
+  } else {
+    CU(cudaStreamSynchronize(s->copy_stream));   // caller may reuse its pinned buffer on return
+  }
+  return SPCA_OK;
+}
+
+spca_status spca_finalize(spca_session* s, double* sigma, double* V, int32_t out_on_device) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  if (!sigma || !V) return fail(s, SPCA_E_INVALID, "sigma and V must be non-NULL");
+  if (s->m < 1) return fail(s, SPCA_E_NUMERIC, "no rows accumulated yet");
+  CU(cudaSetDevice(s->device));
+  double* sd = out_on_device ? sigma : s->fin_sigma;
+  double* vd = out_on_device ? V : s->fin_V;
+  CU(finalize_run(s->state(), s->fin, s->opt.center ? s->m : 0, s->k, sd, vd, s->stream, &s->prof));
+  if (!out_on_device) {
+    CU(cudaMemcpyAsync(sigma, sd, sizeof(double) * s->k, cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaMemcpyAsync(V, vd, sizeof(double) * s->n * s->k, cudaMemcpyDeviceToHost, s->stream));
+  }
+  // the non-finite flag is read after the finalisation kernels so that the stream never idles mid-call
+  CU(cudaMemcpyAsync(s->host_flags, s->flags, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CU(cudaStreamSynchronize(s->stream));
+  if (s->host_flags[0] & 1) return fail(s, SPCA_E_NUMERIC, "non-finite values (NaN/Inf) reached the sketch");
+  return SPCA_OK;
+}
+
+spca_status spca_get_state(spca_session* s, double* H_bar, double* gram_bar, double* colsum, float* shift,
+                           int64_t* m) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  CU(cudaSetDevice(s->device));
+  CU(centered_state(s->state(), s->fin, s->opt.center ? s->m : 0, s->stream));
+  const int L = s->L, l = s->l;
+  if (H_bar)
+    CU(cudaMemcpy2DAsync(H_bar, sizeof(double) * l, s->fin.Hbar, sizeof(double) * L, sizeof(double) * l, s->n,
+                         cudaMemcpyDeviceToHost, s->stream));
+  if (gram_bar)
+    CU(cudaMemcpy2DAsync(gram_bar, sizeof(double) * l, s->fin.gbar, sizeof(double) * L, sizeof(double) * l, l,
+                         cudaMemcpyDeviceToHost, s->stream));
+  if (colsum) CU(cudaMemcpyAsync(colsum, s->colsum, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+  if (shift) CU(cudaMemcpyAsync(shift, s->shift, sizeof(float) * s->n, cudaMemcpyDeviceToHost, s->stream));
+  CU(cudaStreamSynchronize(s->stream));
+  if (m) *m = s->m;
+  return SPCA_OK;
+}
+
+spca_status spca_merge(spca_session* dst, const spca_session* src) {
+  spca_session* s = dst;
+  spca_status st = check_usable(dst);
+  if (st != SPCA_OK) return st;
+  if (!src) return fail(s, SPCA_E_INVALID, "src is NULL");
+  if (src->failed) return fail(s, SPCA_E_STATE, "src session is in an error state");
+  if (src->n != dst->n || src->k != dst->k || src->p != dst->p || src->seed != dst->seed ||
+      src->opt.center != dst->opt.center || src->device != dst->device)
+    return fail(s, SPCA_E_INVALID, "sessions differ in n, k, p, seed, centering or device");
+  if (dst->opt.center && src->m > 0) {
+    if (!dst->shift_set) return fail(s, SPCA_E_INVALID, "dst has no shift yet; update it first");
+    // shifts must agree exactly for the sums to combine
+    float* a = new (std::nothrow) float[dst->n];
+    float* b = new (std::nothrow) float[dst->n];
+    if (!a || !b) { delete[] a; delete[] b; return fail(s, SPCA_E_NOMEM, "host allocation failed"); }
+    cudaError_t e1 = cudaMemcpy(a, dst->shift, sizeof(float) * dst->n, cudaMemcpyDeviceToHost);
+    cudaError_t e2 = cudaMemcpy(b, src->shift, sizeof(float) * dst->n, cudaMemcpyDeviceToHost);
+    const bool same = (e1 == cudaSuccess && e2 == cudaSuccess) && std::memcmp(a, b, sizeof(float) * dst->n) == 0;
+    delete[] a; delete[] b;
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(s, SPCA_E_CUDA, "shift copy failed");
+    if (!same) return fail(s, SPCA_E_INVALID, "sessions use different shifts; give both the same first rows");
+  }
+  CU(cudaSetDevice(dst->device));
+  CU(cudaStreamSynchronize(src->stream));
+  CU(launch_merge(dst->state(), src->state(), dst->stream));
+  CU(cudaStreamSynchronize(dst->stream));
+  dst->m += src->m;
+  return SPCA_OK;
+}
+
+spca_status spca_reset(spca_session* s, uint64_t seed) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  CU(cudaSetDevice(s->device));
+  const int L = s->L;
+  CU(cudaMemsetAsync(s->H, 0, sizeof(float) * s->n * L, s->stream));
+  CU(cudaMemsetAsync(s->shift, 0, sizeof(float) * s->n, s->stream));
+  CU(cudaMemsetAsync(s->colsum, 0, sizeof(double) * s->n, s->stream));
+  CU(cudaMemsetAsync(s->sG, 0, sizeof(double) * L, s->stream));
+  CU(cudaMemsetAsync(s->gram, 0, sizeof(double) * L * L, s->stream));
+  CU(cudaMemsetAsync(s->flags, 0, sizeof(int) * 4, s->stream));
+  s->seed = seed;
+  CU(launch_omega_f32(seed, s->n, s->l, L, s->omega32, L, s->stream, &s->prof));
+  s->m = 0;
+  s->shift_set = false;
+  return SPCA_OK;
+}
+
+spca_status spca_set_profiling(spca_session* s, int32_t on) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  s->prof.timing = (on != 0);
+  return SPCA_OK;
+}
+
+spca_status spca_get_profile(spca_session* s, int32_t kernel, double* total_ms, int64_t* launches) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  if (kernel < 0 || kernel >= SPCA_K_COUNT) return fail(s, SPCA_E_INVALID, "unknown kernel class %d", kernel);
+  CU(cudaStreamSynchronize(s->stream));
+  double tot = 0.0;
+  for (int i = 0; i < s->prof.nmarks; ++i) {
+    if (s->prof.marks[i].id != kernel) continue;
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, s->prof.marks[i].a, s->prof.marks[i].b));
+    tot += ms;
+  }
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = s->prof.launches[kernel];
+  return SPCA_OK;
+}
+
+spca_status spca_clear_profile(spca_session* s) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  CU(cudaStreamSynchronize(s->stream));
+  s->prof.clear();
+  return SPCA_OK;
+}
+
+spca_status spca_sync(spca_session* s) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  CU(cudaStreamSynchronize(s->stream));
+  return SPCA_OK;
+}
+
+spca_status spca_destroy(spca_session* s) {
+  if (!s) return SPCA_OK;
+  cudaSetDevice(s->device);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
+  free_all(s);
+  delete s;
+  return SPCA_OK;
+}
+
+const char* spca_last_error(const spca_session* s) { return s ? s->err : g_thread_err; }
+
+int64_t spca_rows_seen(const spca_session* s) { return s ? s->m : -1; }
+
+spca_status spca_omega_words(uint64_t seed, int64_t n, int32_t l, uint32_t* out) {
+  spca_session* s = nullptr;
+  if (n < 1 || l < 1 || !out) return fail(nullptr, SPCA_E_INVALID, "bad arguments");
+  CU(launch_omega_words(seed, n, l, out, 0));
+  CU(cudaDeviceSynchronize());
+  return SPCA_OK;
+}
+
+spca_status spca_omega(uint64_t seed, int64_t n, int32_t l, float* out) {
+  spca_session* s = nullptr;
+  if (n < 1 || l < 1 || !out) return fail(nullptr, SPCA_E_INVALID, "bad arguments");
+  // FP32 Omega with ld = l: generate into a padded scratch then compact
+  const int L = pad_l(l);
+  float* tmp = nullptr;
+  CU(cudaMalloc(&tmp, sizeof(float) * n * L));
+  cudaError_t e = launch_omega_f32(seed, n, l, L, tmp, L, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2D(out, sizeof(float) * l, tmp, sizeof(float) * L, sizeof(float) * l, n, cudaMemcpyDeviceToDevice);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return fail(nullptr, SPCA_E_CUDA, "omega: %s", cudaGetErrorString(e));
+  CU(cudaDeviceSynchronize());
+  return SPCA_OK;
+}
+
+}  // extern "C"

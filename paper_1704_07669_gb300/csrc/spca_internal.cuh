@@ -1,0 +1,99 @@
+// Internal declarations shared by the translation units of the library.
+// Not part of the public ABI (see include/spca.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "spca.h"
+
+namespace spca {
+
+constexpr int kMaxL = 256;          // largest l accepted
+constexpr int kDefaultBlockRows = 8192;
+
+// Round l up to the column padding of the device state.
+inline int pad_l(int l) { return ((l + 15) / 16) * 16; }
+
+// Launch accounting: every launcher calls begin/end around each kernel it enqueues.
+// Counts are always kept; events are recorded only when timing is on.
+struct Prof {
+  int64_t launches[SPCA_K_COUNT] = {0};
+  bool timing = false;
+  struct Mark { int id; cudaEvent_t a, b; };
+  Mark* marks = nullptr;   // recorded begin/end pairs (events reused after clear)
+  int nmarks = 0, cap = 0;
+  void begin(int id, cudaStream_t st);
+  void end(int id, cudaStream_t st);
+  void clear() { nmarks = 0; for (int i = 0; i < SPCA_K_COUNT; ++i) launches[i] = 0; }
+  void release();
+};
+
+// ---------------------------------------------------------------- launchers
+// Every launcher enqueues on `st` and returns the launch error (cudaGetLastError).
+
+// a1: Omega as FP32 (n x L row-major, columns >= l zero) and raw Philox words.
+cudaError_t launch_omega_f32(uint64_t seed, int64_t n, int l, int L, float* out, int64_t ld,
+                             cudaStream_t st, Prof* prof = nullptr);
+cudaError_t launch_omega_words(uint64_t seed, int64_t n, int l, uint32_t* out, cudaStream_t st);
+
+// Shift c = FP32 of the FP64 column mean of the given rows; part: kShiftParts x n doubles.
+constexpr int kShiftParts = 64;
+cudaError_t launch_shift(const void* rows, int dtype, int64_t m, int64_t n, int64_t ld,
+                         float scale, float* shift, double* part, cudaStream_t st, Prof* prof);
+
+// FP32 SIMT pass over one piece of rows (a2-a5). Workspace pointers are owned by the session.
+struct SimtWork {
+  float* Gpart;       // gp_rows x L (split partials, S x rows_padded)
+  float* G;           // mb x L
+  float* gram_part;   // ceil(mb/32) x L x L
+  float* sG_part;     // ceil(mb/32) x L
+  float* Hpart;       // T x n x L
+  float* cs_part;     // T x n
+  int T;              // max row splits of the H contraction
+  int64_t gp_rows;    // capacity of Gpart in rows (>= mb rounded up to 128)
+  int64_t mb;         // max rows per piece
+};
+
+struct State {
+  int64_t n;
+  int l, L;
+  const float* omega32;   // n x L
+  float* H;               // n x L
+  const float* shift;     // n
+  double* colsum;         // n
+  double* sG;             // L
+  double* gram;           // L x L
+  int* flags;             // [0]: non-finite value seen
+};
+
+cudaError_t simt_pass(const State& s, const SimtWork& w, const void* rows, int dtype,
+                      float scale, int64_t m, int64_t ld, float* G_out, cudaStream_t st, Prof* prof);
+
+// Merge: dst += src (H, colsum, sG, gram).
+cudaError_t launch_merge(const State& dst, const State& src, cudaStream_t st);
+
+// FP64 finalisation (a7). Scratch is owned by the session.
+struct FinalWork {
+  double* Hbar;       // n x L
+  double* gbar;       // L x L
+  double* T;          // L x L
+  double* X;          // L x L
+  double* W;          // L x L
+  double* lam;        // L
+  double* Bt;         // n x L
+  double* Cpart;      // nparts x L x L
+  double* C;          // L x L
+  double* sig;        // L
+  double* Vtmp;       // n x k
+  int* info;          // [0]: rank kept, [1]: route (0 chol, 1 eigen), [2]: jacobi sweeps
+  int nparts;
+};
+
+cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k,
+                         double* sigma_dev, double* V_dev, cudaStream_t st, Prof* prof);
+
+cudaError_t centered_state(const State& s, const FinalWork& f, int64_t m, cudaStream_t st);
+
+}  // namespace spca

@@ -1,0 +1,259 @@
+"""GPU parity of the CUDA library (called through its C ABI) with the FP64 oracle.
+
+Tolerances (FP32 path), from the stated gates of the method's plain FP32 form:
+  G, H_bar, gram_bar, column sums: relative Frobenius error <= 1e-5
+  sigma_1..k: relative error <= 1e-4; right singular vectors: |cos| per column
+  and the largest principal angle checked against the oracle.
+Omega's integer stream must match bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1704_07669_gb300 as spca
+from oracle import philox
+from oracle import spca as O
+from paper_1704_07669_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+TOL_STATE = 1e-5
+TOL_SIGMA = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if DEV is None:
+        pytest.fail("GPU tests need CUDA")
+    spca.build.build()
+    spca.lib()
+
+
+def _oracle_fin(l):
+    return "blocked" if l % 10 == 0 else "gram"
+
+
+def run_gpu(A_host, k, p, seed, update_rows, *, center=True, max_block_rows=0, dtype=torch.float32,
+            on_device=True, want_G=False, block_scale=None):
+    """Run the library on A (host tensor, stored values) fed in updates of update_rows rows."""
+    m, n = A_host.shape
+    l = k + p
+    A_stored = A_host.to(dtype)
+    src = A_stored.to(DEV) if on_device else A_stored
+    G = torch.zeros((m, l), device=DEV, dtype=torch.float32) if want_G else None
+    with spca.Session(n, k, p, seed, center=center, max_block_rows=max_block_rows) as s:
+        for r0 in range(0, m, update_rows):
+            blk = src[r0:r0 + update_rows]
+            if not on_device:
+                blk = blk.numpy() if dtype in (torch.float32, torch.float64) else blk
+            s.update(blk, G_out=None if G is None else G[r0:r0 + update_rows], block_scale=block_scale)
+        sigma, V = s.finalize()
+        st = s.state()
+    return {"sigma": sigma, "V": V, "state": st, "G": None if G is None else G.cpu().double().numpy()}
+
+
+def stored_f64(A_host, dtype):
+    return A_host.to(dtype).double().numpy()
+
+
+def check_sigma_V(res, ref, k, tol_sigma=TOL_SIGMA, tol_cos=1e-6):
+    s_ref = ref["sigma"]
+    nz = s_ref > 1e-12 * max(s_ref[0], 1e-300)
+    rel = np.abs(res["sigma"][nz] - s_ref[nz]) / s_ref[nz]
+    assert rel.max(initial=0.0) <= tol_sigma, rel
+    assert np.all(np.abs(res["sigma"][~nz]) <= 1e-6 * max(s_ref[0], 1.0))
+    if nz.sum():
+        cos = np.abs(np.sum(res["V"][:, nz] * ref["V"][:, nz], axis=0))
+        assert cos.min() >= 1 - tol_cos, cos
+        # same sign convention: the oracle and the library fix signs the same way
+        assert np.all(np.sum(res["V"][:, nz] * ref["V"][:, nz], axis=0) > 0)
+
+
+# ---------------------------------------------------------------------------- a1: Omega
+
+@pytest.mark.parametrize("seed,n,l", [(0, 1, 1), (17040769, 1000, 20), (2**64 - 1, 777, 61),
+                                      (123456789, 40000, 120), (5, 3, 256)])
+def test_omega_words_bit_exact(seed, n, l):
+    qn = (l + 3) // 4
+    out = torch.zeros((n, 4 * qn), dtype=torch.int32, device=DEV)
+    spca.spca_omega_words(seed, n, l, out)
+    got = out.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, philox.omega_words(n, l, seed))
+
+
+@pytest.mark.parametrize("seed,n,l", [(17040769, 10000, 60), (99, 333, 7)])
+def test_omega_values_match_oracle_rounded_to_fp32(seed, n, l):
+    out = torch.zeros((n, l), dtype=torch.float32, device=DEV)
+    spca.spca_omega(seed, n, l, out)
+    got = out.cpu().double().numpy()
+    ref = O.omega(n, l, seed, "f32")
+    diff = got != ref
+    # FP64 Box-Muller on both sides: the FP32 roundings agree except at rare ties
+    assert diff.mean() <= 1e-5
+    assert np.all(np.abs(got - ref) <= np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64) + 0.0)
+
+
+# ---------------------------------------------------------------------------- a2-a7, small workload
+
+@pytest.fixture(scope="module")
+def small():
+    return synth.workload_small()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_small_workload_state_and_result(small, dtype):
+    A = small["A"]
+    k, p, seed, mb = small["k"], small["p"], small["seed"], small["block_rows"]
+    res = run_gpu(A, k, p, seed, mb, dtype=dtype, want_G=True, max_block_rows=256)
+    A64 = stored_f64(A, dtype)
+    Om = O.omega(A64.shape[1], k + p, seed, "f32")
+    c = O.first_block_shift(A64[:mb])
+    assert np.array_equal(res["state"]["shift"].astype(np.float64), c) or \
+        np.max(np.abs(res["state"]["shift"] - c)) <= np.max(np.spacing(np.abs(c).astype(np.float32)))
+    st = O.shifted_state(O.row_blocks(A64, mb), Om, res["state"]["shift"].astype(np.float64))
+    H_bar, gram_bar = O.centering_correction(st["H"], st["gram"], st["s"], st["sG"], st["m"])
+    A_bar = O.center(A64)
+    G_bar = A_bar @ Om
+    assert np.allclose(H_bar, A_bar.T @ G_bar, rtol=0, atol=1e-9 * np.abs(H_bar).max())
+    assert O.rel_fro(res["G"], st["G"]) <= TOL_STATE
+    assert O.rel_fro(res["state"]["H_bar"], A_bar.T @ G_bar) <= TOL_STATE
+    assert O.rel_fro(res["state"]["gram_bar"], G_bar.T @ G_bar) <= TOL_STATE
+    assert O.rel_fro(res["state"]["colsum"], st["s"]) <= TOL_STATE
+    assert res["state"]["m"] == A64.shape[0]
+    ref = O.single_pass_pca(A64, k, p, seed, mb, finalize="blocked", omega_form="f32")
+    check_sigma_V(res, ref, k)
+
+
+def test_centering_off_matches_raw_oracle(small):
+    A = small["A"][:900]
+    res = run_gpu(A, 8, 7, 77, 128, center=False)
+    ref = O.single_pass_pca(stored_f64(A, torch.float32), 8, 7, 77, 128, center_columns=False,
+                            finalize="gram", omega_form="f32")
+    check_sigma_V(res, ref, 8)
+
+
+def test_host_rows_equal_device_rows_bitwise(small):
+    A = small["A"][:1200]
+    a = run_gpu(A, 10, 10, 5, 300, on_device=True, max_block_rows=512)
+    b = run_gpu(A, 10, 10, 5, 300, on_device=False, max_block_rows=512)
+    assert np.array_equal(a["sigma"], b["sigma"]) and np.array_equal(a["V"], b["V"])
+
+
+def test_update_granularity_does_not_change_the_result(small):
+    A = small["A"][:1000]
+    ref = run_gpu(A, 10, 10, 9, 1000)
+    for rows, mb in [(1, 0), (37, 64), (250, 100)]:
+        got = run_gpu(A, 10, 10, 9, rows, max_block_rows=mb)
+        assert np.max(np.abs(got["sigma"] - ref["sigma"]) / ref["sigma"]) < 2e-6
+        assert O.max_principal_sine(got["V"], ref["V"]) < 1e-4
+
+
+# ---------------------------------------------------------------------------- edge cases
+
+EDGE = [
+    # (m, n, k, p, update_rows, max_block_rows, center, note)
+    (1, 50, 1, 0, 1, 0, True, "one row, centred: all-zero data"),
+    (5, 60, 8, 4, 5, 0, True, "fewer rows than l: rank-deficient Gram"),
+    (300, 16, 10, 6, 64, 0, True, "l = n"),
+    (700, 1001, 6, 5, 700, 0, True, "n not a multiple of 4"),
+    (513, 129, 1, 0, 100, 128, True, "l = 1, ragged tiles"),
+    (400, 300, 200, 56, 400, 0, True, "l = 256 (largest)"),
+    (2500, 333, 12, 8, 2500, 0, False, "raw rows, odd n"),
+]
+
+
+@pytest.mark.parametrize("m,n,k,p,rows,mb,center,note", EDGE, ids=[e[-1] for e in EDGE])
+def test_edge_shapes(m, n, k, p, rows, mb, center, note):
+    A = synth.low_rank_plus_noise(m, n, synth.spectrum("type2", min(m, n, 80)), noise_std=1e-3, mean_std=0.3,
+                                  seed=m * 7 + n, dtype=torch.float32)
+    res = run_gpu(A, k, p, 31 + m, rows, center=center, max_block_rows=mb)
+    ref = O.single_pass_pca(stored_f64(A, torch.float32), k, p, 31 + m, rows, center_columns=center,
+                            finalize="gram", omega_form="f32")
+    check_sigma_V(res, ref, k, tol_sigma=TOL_SIGMA, tol_cos=1e-5)
+
+
+def test_strided_rows_ld_greater_than_n():
+    W = synth.low_rank_plus_noise(600, 1024, synth.spectrum("type3", 40), noise_std=1e-4, mean_std=1.0, seed=3,
+                                  dtype=torch.float32)
+    A = W[:, :999]                       # ld = 1024 > n = 999
+    res = run_gpu(A, 10, 10, 8, 200)
+    ref = O.single_pass_pca(A.double().numpy(), 10, 10, 8, 200, finalize="blocked", omega_form="f32")
+    check_sigma_V(res, ref, 10)
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float8_e4m3fn])
+def test_reduced_precision_storage(dtype):
+    A = synth.low_rank_plus_noise(800, 500, synth.spectrum("type4", 100), noise_std=1e-3, mean_std=0.0, seed=12,
+                                  dtype=torch.float32)
+    scale = None
+    if dtype == torch.float8_e4m3fn:
+        scale = float(A.abs().max()) / 448.0
+        stored = (A / scale).to(dtype)
+        A64 = stored.double().numpy() * scale
+        src = stored
+    else:
+        stored = A.to(dtype)
+        A64 = stored.double().numpy()
+        src = stored
+    with spca.Session(500, 10, 10, 21, max_block_rows=256) as s:
+        s.update(src.to(DEV), block_scale=scale)
+        sigma, V = s.finalize()
+    ref = O.single_pass_pca(A64, 10, 10, 21, 800, finalize="blocked", omega_form="f32")
+    check_sigma_V({"sigma": sigma, "V": V}, ref, 10)
+
+
+def test_non_finite_input_is_reported():
+    A = torch.randn(64, 40, device=DEV)
+    A[5, 7] = float("nan")
+    with spca.Session(40, 4, 4, 1) as s:
+        s.update(A)
+        with pytest.raises(spca.SpcaError) as ei:
+            s.finalize()
+        assert ei.value.status == 5
+
+
+def test_finalize_without_rows_is_an_error():
+    with spca.Session(40, 4, 4, 1) as s:
+        with pytest.raises(spca.SpcaError) as ei:
+            s.finalize()
+        assert ei.value.status == 5
+
+
+def test_reset_starts_a_fresh_pass(small):
+    A = small["A"][:600].to(DEV, torch.float32)
+    with spca.Session(1000, 10, 10, 3) as s:
+        s.update(torch.randn(100, 1000, device=DEV))
+        s.reset(3)
+        s.update(A)
+        a = s.finalize()
+    with spca.Session(1000, 10, 10, 3) as s:
+        s.update(A)
+        b = s.finalize()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+# ---------------------------------------------------------------------------- full size
+
+def test_full_size_100000x10000_fp32_against_oracle():
+    w = synth.workload_c2(device=DEV)
+    A = w["A"]
+    k, p, seed, mb = w["k"], w["p"], w["seed"], w["block_rows"]
+    m, n = A.shape
+    with spca.Session(n, k, p, seed) as s:
+        for r0 in range(0, m, mb):
+            s.update(A[r0:r0 + mb])
+        sigma, V = s.finalize()
+        st = s.state()
+    A64 = A.cpu().double().numpy()
+    del A
+    Om = O.omega(n, k + p, seed, "f32")
+    ref = O.single_pass_pca(A64, k, p, seed, mb, finalize="blocked", omega_form="f32")
+    # sampled state check: H_bar rows of 64 random features from the oracle's own pass
+    rng = np.random.default_rng(0)
+    rows = rng.choice(n, 64, replace=False)
+    G_bar = O.center(A64) @ Om
+    H_s = O.center(A64)[:, rows].T @ G_bar
+    assert O.rel_fro(st["H_bar"][rows], H_s) <= TOL_STATE
+    assert O.rel_fro(st["gram_bar"], G_bar.T @ G_bar) <= TOL_STATE
+    check_sigma_V({"sigma": sigma, "V": V}, ref, k, tol_cos=1e-4)
