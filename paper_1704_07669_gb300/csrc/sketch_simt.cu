@@ -272,8 +272,8 @@ g_partial_kernel(const T* __restrict__ A, int64_t m, int64_t n, int64_t ld, cons
 
 // G = sum over splits (fixed order); per group of 32 rows: Gram and column-sum partials.
 __global__ void g_finish_kernel(const float* __restrict__ Gpart, int S, int64_t mstride, int64_t m, int L, int l,
-                                float* __restrict__ G, float* __restrict__ G_out, float* __restrict__ gram_part,
-                                float* __restrict__ sG_part, int* __restrict__ flags) {
+                                float* __restrict__ G, float* __restrict__ G_out, double* __restrict__ gram_part,
+                                double* __restrict__ sG_part, int* __restrict__ flags) {
   extern __shared__ float Gs[];   // GROUP_ROWS x L
   const int64_t r0 = static_cast<int64_t>(blockIdx.x) * GROUP_ROWS;
   bool bad = false;
@@ -291,32 +291,56 @@ __global__ void g_finish_kernel(const float* __restrict__ Gpart, int S, int64_t 
   }
   if (bad) atomicOr(flags, 1);
   __syncthreads();
+  // Gram partial in double-float arithmetic: each product is split exactly into p + pe
+  // (fma), each addition into s + se (two-sum), so the group sum carries ~48 bits.
   for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
     const int c1 = e / L, c2 = e % L;
-    float acc = 0.f;
+    float hi = 0.f, lo = 0.f;
 #pragma unroll 8
-    for (int r = 0; r < GROUP_ROWS; ++r) acc = fmaf(Gs[r * L + c1], Gs[r * L + c2], acc);
-    gram_part[static_cast<int64_t>(blockIdx.x) * L * L + e] = acc;
+    for (int r = 0; r < GROUP_ROWS; ++r) {
+      const float a = Gs[r * L + c1], b = Gs[r * L + c2];
+      const float p = a * b;
+      const float pe = fmaf(a, b, -p);
+      const float s = hi + p;
+      const float bb = s - hi;
+      const float se = (hi - (s - bb)) + (p - bb);
+      hi = s;
+      lo += se + pe;
+    }
+    gram_part[static_cast<int64_t>(blockIdx.x) * L * L + e] = static_cast<double>(hi) + static_cast<double>(lo);
   }
   for (int c = threadIdx.x; c < L; c += blockDim.x) {
-    float acc = 0.f;
-    for (int r = 0; r < GROUP_ROWS; ++r) acc += Gs[r * L + c];
+    double acc = 0.0;
+    for (int r = 0; r < GROUP_ROWS; ++r) acc += static_cast<double>(Gs[r * L + c]);
     sG_part[static_cast<int64_t>(blockIdx.x) * L + c] = acc;
   }
 }
 
-__global__ void gram_accum_kernel(const float* __restrict__ gram_part, const float* __restrict__ sG_part, int parts,
-                                  int L, double* __restrict__ gram, double* __restrict__ sG) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < L * L) {
-    double acc = 0.0;
-    for (int p = 0; p < parts; ++p) acc += static_cast<double>(gram_part[static_cast<int64_t>(p) * L * L + e]);
-    gram[e] += acc;
+// Gram += sum of the group partials. A block owns 32 entries (its lanes); warp w sums the
+// partials p = w, w + 8, ... in order, then the 8 warp sums are added in warp order.
+constexpr int ACC_WARPS = 8;
+__global__ void __launch_bounds__(32 * ACC_WARPS)
+gram_accum_kernel(const double* __restrict__ gram_part, const double* __restrict__ sG_part, int parts, int L,
+                  double* __restrict__ gram, double* __restrict__ sG) {
+  __shared__ double red[ACC_WARPS][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  const int LL = L * L;
+  // entries [0, LL) are the Gram matrix, [LL, LL + L) the column sums of G
+  double acc = 0.0;
+  if (e < LL) {
+    for (int p = w; p < parts; p += ACC_WARPS) acc += gram_part[static_cast<int64_t>(p) * LL + e];
+  } else if (e < LL + L) {
+    for (int p = w; p < parts; p += ACC_WARPS) acc += sG_part[static_cast<int64_t>(p) * L + (e - LL)];
   }
-  if (e < L) {
-    double acc = 0.0;
-    for (int p = 0; p < parts; ++p) acc += static_cast<double>(sG_part[static_cast<int64_t>(p) * L + e]);
-    sG[e] += acc;
+  red[w][lane] = acc;
+  __syncthreads();
+  if (w == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int ww = 0; ww < ACC_WARPS; ++ww) t += red[ww][lane];
+    if (e < LL) gram[e] += t;
+    else if (e < LL + L) sG[e - LL] += t;
   }
 }
 
@@ -417,12 +441,12 @@ h_partial_kernel(const T* __restrict__ A, int64_t m, int64_t n, int64_t ld, cons
 }
 
 __global__ void h_finish_kernel(const float* __restrict__ Hpart, const float* __restrict__ cs_part, int T, int64_t n,
-                                int L, float* __restrict__ H, double* __restrict__ colsum) {
+                                int L, double* __restrict__ H, double* __restrict__ colsum) {
   const int64_t total = n * L;
   for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
        idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    float acc = 0.f;
-    for (int t = 0; t < T; ++t) acc += Hpart[static_cast<int64_t>(t) * total + idx];
+    double acc = 0.0;
+    for (int t = 0; t < T; ++t) acc += static_cast<double>(Hpart[static_cast<int64_t>(t) * total + idx]);
     H[idx] += acc;
     if (idx < n) {
       double a2 = 0.0;
@@ -432,7 +456,7 @@ __global__ void h_finish_kernel(const float* __restrict__ Hpart, const float* __
   }
 }
 
-__global__ void merge_kernel(float* __restrict__ H, const float* __restrict__ Hs, double* __restrict__ colsum,
+__global__ void merge_kernel(double* __restrict__ H, const double* __restrict__ Hs, double* __restrict__ colsum,
                              const double* __restrict__ colsum_s, double* __restrict__ gram,
                              const double* __restrict__ gram_s, double* __restrict__ sG,
                              const double* __restrict__ sG_s, int64_t n, int L) {
@@ -485,7 +509,8 @@ cudaError_t simt_pass_t(const State& s, const SimtWork& w, const T* rows, float 
                                                                        w.gram_part, w.sG_part, s.flags);
   prof->end(SPCA_K_G_FINISH, st);
   prof->begin(SPCA_K_GRAM_ACCUM, st);
-  gram_accum_kernel<<<(L * L + 255) / 256, 256, 0, st>>>(w.gram_part, w.sG_part, groups, L, s.gram, s.sG);
+  gram_accum_kernel<<<(L * L + L + 31) / 32, 32 * ACC_WARPS, 0, st>>>(w.gram_part, w.sG_part, groups, L, s.gram,
+                                                                       s.sG);
   prof->end(SPCA_K_GRAM_ACCUM, st);
   // a4: split the rows into T slices of whole BK chunks
   const int f_tiles = static_cast<int>((s.n + BM - 1) / BM);

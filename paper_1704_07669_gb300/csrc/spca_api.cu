@@ -87,7 +87,7 @@ struct spca_session {
 
   // state
   float* omega32 = nullptr;
-  float* H = nullptr;
+  double* H = nullptr;
   float* shift = nullptr;
   double* colsum = nullptr;
   double* sG = nullptr;
@@ -286,7 +286,7 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   CC(dalloc(&s->fin_sigma, k));
   CC(dalloc(&s->fin_V, size_t(n) * k));
 
-  CC(cudaMemsetAsync(s->H, 0, sizeof(float) * n * L, s->stream));
+  CC(cudaMemsetAsync(s->H, 0, sizeof(double) * n * L, s->stream));
   CC(cudaMemsetAsync(s->shift, 0, sizeof(float) * n, s->stream));
   CC(cudaMemsetAsync(s->colsum, 0, sizeof(double) * n, s->stream));
   CC(cudaMemsetAsync(s->sG, 0, sizeof(double) * L, s->stream));
@@ -399,7 +399,8 @@ spca_status spca_finalize(spca_session* s, double* sigma, double* V, int32_t out
   CU(cudaSetDevice(s->device));
   double* sd = out_on_device ? sigma : s->fin_sigma;
   double* vd = out_on_device ? V : s->fin_V;
-  CU(finalize_run(s->state(), s->fin, s->opt.center ? s->m : 0, s->k, sd, vd, s->stream, &s->prof));
+  CU(finalize_run(s->state(), s->fin, s->opt.center ? s->m : 0, s->k, sd, vd, s->stream, &s->prof, s->m,
+                  s->opt.center != 0));
   if (!out_on_device) {
     CU(cudaMemcpyAsync(sigma, sd, sizeof(double) * s->k, cudaMemcpyDeviceToHost, s->stream));
     CU(cudaMemcpyAsync(V, vd, sizeof(double) * s->n * s->k, cudaMemcpyDeviceToHost, s->stream));
@@ -466,7 +467,7 @@ spca_status spca_reset(spca_session* s, uint64_t seed) {
   if (st != SPCA_OK) return st;
   CU(cudaSetDevice(s->device));
   const int L = s->L;
-  CU(cudaMemsetAsync(s->H, 0, sizeof(float) * s->n * L, s->stream));
+  CU(cudaMemsetAsync(s->H, 0, sizeof(double) * s->n * L, s->stream));
   CU(cudaMemsetAsync(s->shift, 0, sizeof(float) * s->n, s->stream));
   CU(cudaMemsetAsync(s->colsum, 0, sizeof(double) * s->n, s->stream));
   CU(cudaMemsetAsync(s->sG, 0, sizeof(double) * L, s->stream));

@@ -47,8 +47,8 @@ cudaError_t launch_shift(const void* rows, int dtype, int64_t m, int64_t n, int6
 struct SimtWork {
   float* Gpart;       // gp_rows x L (split partials, S x rows_padded)
   float* G;           // mb x L
-  float* gram_part;   // ceil(mb/32) x L x L
-  float* sG_part;     // ceil(mb/32) x L
+  double* gram_part;  // ceil(mb/32) x L x L (double-float group sums)
+  double* sG_part;    // ceil(mb/32) x L
   float* Hpart;       // T x n x L
   float* cs_part;     // T x n
   int T;              // max row splits of the H contraction
@@ -60,7 +60,7 @@ struct State {
   int64_t n;
   int l, L;
   const float* omega32;   // n x L
-  float* H;               // n x L
+  double* H;              // n x L (FP64 state)
   const float* shift;     // n
   double* colsum;         // n
   double* sG;             // L
@@ -91,8 +91,11 @@ struct FinalWork {
   int nparts;
 };
 
+// m: the row count used by the centering algebra (0 when centering is off);
+// rows_seen / centered bound the rank of the Gram matrix (m - 1 when centred).
 cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k,
-                         double* sigma_dev, double* V_dev, cudaStream_t st, Prof* prof);
+                         double* sigma_dev, double* V_dev, cudaStream_t st, Prof* prof,
+                         int64_t rows_seen, bool centered);
 
 cudaError_t centered_state(const State& s, const FinalWork& f, int64_t m, cudaStream_t st);
 
