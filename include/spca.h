@@ -172,6 +172,14 @@ const char* spca_last_error(const spca_session* s);
 int64_t spca_rows_seen(const spca_session* s);
 
 /*
+ * spca_describe - one-line text describing the session's arithmetic and launch
+ * configuration (math form, padded l, cluster size, features per CTA, clusters,
+ * shared memory per CTA). The string is owned by the session and valid until the
+ * next call on it; "" for a NULL session.
+ */
+const char* spca_describe(spca_session* s);
+
+/*
  * spca_reset - start a new pass on the same session: zero H, the Gram matrix,
  * the sums and the row count, forget the shift, and regenerate Omega for
  * `seed` (Alg. 4 steps 1-3 again, without reallocating). Stream-ordered.
@@ -188,7 +196,8 @@ typedef enum {
   SPCA_K_H_PARTIAL = 5,   /* a4: H += A_hat^T G contraction (+ col sums)   */
   SPCA_K_H_FINISH = 6,    /* a4/a5: split reduction into H and col sums    */
   SPCA_K_FINALIZE = 7,    /* a7: all FP64 finalisation kernels together    */
-  SPCA_K_COUNT = 8
+  SPCA_K_TC_SKETCH = 8,   /* a2-a5 fused on the tensor cores (BF16 math)    */
+  SPCA_K_COUNT = 9
 } spca_kernel_id;
 
 /*

@@ -61,6 +61,7 @@ def lib():
             "spca_last_error": (ctypes.c_char_p, [vp]),
             "spca_rows_seen": (i64, [vp]),
             "spca_reset": (i32, [vp, u64]),
+            "spca_describe": (ctypes.c_char_p, [vp]),
             "spca_set_profiling": (i32, [vp, i32]),
             "spca_get_profile": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
             "spca_clear_profile": (i32, [vp]),
@@ -176,11 +177,17 @@ def spca_rows_seen(handle):
     return lib().spca_rows_seen(handle)
 
 
+def spca_describe(handle):
+    d = lib().spca_describe(handle)
+    return d.decode() if d else ""
+
+
 def spca_reset(handle, seed):
     _check(lib().spca_reset(handle, int(seed) & 0xFFFFFFFFFFFFFFFF), handle)
 
 
-KERNEL_NAMES = ["omega", "shift", "g_partial", "g_finish", "gram_accum", "h_partial", "h_finish", "finalize"]
+KERNEL_NAMES = ["omega", "shift", "g_partial", "g_finish", "gram_accum", "h_partial", "h_finish", "finalize",
+                "tc_sketch"]
 
 
 def spca_set_profiling(handle, on):

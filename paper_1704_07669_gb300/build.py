@@ -54,9 +54,11 @@ def build(force=False, verbose=False):
     srcs = sources()
     objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
+    extra = os.environ.get("SPCA_NVCC_FLAGS", "").split()   # e.g. -DSPCA_TC_TRACE
+
     def compile_one(pair):
         src, obj = pair
-        cmd = [nvcc] + ARCH + CFLAGS + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + CFLAGS + extra + ["-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

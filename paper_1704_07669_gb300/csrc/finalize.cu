@@ -239,7 +239,6 @@ __device__ void blk_gemm(const double* A, bool ta, const double* B, bool tb, dou
 __device__ void blk_jacobi_eig(double* A, double* W, double* lam, int d, int ld, double* red, int* sweeps_out) {
   __shared__ double cs[kMaxL / 2 + 1], sn[kMaxL / 2 + 1];
   __shared__ int P[kMaxL / 2 + 1], Q[kMaxL / 2 + 1];
-  __shared__ int active;
   const int de = d + (d & 1);           // even count; index d (when d is odd) is a dummy
   const int npairs = de / 2;
   for (int e = threadIdx.x; e < d * d; e += blockDim.x) W[(e / d) * ld + e % d] = ((e / d) == (e % d)) ? 1.0 : 0.0;
@@ -259,8 +258,6 @@ __device__ void blk_jacobi_eig(double* A, double* W, double* lam, int d, int ld,
     // themselves (about eps * lambda_max per entry) keeps it from shrinking further
     if (off_sum <= 1e-26 * tot_sum || tot_sum == 0.0) break;
     for (int round = 0; round < de - 1; ++round) {
-      if (threadIdx.x == 0) active = 0;
-      __syncthreads();
       for (int pi = threadIdx.x; pi < npairs; pi += blockDim.x) {
         int p, q;
         if (pi == 0) {
@@ -280,13 +277,11 @@ __device__ void blk_jacobi_eig(double* A, double* W, double* lam, int d, int ld,
             const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
             c = 1.0 / sqrt(1.0 + t * t);
             s = t * c;
-            active = 1;
           }
         }
         P[pi] = p; Q[pi] = q; cs[pi] = c; sn[pi] = s;
       }
       __syncthreads();
-      if (!active) continue;
       // rows: A <- J^T A
       for (int e = threadIdx.x; e < npairs * d; e += blockDim.x) {
         const int pi = e / d, j = e % d;

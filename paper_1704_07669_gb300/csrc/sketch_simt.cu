@@ -592,6 +592,12 @@ cudaError_t simt_pass(const State& s, const SimtWork& w, const void* rows, int d
   }
 }
 
+cudaError_t launch_gram_accum(const double* gram_part, const double* sG_part, int parts, int L, double* gram,
+                              double* sG, cudaStream_t st) {
+  gram_accum_kernel<<<(L * L + L + 31) / 32, 32 * ACC_WARPS, 0, st>>>(gram_part, sG_part, parts, L, gram, sG);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_merge(const State& dst, const State& src, cudaStream_t st) {
   const int64_t total = dst.n > dst.L ? dst.n * dst.L : static_cast<int64_t>(dst.L) * dst.L;
   merge_kernel<<<grid_for(total, 256), 256, 0, st>>>(dst.H, src.H, dst.colsum, src.colsum, dst.gram,

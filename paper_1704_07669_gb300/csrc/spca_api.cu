@@ -84,6 +84,7 @@ struct spca_session {
   int64_t m = 0;
   bool shift_set = false;
   char err[512] = "";
+  char desc[256] = "";
 
   // state
   float* omega32 = nullptr;
@@ -110,6 +111,11 @@ struct spca_session {
   cudaEvent_t copied[2] = {nullptr, nullptr};
   cudaEvent_t consumed[2] = {nullptr, nullptr};
   int next_stage = 0;
+
+  // tensor-core path (math = BF16)
+  bool tc = false;
+  TcWork tcw{};
+  TcPending pend;
 
   Prof prof;
 
@@ -154,7 +160,8 @@ void free_all(spca_session* s) {
   void* bufs[] = {s->omega32, s->H, s->shift, s->colsum, s->sG, s->gram, s->flags, s->simt.Gpart, s->simt.G,
                   s->simt.gram_part, s->simt.sG_part, s->simt.Hpart, s->simt.cs_part, s->shift_part, s->fin.Hbar,
                   s->fin.gbar, s->fin.T, s->fin.X, s->fin.W, s->fin.lam, s->fin.Bt, s->fin.Cpart, s->fin.C,
-                  s->fin.sig, s->fin.info, s->fin_sigma, s->fin_V, s->dstage[0], s->dstage[1]};
+                  s->fin.sig, s->fin.info, s->fin_sigma, s->fin_V, s->dstage[0], s->dstage[1],
+                  s->tcw.om16, s->tcw.Hpart, s->tcw.cs_part, s->tcw.gram_part, s->tcw.sG_part};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < 2; ++i) {
@@ -174,12 +181,37 @@ spca_status check_usable(spca_session* s) {
   return SPCA_OK;
 }
 
-// One piece of at most max_block_rows rows, resident on the device.
+// Launch the tensor-core pass over the row blocks batched so far.
+spca_status flush_tc(spca_session* s) {
+  if (!s->tc || s->pend.nseg == 0) return SPCA_OK;
+  CU(tc_pass(s->state(), s->tcw, s->pend, s->stream, &s->prof));
+  s->pend.nseg = 0;
+  s->pend.rows_total = 0;
+  return SPCA_OK;
+}
+
+// One piece of rows resident on the device. The FP32 path processes it at once; the
+// tensor-core path batches device-resident blocks (defer) into one persistent launch.
 spca_status run_piece(spca_session* s, const void* rows, int64_t m, int64_t ld, int dtype, float scale,
-                      float* G_out) {
+                      float* G_out, bool defer) {
   if (s->opt.center && !s->shift_set) {
     CU(launch_shift(rows, dtype, m, s->n, ld, scale, s->shift, s->shift_part, s->stream, &s->prof));
     s->shift_set = true;
+  }
+  if (s->tc) {
+    if (s->pend.nseg == kTcPendingMax) {
+      spca_status st = flush_tc(s);
+      if (st != SPCA_OK) return st;
+    }
+    const int i = s->pend.nseg++;
+    s->pend.rows[i] = static_cast<const float*>(rows);
+    s->pend.m[i] = m;
+    s->pend.ld[i] = ld;
+    s->pend.gout[i] = G_out;
+    s->pend.rows_total += m;
+    s->m += m;
+    if (!defer || s->pend.rows_total >= kTcPendingRows) return flush_tc(s);
+    return SPCA_OK;
   }
   SimtWork w = s->simt;
   CU(simt_pass(s->state(), w, rows, dtype, scale, m, ld, G_out, s->stream, &s->prof));
@@ -215,8 +247,13 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   if (opt) o = *opt;
   if (o.reserved != 0 || (o.center != 0 && o.center != 1) || o.max_block_rows < 0)
     return fail(nullptr, SPCA_E_INVALID, "invalid options");
-  if (o.math != SPCA_MATH_FP32)
+  if (o.math != SPCA_MATH_FP32 && o.math != SPCA_MATH_BF16)
     return fail(nullptr, SPCA_E_UNSUPPORTED, "math form %d is not available in this build", o.math);
+  TcConfig tcfg{};
+  if (o.math == SPCA_MATH_BF16 && !tc_config(n, pad_l(static_cast<int>(l)), &tcfg))
+    return fail(nullptr, SPCA_E_UNSUPPORTED,
+                "the tensor-core pass needs l <= 64 and n <= 16 x 640 on a device with 16-CTA clusters "
+                "(n=%lld, l=%lld)", (long long)n, (long long)l);
 
   s = new (std::nothrow) spca_session();
   if (!s) return fail(nullptr, SPCA_E_NOMEM, "host allocation failed");
@@ -245,7 +282,8 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
     s->own_stream = true;
   }
   CC(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
-  CC(dalloc(&s->omega32, n * L));
+  s->tc = (o.math == SPCA_MATH_BF16);
+  if (!s->tc) CC(dalloc(&s->omega32, n * L));
   CC(dalloc(&s->H, n * L));
   CC(dalloc(&s->shift, n));
   CC(dalloc(&s->colsum, n));
@@ -256,18 +294,30 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
 
   SimtWork& w = s->simt;
   w.mb = mb;
-  const int64_t mb_pad = ((mb + 127) / 128) * 128;
-  w.gp_rows = mb_pad > 65536 ? mb_pad : 65536;
-  s->gp_rows = w.gp_rows;
-  int64_t tmax = (int64_t(16) << 20) / (n * L);
-  w.T = static_cast<int>(tmax < 1 ? 1 : (tmax > 16 ? 16 : tmax));
-  CC(dalloc(&w.Gpart, size_t(s->gp_rows) * L));
-  CC(dalloc(&w.G, size_t(mb) * L));
-  const int64_t groups = (mb + 31) / 32;
-  CC(dalloc(&w.gram_part, size_t(groups) * L * L));
-  CC(dalloc(&w.sG_part, size_t(groups) * L));
-  CC(dalloc(&w.Hpart, size_t(w.T) * n * L));
-  CC(dalloc(&w.cs_part, size_t(w.T) * n));
+  if (!s->tc) {
+    const int64_t mb_pad = ((mb + 127) / 128) * 128;
+    w.gp_rows = mb_pad > 65536 ? mb_pad : 65536;
+    s->gp_rows = w.gp_rows;
+    int64_t tmax = (int64_t(16) << 20) / (n * L);
+    w.T = static_cast<int>(tmax < 1 ? 1 : (tmax > 16 ? 16 : tmax));
+    CC(dalloc(&w.Gpart, size_t(s->gp_rows) * L));
+    CC(dalloc(&w.G, size_t(mb) * L));
+    const int64_t groups = (mb + 31) / 32;
+    CC(dalloc(&w.gram_part, size_t(groups) * L * L));
+    CC(dalloc(&w.sG_part, size_t(groups) * L));
+    CC(dalloc(&w.Hpart, size_t(w.T) * n * L));
+    CC(dalloc(&w.cs_part, size_t(w.T) * n));
+  } else {
+    TcWork& t = s->tcw;
+    t.cfg = tcfg;
+    const int64_t npad = static_cast<int64_t>(tcfg.CS) * tcfg.w;
+    const int64_t nctas = static_cast<int64_t>(tcfg.nclusters) * tcfg.CS;
+    CC(dalloc(&t.om16, size_t(npad) * L));
+    CC(dalloc(&t.Hpart, size_t(tcfg.nclusters) * npad * L));
+    CC(dalloc(&t.cs_part, size_t(tcfg.nclusters) * npad));
+    CC(dalloc(&t.gram_part, size_t(nctas) * L * L));
+    CC(dalloc(&t.sG_part, size_t(nctas) * L));
+  }
   CC(dalloc(&s->shift_part, size_t(kShiftParts) * n));
 
   FinalWork& f = s->fin;
@@ -292,7 +342,11 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   CC(cudaMemsetAsync(s->sG, 0, sizeof(double) * L, s->stream));
   CC(cudaMemsetAsync(s->gram, 0, sizeof(double) * L * L, s->stream));
   CC(cudaMemsetAsync(s->flags, 0, sizeof(int) * 4, s->stream));
-  CC(launch_omega_f32(seed, n, s->l, L, s->omega32, L, s->stream));
+  if (s->tc) {
+    CC(launch_omega_bf16(seed, n, static_cast<int64_t>(tcfg.CS) * tcfg.w, s->l, L, s->tcw.om16, s->stream, nullptr));
+  } else {
+    CC(launch_omega_f32(seed, n, s->l, L, s->omega32, L, s->stream));
+  }
   CC(cudaStreamSynchronize(s->stream));
 #undef CC
   *out = s;
@@ -317,6 +371,8 @@ spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t 
   }
   if (rows_on_device != 0 && rows_on_device != 1) return fail(s, SPCA_E_INVALID, "rows_on_device must be 0 or 1");
   CU(cudaSetDevice(s->device));
+  if (s->tc && dtype != SPCA_F32)
+    return fail(s, SPCA_E_UNSUPPORTED, "the tensor-core pass reads FP32 rows in this build (dtype %d)", dtype);
   const int64_t mb = s->simt.mb;
   if (rows_on_device) {
     cudaPointerAttributes attr;
@@ -328,7 +384,7 @@ spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t 
     for (int64_t r0 = 0; r0 < m_i; r0 += mb) {
       const int64_t mr = (m_i - r0) < mb ? (m_i - r0) : mb;
       const char* base = static_cast<const char*>(rows) + size_t(r0) * ld * es;
-      st = run_piece(s, base, mr, ld, dtype, scale, G_out ? G_out + r0 * s->l : nullptr);
+      st = run_piece(s, base, mr, ld, dtype, scale, G_out ? G_out + r0 * s->l : nullptr, true);
       if (st != SPCA_OK) return st;
     }
     return SPCA_OK;
@@ -379,7 +435,7 @@ spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t 
     }
     CU(cudaEventRecord(s->copied[b], s->copy_stream));
     CU(cudaStreamWaitEvent(s->stream, s->copied[b], 0));
-    st = run_piece(s, s->dstage[b], mr, s->n, dtype, scale, G_out ? G_out + r0 * s->l : nullptr);
+    st = run_piece(s, s->dstage[b], mr, s->n, dtype, scale, G_out ? G_out + r0 * s->l : nullptr, false);
     if (st != SPCA_OK) return st;
     CU(cudaEventRecord(s->consumed[b], s->stream));
   }
@@ -397,6 +453,8 @@ spca_status spca_finalize(spca_session* s, double* sigma, double* V, int32_t out
   if (!sigma || !V) return fail(s, SPCA_E_INVALID, "sigma and V must be non-NULL");
   if (s->m < 1) return fail(s, SPCA_E_NUMERIC, "no rows accumulated yet");
   CU(cudaSetDevice(s->device));
+  st = flush_tc(s);
+  if (st != SPCA_OK) return st;
   double* sd = out_on_device ? sigma : s->fin_sigma;
   double* vd = out_on_device ? V : s->fin_V;
   CU(finalize_run(s->state(), s->fin, s->opt.center ? s->m : 0, s->k, sd, vd, s->stream, &s->prof, s->m,
@@ -408,6 +466,7 @@ spca_status spca_finalize(spca_session* s, double* sigma, double* V, int32_t out
   // the non-finite flag is read after the finalisation kernels so that the stream never idles mid-call
   CU(cudaMemcpyAsync(s->host_flags, s->flags, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CU(cudaStreamSynchronize(s->stream));
+  if (s->host_flags[0] & 2) return fail(s, SPCA_E_TIMEOUT, "a bounded device wait gave up during the pass");
   if (s->host_flags[0] & 1) return fail(s, SPCA_E_NUMERIC, "non-finite values (NaN/Inf) reached the sketch");
   return SPCA_OK;
 }
@@ -417,6 +476,8 @@ spca_status spca_get_state(spca_session* s, double* H_bar, double* gram_bar, dou
   spca_status st = check_usable(s);
   if (st != SPCA_OK) return st;
   CU(cudaSetDevice(s->device));
+  st = flush_tc(s);
+  if (st != SPCA_OK) return st;
   CU(centered_state(s->state(), s->fin, s->opt.center ? s->m : 0, s->stream));
   const int L = s->L, l = s->l;
   if (H_bar)
@@ -455,6 +516,14 @@ spca_status spca_merge(spca_session* dst, const spca_session* src) {
     if (!same) return fail(s, SPCA_E_INVALID, "sessions use different shifts; give both the same first rows");
   }
   CU(cudaSetDevice(dst->device));
+  st = flush_tc(dst);
+  if (st != SPCA_OK) return st;
+  {
+    // src's batched blocks belong to its sum too (flushing does not change what it represents)
+    spca_session* ms = const_cast<spca_session*>(src);
+    st = flush_tc(ms);
+    if (st != SPCA_OK) return fail(s, st, "flushing src failed: %s", ms->err);
+  }
   CU(cudaStreamSynchronize(src->stream));
   CU(launch_merge(dst->state(), src->state(), dst->stream));
   CU(cudaStreamSynchronize(dst->stream));
@@ -474,7 +543,14 @@ spca_status spca_reset(spca_session* s, uint64_t seed) {
   CU(cudaMemsetAsync(s->gram, 0, sizeof(double) * L * L, s->stream));
   CU(cudaMemsetAsync(s->flags, 0, sizeof(int) * 4, s->stream));
   s->seed = seed;
-  CU(launch_omega_f32(seed, s->n, s->l, L, s->omega32, L, s->stream, &s->prof));
+  s->pend.nseg = 0;          // blocks batched for the previous pass are dropped with it
+  s->pend.rows_total = 0;
+  if (s->tc) {
+    CU(launch_omega_bf16(seed, s->n, static_cast<int64_t>(s->tcw.cfg.CS) * s->tcw.cfg.w, s->l, L, s->tcw.om16,
+                         s->stream, &s->prof));
+  } else {
+    CU(launch_omega_f32(seed, s->n, s->l, L, s->omega32, L, s->stream, &s->prof));
+  }
   s->m = 0;
   s->shift_set = false;
   return SPCA_OK;
@@ -515,6 +591,8 @@ spca_status spca_clear_profile(spca_session* s) {
 spca_status spca_sync(spca_session* s) {
   spca_status st = check_usable(s);
   if (st != SPCA_OK) return st;
+  st = flush_tc(s);
+  if (st != SPCA_OK) return st;
   CU(cudaStreamSynchronize(s->stream));
   return SPCA_OK;
 }
@@ -532,6 +610,20 @@ spca_status spca_destroy(spca_session* s) {
 const char* spca_last_error(const spca_session* s) { return s ? s->err : g_thread_err; }
 
 int64_t spca_rows_seen(const spca_session* s) { return s ? s->m : -1; }
+
+const char* spca_describe(spca_session* s) {
+  if (!s) return "";
+  if (s->tc) {
+    snprintf(s->desc, sizeof(s->desc),
+             "math=bf16 n=%lld l=%d L=%d cluster=%d w=%d clusters=%d ctas=%d smem=%u", (long long)s->n, s->l, s->L,
+             s->tcw.cfg.CS, s->tcw.cfg.w, s->tcw.cfg.nclusters, s->tcw.cfg.nclusters * s->tcw.cfg.CS,
+             s->tcw.cfg.smem);
+  } else {
+    snprintf(s->desc, sizeof(s->desc), "math=fp32 n=%lld l=%d L=%d max_block_rows=%lld row_splits<=%d",
+             (long long)s->n, s->l, s->L, (long long)s->simt.mb, s->simt.T);
+  }
+  return s->desc;
+}
 
 spca_status spca_omega_words(uint64_t seed, int64_t n, int32_t l, uint32_t* out) {
   spca_session* s = nullptr;

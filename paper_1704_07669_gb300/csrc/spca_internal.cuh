@@ -74,6 +74,45 @@ cudaError_t simt_pass(const State& s, const SimtWork& w, const void* rows, int d
 // Merge: dst += src (H, colsum, sG, gram).
 cudaError_t launch_merge(const State& dst, const State& src, cudaStream_t st);
 
+// gram += sum of `parts` partial Gram matrices (fixed order), sG likewise.
+cudaError_t launch_gram_accum(const double* gram_part, const double* sG_part, int parts, int L, double* gram,
+                              double* sG, cudaStream_t st);
+
+// ---------------------------------------------------------------- tensor-core pass (BF16)
+struct TcConfig {
+  int CS;             // cluster size (CTAs sharing one row tile, splitting the features)
+  int w;              // features per CTA (multiple of 128)
+  int nclusters;      // co-resident clusters launched
+  uint32_t smem;      // dynamic shared memory per CTA
+};
+
+struct TcWork {
+  TcConfig cfg;
+  __nv_bfloat16* om16;   // Omega, BF16, pre-swizzled 64-feature chunks (CS*w/64 chunks x L x 64)
+  float* Hpart;          // nclusters x (CS*w) x L
+  double* cs_part;       // nclusters x (CS*w)
+  double* gram_part;     // nclusters*CS x L x L
+  double* sG_part;       // nclusters*CS x L
+};
+
+constexpr int kTcPendingMax = 48;       // row blocks batched into one launch
+constexpr int64_t kTcPendingRows = 65536;
+
+struct TcPending {
+  int nseg = 0;
+  int64_t rows_total = 0;
+  const float* rows[kTcPendingMax];
+  int64_t m[kTcPendingMax];
+  int64_t ld[kTcPendingMax];
+  float* gout[kTcPendingMax];
+};
+
+// Whether (n, L) fits the fused kernel; fills the launch configuration.
+bool tc_config(int64_t n, int L, TcConfig* cfg);
+cudaError_t launch_omega_bf16(uint64_t seed, int64_t n, int64_t npad, int l, int L, __nv_bfloat16* out,
+                              cudaStream_t st, Prof* prof);
+cudaError_t tc_pass(const State& s, const TcWork& w, const TcPending& pend, cudaStream_t st, Prof* prof);
+
 // FP64 finalisation (a7). Scratch is owned by the session.
 struct FinalWork {
   double* Hbar;       // n x L
