@@ -4,27 +4,33 @@
 //
 // Decomposition. A thread-block cluster of CS CTAs splits the n features: CTA `rank`
 // owns features [rank*w, rank*w + w). Clusters walk over 128-row tiles of the rows
-// handed to the launch. For one tile, every CTA of the cluster
-//   1. loads its 128 x w slice of A (FP32), subtracts the shift c, rounds to BF16 and
-//      writes it to shared memory in the 128-byte-swizzled K-major layout (a2);
-//   2. MMA1: D1[128 x L] = A_hat_slice (K-major) x Omega_slice (K-major chunks of 64
-//      features streamed by 1-D bulk copies from a pre-swizzled BF16 copy of Omega):
-//      the partial sketch of its features (a3);
-//   3. reduces the CS partials of D1 over distributed shared memory in a fixed order:
-//      CTA `rank` sums rows [rank*128/CS, (rank+1)*128/CS), rounds them to BF16 (the
-//      G_hat' that every later step uses) and writes them into G^T tiles of all CTAs;
-//   4. accumulates the Gram matrix G'^T G' and 1^T G' of its rows (a5);
-//   5. MMA2: H[w x L] += A_hat_slice^T (the same shared-memory tile read MN-major) x G'
+// handed to the launch. Per tile, in every CTA of the cluster:
+//   1. eight loader warps read the 128 x w slice of A (FP32) one 64-feature block at a
+//      time, subtract the shift c, round to BF16 and store it in shared memory in the
+//      128-byte-swizzled K-major layout (a2). Two register batches are in flight, and
+//      the next tile's slice is prefetched into L2 while this tile computes;
+//   2. MMA1 (issued by a ninth warp as soon as each feature block is stored):
+//      D1[128 x L] = A_hat_slice (K-major) x Omega_slice (K-major chunks of 64 features
+//      streamed through a ring by 1-D bulk copies of a pre-swizzled BF16 Omega) (a3);
+//   3. the CS partials of D1 are reduced over distributed shared memory in a fixed
+//      order: CTA `rank` sums rows [rank*128/CS, (rank+1)*128/CS) and rounds them to
+//      BF16 (the G_hat' that every later step uses); column `l` of G' is set to 1 for
+//      every valid row, so that MMA2 also produces the column sums of A_hat (a5);
+//   4. each CTA accumulates G'^T G' and 1^T G' of its rows and publishes them packed;
+//      every CTA pulls all 128 rows into its own G^T operand tile;
+//   5. MMA2: H[w x L] += A_hat_slice^T (the same shared-memory tile, read MN-major) x G'
 //      (K-major), H resident in TMEM for the whole launch (a4).
-// Column sums of the BF16 A_hat values are kept by the loading threads (a5). At the
-// end each CTA writes its H slice, sums and Gram partial; a finish kernel adds the
-// per-cluster partials to the FP64 session state in a fixed order.
+// At the end each CTA writes its H slice (with the column sums in column l) and its Gram
+// partial; a finish kernel adds the per-cluster partials to the FP64 session state in a
+// fixed order.
 //
-// All mbarrier waits are bounded; a CTA that gives up sets flags[0] bit 2 and keeps
-// taking part in the cluster barriers (every CTA runs the same number of them).
+// All mbarrier waits are bounded; a thread that gives up sets flags[0] bit 2, skips
+// later waits and keeps taking part in the cluster barriers (every CTA of a cluster
+// runs the same number of them), so no wait can hang the GPU.
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 
 #include "philox.cuh"
@@ -34,9 +40,14 @@ namespace spca {
 
 namespace {
 
-constexpr int TC_ROWS = 128;      // rows per tile = M of MMA1
-constexpr int TC_NT = 256;        // threads per CTA
-constexpr int OM_STAGES = 4;      // Omega chunk ring depth
+constexpr int TC_ROWS = 128;       // rows per tile = M of MMA1
+constexpr int TC_LOADERS = 352;    // warps 0-10 load and convert A
+constexpr int TC_NT = 384;         // + warp 11: MMA issue, Omega ring, L2 prefetch
+constexpr int MMA_WARP = 11;
+constexpr int LOAD_ITEMS = (TC_ROWS * 8 + TC_LOADERS - 1) / TC_LOADERS;   // (row, chunk) items per loader
+constexpr int OM_STAGES = 4;       // Omega chunk ring depth
+constexpr int MAX_CHUNKS = 10;     // w / 64 <= 10
+constexpr int GRAM_PER_THREAD = 6;    // lower-triangle Gram entries per thread (L <= 64)
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t WAIT_LIMIT = 1u << 20;   // tries per wait; a thread that gives up skips later waits
 
@@ -52,7 +63,8 @@ __host__ __device__ __forceinline__ uint32_t sw128(uint32_t row, uint32_t colbyt
   return o ^ (((o >> 7) & 7u) << 4);
 }
 
-// tcgen05 shared-memory matrix descriptor, 128-byte swizzle
+// tcgen05 shared-memory matrix descriptor, 128-byte swizzle. The start address sits in
+// the low 14 bits (address / 16), so adding (byte offset / 16) moves the start.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
   d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
@@ -72,6 +84,9 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn, int b_
 
 __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
@@ -95,6 +110,9 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                "l"(src), "r"(bytes), "r"(mbar)
                : "memory");
 }
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -116,8 +134,8 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_cta() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_cluster() { asm volatile("fence.proxy.async.shared::cluster;" ::: "memory"); }
 __device__ __forceinline__ void cluster_sync() {
+  __syncwarp();   // the .aligned forms need the whole warp converged
   asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -140,15 +158,17 @@ __device__ __forceinline__ uint32_t mapa(uint32_t a, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
   return r;
 }
-__device__ __forceinline__ float4 ld_dsmem_v4(uint32_t a) {
+__device__ __forceinline__ float4 ld_dsmem_v4f(uint32_t a) {
   float4 v;
   asm volatile("ld.shared::cluster.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a)
                : "memory");
   return v;
 }
-__device__ __forceinline__ void st_dsmem_v4(uint32_t a, uint4 v) {
-  asm volatile("st.shared::cluster.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+__device__ __forceinline__ uint4 ld_dsmem_v4u(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared::cluster.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a)
                : "memory");
+  return v;
 }
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
@@ -162,7 +182,7 @@ __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(_
 
 struct TcLayout {
   int L, w, CS, RPC;
-  uint32_t a_bytes, ring_bytes, gt_bytes, shift_bytes, y_bytes, bar_bytes, total;
+  uint32_t a_bytes, ring_bytes, gt_bytes, shift_bytes, y_bytes, yt_bytes, bar_bytes, total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int L, int w, int CS) {
@@ -174,9 +194,10 @@ __host__ __device__ inline TcLayout tc_layout(int L, int w, int CS) {
   t.ring_bytes = ((ring > xch ? ring : xch) + 1023u) & ~1023u;
   t.gt_bytes = 256u * static_cast<uint32_t>(L);                        // G^T: L x 128 rows BF16
   t.shift_bytes = ((static_cast<uint32_t>(w) * 4u) + 15u) & ~15u;
-  t.y_bytes = ((static_cast<uint32_t>(t.RPC) * L * 4u) + 15u) & ~15u;
-  t.bar_bytes = 8u * (2 * OM_STAGES + 2);
-  t.total = 1024u + t.a_bytes + t.ring_bytes + t.gt_bytes + t.shift_bytes + t.y_bytes + t.bar_bytes;
+  t.y_bytes = ((static_cast<uint32_t>(t.RPC) * L * 4u) + 15u) & ~15u;  // own reduced rows, FP32
+  t.yt_bytes = static_cast<uint32_t>(L) * (t.RPC / 8) * 16u;            // same, packed BF16 [L][RPC/8]
+  t.bar_bytes = 8u * (2 * OM_STAGES + MAX_CHUNKS + 2);
+  t.total = 1024u + t.a_bytes + t.ring_bytes + t.gt_bytes + t.shift_bytes + t.y_bytes + t.yt_bytes + t.bar_bytes;
   return t;
 }
 
@@ -199,8 +220,7 @@ struct TcArgs {
   int vec_ok;
   const float* shift;
   const __nv_bfloat16* om16;   // chunk g at om16 + g * L * 64 (pre-swizzled)
-  float* Hpart;                // nclusters x (CS w) x L
-  double* cs_part;             // nclusters x (CS w)
+  float* Hpart;                // nclusters x (CS w) x L (column l: column sums)
   double* gram_part;           // nctas x L x L
   double* sG_part;             // nctas x L
   int* flags;
@@ -224,22 +244,31 @@ struct TcArgs {
 
 namespace {
 
+__device__ __forceinline__ int find_seg(const TcArgs& a, int64_t tile) {
+  int sgi = 0;
+  while (sgi + 1 < a.nseg && a.seg[sgi + 1].tile0 <= tile) ++sgi;
+  return sgi;
+}
+
+// one CTA of 12 warps per SM (<= 170 registers per thread)
 __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int L = a.L, w = a.w, CS = a.CS;
+  const int L = a.L, w = a.w, CS = a.CS, l = a.l;
   const TcLayout lay = tc_layout(L, w, CS);
-  const int RPC = lay.RPC;
+  const int RPC = lay.RPC, G8 = RPC / 8;
   uint8_t* sA = base;
   uint8_t* sRing = sA + lay.a_bytes;
   float* sX = reinterpret_cast<float*>(sRing);              // exchange buffer (aliases the ring)
   uint8_t* sGt = sRing + lay.ring_bytes;
   float* sShift = reinterpret_cast<float*>(sGt + lay.gt_bytes);
   float* sY = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(sShift) + lay.shift_bytes);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sY) + lay.y_bytes);
-  uint64_t* full = bars;                    // [OM_STAGES]
-  uint64_t* empty = bars + OM_STAGES;       // [OM_STAGES]
-  uint64_t* mma1_done = bars + 2 * OM_STAGES;
+  uint4* sYt = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(sY) + lay.y_bytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sYt) + lay.yt_bytes);
+  uint64_t* full = bars;                       // [OM_STAGES]
+  uint64_t* empty = bars + OM_STAGES;          // [OM_STAGES]
+  uint64_t* ablk = bars + 2 * OM_STAGES;       // [MAX_CHUNKS]: feature block stored
+  uint64_t* mma1_done = ablk + MAX_CHUNKS;
   uint64_t* mma2_done = mma1_done + 1;
   __shared__ uint32_t tmem_sh;
   __shared__ int dead_sh;
@@ -255,6 +284,9 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
   const int xld = L + 4;                    // exchange row stride (floats)
   const uint32_t chunk_bytes = static_cast<uint32_t>(L) * 128u;
   const int64_t g0 = f0 / 64;               // first Omega chunk of this slice
+  // bytes of one row segment of this slice that exist (features < n), for L2 prefetch
+  int64_t seg_feats = n - f0 < w ? n - f0 : w;
+  const uint32_t pf_bytes = seg_feats > 0 ? static_cast<uint32_t>((seg_feats * 4) & ~int64_t(15)) : 0u;
 
   for (int i = tid; i < w; i += TC_NT) sShift[i] = (f0 + i < n) ? a.shift[f0 + i] : 0.f;
   if (tid == 0) {
@@ -262,6 +294,7 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
       mbar_init(su32(&full[s]), 1);
       mbar_init(su32(&empty[s]), 1);
     }
+    for (int c = 0; c < MAX_CHUNKS; ++c) mbar_init(su32(&ablk[c]), TC_LOADERS);
     mbar_init(su32(mma1_done), 1);
     mbar_init(su32(mma2_done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -279,22 +312,12 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
   const uint32_t tD1 = tmem;
   const uint32_t tH = tmem + static_cast<uint32_t>(L);
 
-  // loader mapping: CPR chunks of 8 features per row; RP row phases
-  const int CPR = w / 8;
-  const int RP = TC_NT / CPR;
-  const bool loader = tid < RP * CPR;
-  const int cc = loader ? tid % CPR : 0;
-  const int rp = loader ? tid / CPR : 0;
-  double cs_acc[8];
+  double gram_acc[GRAM_PER_THREAD];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) cs_acc[i] = 0.0;
-  // Gram entries owned by this thread: e = tid + TC_NT * i, i < 16 (L <= 64)
-  double gram_acc[16];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) gram_acc[i] = 0.0;
+  for (int i = 0; i < GRAM_PER_THREAD; ++i) gram_acc[i] = 0.0;
   double sg_acc = 0.0;
 
-  // thread-0 ring bookkeeping
+  // MMA-thread state
   uint32_t fills[OM_STAGES] = {0, 0, 0, 0};
   uint32_t cons[OM_STAGES] = {0, 0, 0, 0};
   uint32_t iter = 0;
@@ -302,50 +325,39 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
   bool any_tile = false;
   const uint32_t id1 = idesc_bf16(TC_ROWS, L, 0, 0);
   const uint32_t id2 = idesc_bf16(TC_ROWS, L, 1, 0);
+  const uint64_t dA1 = sdesc(su32(sA), 16, 1024);        // MMA1 A: K-major rows x features
+  const uint64_t dA2 = sdesc(su32(sA), 16384, 1024);     // MMA2 A: MN-major features x rows
+  const uint64_t dB2 = sdesc(su32(sGt), 16, 1024);       // MMA2 B: K-major L x rows
+  const uint64_t dR = sdesc(su32(sRing), 16, 1024);      // MMA1 B: ring stage 0
+
+  // prefetch the first tile of this cluster into L2
+  if (warp == MMA_WARP && cid < a.ntiles && a.vec_ok && pf_bytes) {
+    const TcSeg& sg = a.seg[find_seg(a, cid)];
+    const int64_t row0 = (static_cast<int64_t>(cid) - sg.tile0) * TC_ROWS;
+    for (int rr = lane; rr < TC_ROWS; rr += 32) {
+      if (row0 + rr < sg.m) prefetch_l2(sg.rows + (row0 + rr) * sg.ld + f0, pf_bytes);
+    }
+  }
 
   for (int64_t tile = cid; tile < a.ntiles; tile += ncl, ++iter) {
-    // locate the segment of this tile
-    int sgi = 0;
-    while (sgi + 1 < a.nseg && a.seg[sgi + 1].tile0 <= tile) ++sgi;
-    const TcSeg sg = a.seg[sgi];
+    const TcSeg sg = a.seg[find_seg(a, tile)];
     const int64_t row0 = (tile - sg.tile0) * TC_ROWS;
-
     TC_TRACE(0);
-    // (a) Omega prefetch for the first stages
-    auto issue = [&](int c) {
-      const int s = c % OM_STAGES;
-      if (fills[s] > 0 && !dead) {
-        if (!mbar_wait(su32(&empty[s]), (fills[s] - 1) & 1u)) dead = true;
-      }
-      mbar_expect_tx(su32(&full[s]), chunk_bytes);
-      bulk_g2s(su32(sRing + s * chunk_bytes), a.om16 + (g0 + c) * static_cast<int64_t>(L) * 64, chunk_bytes,
-               su32(&full[s]));
-      ++fills[s];
-    };
-    if (tid == 0) {
-      // the ring held the previous tile's exchange rows (generic proxy writes)
-      fence_async_cta();
-      for (int c = 0; c < nchunk && c < OM_STAGES; ++c) issue(c);
-    }
 
-    // (b) load, shift, round to BF16, store swizzled; column sums of the stored values
-    if (loader) {
-      const int64_t fbase = f0 + cc * 8;
-      const float* shv = sShift + cc * 8;
-      const int fb = (cc * 8) / 64;
-      const uint32_t colbyte = static_cast<uint32_t>((cc * 8) % 64) * 2u;
-      float csl[8];
+    if (warp < MMA_WARP) {
+      // ------------------------------------------------ loaders: A slice -> BF16 swizzled tile
+      // a 64-feature block is 128 rows x 8 chunks of 8 features; loader thread t takes the
+      // (row, chunk) items t, t + TC_LOADERS, t + 2 TC_LOADERS (< 1024)
+      auto gload = [&](int fb, float4 (&v)[LOAD_ITEMS][2]) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) csl[i] = 0.f;
-      for (int r = rp; r < TC_ROWS; r += RP * 4) {
-        float4 v[4][2];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int rr = r + u * RP;
+        for (int u = 0; u < LOAD_ITEMS; ++u) {
+          const int item = tid + TC_LOADERS * u;
+          const int rr = item >> 3, cc = item & 7;
+          const int64_t fbase = f0 + fb * 64 + cc * 8;
           const int64_t grow = row0 + rr;
           v[u][0] = make_float4(0.f, 0.f, 0.f, 0.f);
           v[u][1] = v[u][0];
-          if (rr < TC_ROWS && grow < sg.m) {
+          if (item < TC_ROWS * 8 && grow < sg.m) {
             const float* src = sg.rows + grow * sg.ld + fbase;
             if (a.vec_ok && fbase + 7 < n) {
               v[u][0] = __ldg(reinterpret_cast<const float4*>(src));
@@ -359,62 +371,96 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
             }
           }
         }
+      };
+      auto convert = [&](int fb, const float4 (&v)[LOAD_ITEMS][2]) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int rr = r + u * RP;
-          if (rr >= TC_ROWS) continue;
-          const int64_t grow = row0 + rr;
-          const bool valid = grow < sg.m;
-          float x[8] = {v[u][0].x, v[u][0].y, v[u][0].z, v[u][0].w, v[u][1].x, v[u][1].y, v[u][1].z, v[u][1].w};
+        for (int u = 0; u < LOAD_ITEMS; ++u) {
+          const int item = tid + TC_LOADERS * u;
+          if (item >= TC_ROWS * 8) continue;
+          const int rr = item >> 3, cc = item & 7;
+          const float* shv = sShift + fb * 64 + cc * 8;
+          const int64_t fbase = f0 + fb * 64 + cc * 8;
+          const bool valid = row0 + rr < sg.m;
+          const float x[8] = {v[u][0].x, v[u][0].y, v[u][0].z, v[u][0].w, v[u][1].x, v[u][1].y, v[u][1].z, v[u][1].w};
           uint32_t pk[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            float lo = valid && (fbase + 2 * q < n) ? x[2 * q] - shv[2 * q] : 0.f;
-            float hi = valid && (fbase + 2 * q + 1 < n) ? x[2 * q + 1] - shv[2 * q + 1] : 0.f;
+            const float lo = valid && (fbase + 2 * q < n) ? x[2 * q] - shv[2 * q] : 0.f;
+            const float hi = valid && (fbase + 2 * q + 1 < n) ? x[2 * q + 1] - shv[2 * q + 1] : 0.f;
             pk[q] = pack_bf16(lo, hi);
-            csl[2 * q] += __uint_as_float(pk[q] << 16);
-            csl[2 * q + 1] += __uint_as_float(pk[q] & 0xFFFF0000u);
           }
           const uint32_t off = static_cast<uint32_t>(fb) * 16384u + static_cast<uint32_t>(rr >> 3) * 1024u +
-                               sw128(static_cast<uint32_t>(rr & 7), colbyte);
+                               sw128(static_cast<uint32_t>(rr & 7), static_cast<uint32_t>(cc) * 16u);
           *reinterpret_cast<uint4*>(sA + off) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
-      }
-#pragma unroll
-      for (int i = 0; i < 8; ++i) cs_acc[i] += static_cast<double>(csl[i]);
-    }
-    fence_async_cta();
-    __syncthreads();
-
-    TC_TRACE(1);
-    // (c) MMA1 over the feature chunks, Omega streamed through the ring
-    if (tid == 0) {
-      tc_fence_after();
-      for (int c = 0; c < nchunk; ++c) {
-        const int s = c % OM_STAGES;
-        if (!dead && !mbar_wait(su32(&full[s]), cons[s] & 1u)) dead = true;
-        ++cons[s];
-        if (!dead) {
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t aaddr = su32(sA) + static_cast<uint32_t>(c) * 16384u + kk * 32u;
-            const uint32_t baddr = su32(sRing + s * chunk_bytes) + kk * 32u;
-            mma_bf16(tD1, sdesc(aaddr, 16, 1024), sdesc(baddr, 16, 1024), id1, (c | kk) != 0 ? 1u : 0u);
-          }
+        fence_async_cta();
+        mbar_arrive(su32(&ablk[fb]));
+      };
+      // two register batches in flight: block fb+1 loads while block fb converts
+      float4 bufA[LOAD_ITEMS][2], bufB[LOAD_ITEMS][2];
+      gload(0, bufA);
+      for (int fb = 0; fb < nchunk; fb += 2) {
+        if (fb + 1 < nchunk) gload(fb + 1, bufB);
+        convert(fb, bufA);
+        if (fb + 1 < nchunk) {
+          if (fb + 2 < nchunk) gload(fb + 2, bufA);
+          convert(fb + 1, bufB);
         }
-        mma_commit(su32(&empty[s]));
-        // refill the stage consumed one chunk earlier: its MMAs precede the ones just
-        // queued, so waiting for them keeps the tensor pipe busy
-        if (c >= 1 && c - 1 + OM_STAGES < nchunk) issue(c - 1 + OM_STAGES);
       }
-      mma_commit(su32(mma1_done));
+    } else {
+      // ------------------------------------------------ MMA warp: MMA1 as feature blocks arrive
+      if (lane == 0) {
+        auto issue = [&](int c) {
+          const int s = c % OM_STAGES;
+          if (fills[s] > 0 && !dead) {
+            if (!mbar_wait(su32(&empty[s]), (fills[s] - 1) & 1u)) dead = true;
+          }
+          mbar_expect_tx(su32(&full[s]), chunk_bytes);
+          bulk_g2s(su32(sRing + s * chunk_bytes), a.om16 + (g0 + c) * static_cast<int64_t>(L) * 64, chunk_bytes,
+                   su32(&full[s]));
+          ++fills[s];
+        };
+        fence_async_cta();   // the ring held the previous tile's exchange rows (generic writes)
+        for (int c = 0; c < nchunk && c < OM_STAGES; ++c) issue(c);
+        tc_fence_after();
+        for (int c = 0; c < nchunk; ++c) {
+          const int s = c % OM_STAGES;
+          if (!dead && !mbar_wait(su32(&ablk[c]), iter & 1u)) dead = true;
+          if (!dead && !mbar_wait(su32(&full[s]), cons[s] & 1u)) dead = true;
+          ++cons[s];
+          if (!dead) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ad = dA1 + ((static_cast<uint32_t>(c) * 16384u + kk * 32u) >> 4);
+              const uint64_t bd = dR + ((static_cast<uint32_t>(s) * chunk_bytes + kk * 32u) >> 4);
+              mma_bf16(tD1, ad, bd, id1, (c | kk) != 0 ? 1u : 0u);
+            }
+          }
+          mma_commit(su32(&empty[s]));
+          // refill the stage consumed one chunk earlier: its MMAs precede the ones just queued
+          if (c >= 1 && c - 1 + OM_STAGES < nchunk) issue(c - 1 + OM_STAGES);
+        }
+        mma_commit(su32(mma1_done));
+      }
+      __syncwarp();
+      // prefetch the next tile of this cluster into L2 while this one computes
+      const int64_t nt = tile + ncl;
+      if (nt < a.ntiles && a.vec_ok && pf_bytes) {
+        const TcSeg& sn = a.seg[find_seg(a, nt)];
+        const int64_t r0n = (nt - sn.tile0) * TC_ROWS;
+        for (int rr = lane; rr < TC_ROWS; rr += 32) {
+          if (r0n + rr < sn.m) prefetch_l2(sn.rows + (r0n + rr) * sn.ld + f0, pf_bytes);
+        }
+      }
     }
-    // (d) D1 -> exchange buffer (rows x L, FP32)
-    TC_TRACE(2);
+    TC_TRACE(1);
+
+    // ------------------------------------------------ D1 -> exchange buffer (rows x L, FP32)
     if (!dead && !mbar_wait(su32(mma1_done), iter & 1u)) dead = true;
-    TC_TRACE(3);
+    __syncwarp();
     tc_fence_after();
-    {
+    TC_TRACE(2);
+    if (warp < 8) {
       const int q = warp & 3, half = warp >> 2;
       const int row = q * 32 + lane;
       const int cbeg = half * (L / 2), cend = cbeg + L / 2;
@@ -427,20 +473,19 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
       }
     }
     tc_fence_before();
-    TC_TRACE(4);
+    TC_TRACE(3);
     cluster_sync();   // #1: all partials of the tile are in place
-    TC_TRACE(5);
+    TC_TRACE(4);
 
-    // (e) reduce own rows over the cluster (fixed peer order), round to BF16
+    // ------------------------------------------------ reduce own rows over the cluster
     const int r0 = static_cast<int>(rank) * RPC;
     for (int it = tid; it < RPC * (L / 4); it += TC_NT) {
       const int rr = it / (L / 4), c4 = it % (L / 4);
       const uint32_t laddr = su32(sX + (r0 + rr) * xld + c4 * 4);
-      // issue every peer load before the first add (one round trip), then sum in peer order
-      float4 v[16];
+      float4 v[16];   // every peer load in flight before the first add, then sum in peer order
 #pragma unroll
       for (int p = 0; p < 16; ++p) {
-        if (p < CS) v[p] = ld_dsmem_v4(mapa(laddr, static_cast<uint32_t>(p)));
+        if (p < CS) v[p] = ld_dsmem_v4f(mapa(laddr, static_cast<uint32_t>(p)));
       }
       float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -449,38 +494,38 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
           acc.x += v[p].x; acc.y += v[p].y; acc.z += v[p].z; acc.w += v[p].w;
         }
       }
-      float* y = sY + rr * L + c4 * 4;
-      y[0] = bf16_round(acc.x); y[1] = bf16_round(acc.y); y[2] = bf16_round(acc.z); y[3] = bf16_round(acc.w);
       if (!(isfinite(acc.x) && isfinite(acc.y) && isfinite(acc.z) && isfinite(acc.w))) atomicOr(a.flags, 1);
+      float y[4] = {bf16_round(acc.x), bf16_round(acc.y), bf16_round(acc.z), bf16_round(acc.w)};
+      const int cl = l - c4 * 4;
+      if (cl >= 0 && cl < 4) y[cl] = (row0 + r0 + rr < sg.m) ? 1.f : 0.f;   // ones column -> column sums
+      float* dst = sY + rr * L + c4 * 4;
+      dst[0] = y[0]; dst[1] = y[1]; dst[2] = y[2]; dst[3] = y[3];
     }
     __syncthreads();
-    TC_TRACE(6);
-    // (f) pack 8 rows of one G^T row into 16 bytes and store them into every CTA's G^T
-    for (int it = tid; it < L * (RPC / 8); it += TC_NT) {
-      const int lc = it % L, g8 = it / L;
-      const int rr0 = g8 * 8;
+    TC_TRACE(5);
+    // publish the own rows packed as G^T chunks: 8 rows of one column in 16 bytes
+    for (int it = tid; it < L * G8; it += TC_NT) {
+      const int lc = it / G8, g = it % G8;
+      const float* y = sY + (g * 8) * L + lc;
       uint4 pk;
-      pk.x = pack_bf16(sY[(rr0 + 0) * L + lc], sY[(rr0 + 1) * L + lc]);
-      pk.y = pack_bf16(sY[(rr0 + 2) * L + lc], sY[(rr0 + 3) * L + lc]);
-      pk.z = pack_bf16(sY[(rr0 + 4) * L + lc], sY[(rr0 + 5) * L + lc]);
-      pk.w = pack_bf16(sY[(rr0 + 6) * L + lc], sY[(rr0 + 7) * L + lc]);
-      const int r = r0 + rr0;
-      const uint32_t off = static_cast<uint32_t>(r >> 6) * (static_cast<uint32_t>(L) * 128u) +
-                           static_cast<uint32_t>(lc >> 3) * 1024u +
-                           sw128(static_cast<uint32_t>(lc & 7), static_cast<uint32_t>(r & 63) * 2u);
-      const uint32_t laddr = su32(sGt + off);
-      for (int p = 0; p < CS; ++p) st_dsmem_v4(mapa(laddr, static_cast<uint32_t>(p)), pk);
+      pk.x = pack_bf16(y[0 * L], y[1 * L]);
+      pk.y = pack_bf16(y[2 * L], y[3 * L]);
+      pk.z = pack_bf16(y[4 * L], y[5 * L]);
+      pk.w = pack_bf16(y[6 * L], y[7 * L]);
+      sYt[lc * G8 + g] = pk;
     }
-    fence_async_cluster();
-    // (g) Gram, sums of G and the optional G output from the local rows
+    // Gram, sums of G and the optional G output from the own rows
     {
-      const int LL = L * L;
+      const int LT = L * (L + 1) / 2;   // lower triangle, row by row
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < GRAM_PER_THREAD; ++i) {
         const int e = tid + TC_NT * i;
-        if (e < LL) {
-          const int c1 = e / L, c2 = e % L;
-          float acc = 0.f;
+        if (e < LT) {
+          int c1 = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) - 1.f) * 0.5f);
+          while (c1 * (c1 + 1) / 2 > e) --c1;
+          while ((c1 + 1) * (c1 + 2) / 2 <= e) ++c1;
+          const int c2 = e - c1 * (c1 + 1) / 2;
+          float acc = 0.f;   // products of BF16 values are exact in FP32
           for (int rr = 0; rr < RPC; ++rr) acc = fmaf(sY[rr * L + c1], sY[rr * L + c2], acc);
           gram_acc[i] += static_cast<double>(acc);
         }
@@ -491,29 +536,40 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
         sg_acc += acc;
       }
       if (sg.gout != nullptr) {
-        for (int it = tid; it < RPC * a.l; it += TC_NT) {
-          const int rr = it / a.l, c = it % a.l;
+        for (int it = tid; it < RPC * l; it += TC_NT) {
+          const int rr = it / l, c = it % l;
           const int64_t grow = row0 + r0 + rr;
-          if (grow < sg.m) sg.gout[grow * a.l + c] = sY[rr * L + c];
+          if (grow < sg.m) sg.gout[grow * l + c] = sY[rr * L + c];
         }
       }
     }
+    TC_TRACE(6);
+    cluster_sync();   // #2: every CTA's rows are published
     TC_TRACE(7);
-    cluster_sync();   // #2: every G^T tile is complete
+    // pull all 128 rows of G' into the own G^T operand tile (K-major, L x 128 rows)
+    for (int it = tid; it < L * (TC_ROWS / 8); it += TC_NT) {
+      const int lc = it / (TC_ROWS / 8), g = it % (TC_ROWS / 8);
+      const int p = g / G8, gl = g % G8;
+      const uint4 pk = ld_dsmem_v4u(mapa(su32(sYt + lc * G8 + gl), static_cast<uint32_t>(p)));
+      const uint32_t off = static_cast<uint32_t>(g >> 3) * (static_cast<uint32_t>(L) * 128u) +
+                           static_cast<uint32_t>(lc >> 3) * 1024u +
+                           sw128(static_cast<uint32_t>(lc & 7), static_cast<uint32_t>(g & 7) * 16u);
+      *reinterpret_cast<uint4*>(sGt + off) = pk;
+    }
+    fence_async_cta();
+    __syncthreads();
     TC_TRACE(8);
 
-    // (h) MMA2: H += A_hat_slice^T G'
-    if (tid == 0) {
+    // ------------------------------------------------ MMA2: H += A_hat_slice^T G'
+    if (warp == MMA_WARP && lane == 0) {
       tc_fence_after();
       if (!dead) {
         for (int mt = 0; mt < w / 128; ++mt) {
 #pragma unroll
           for (int ks = 0; ks < TC_ROWS / 16; ++ks) {
-            const uint32_t aaddr = su32(sA) + static_cast<uint32_t>(2 * mt) * 16384u + static_cast<uint32_t>(ks) * 2048u;
-            const uint32_t baddr = su32(sGt) + static_cast<uint32_t>(ks >> 2) * (static_cast<uint32_t>(L) * 128u) +
-                                   static_cast<uint32_t>(ks & 3) * 32u;
-            const uint32_t acc = (any_tile || ks > 0) ? 1u : 0u;
-            mma_bf16(tH + static_cast<uint32_t>(mt * L), sdesc(aaddr, 16384, 1024), sdesc(baddr, 16, 1024), id2, acc);
+            const uint64_t ad = dA2 + ((static_cast<uint32_t>(2 * mt) * 16384u + static_cast<uint32_t>(ks) * 2048u) >> 4);
+            const uint64_t bd = dB2 + ((static_cast<uint32_t>(ks >> 2) * chunk_bytes + static_cast<uint32_t>(ks & 3) * 32u) >> 4);
+            mma_bf16(tH + static_cast<uint32_t>(mt * L), ad, bd, id2, (any_tile || ks > 0) ? 1u : 0u);
           }
         }
       }
@@ -521,8 +577,9 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
     }
     any_tile = true;
     if (!dead && !mbar_wait(su32(mma2_done), iter & 1u)) dead = true;
-    TC_TRACE(9);
+    __syncwarp();
     tc_fence_after();
+    TC_TRACE(9);
   }
 
   // ---------------------------------------------------------------- epilogue
@@ -533,8 +590,7 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
   __syncthreads();
   const int64_t npad = static_cast<int64_t>(CS) * w;
   const int64_t cta = static_cast<int64_t>(cid) * CS + rank;
-  // H slice: TMEM lanes = features of each 128-feature tile
-  {
+  if (warp < 8) {   // H slice: TMEM lanes = features of each 128-feature tile
     const int q = warp & 3, half = warp >> 2;
     for (int mt = 0; mt < w / 128; ++mt) {
       const int64_t feat = f0 + mt * 128 + q * 32 + lane;
@@ -552,24 +608,19 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
       }
     }
   }
-  // column sums: combine the row phases in order through shared memory (sA is free now)
-  double* stage = reinterpret_cast<double*>(sA);
-  if (loader) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) stage[rp * w + cc * 8 + i] = cs_acc[i];
-  }
-  __syncthreads();
-  for (int f = tid; f < w; f += TC_NT) {
-    double s = 0.0;
-    for (int p = 0; p < RP; ++p) s += stage[p * w + f];
-    a.cs_part[static_cast<int64_t>(cid) * npad + f0 + f] = s;
-  }
   {
-    const int LL = L * L;
+    const int LL = L * L, LT = L * (L + 1) / 2;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < GRAM_PER_THREAD; ++i) {
       const int e = tid + TC_NT * i;
-      if (e < LL) a.gram_part[cta * LL + e] = gram_acc[i];
+      if (e < LT) {
+        int c1 = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) - 1.f) * 0.5f);
+        while (c1 * (c1 + 1) / 2 > e) --c1;
+        while ((c1 + 1) * (c1 + 2) / 2 <= e) ++c1;
+        const int c2 = e - c1 * (c1 + 1) / 2;
+        a.gram_part[cta * LL + c1 * L + c2] = gram_acc[i];
+        a.gram_part[cta * LL + c2 * L + c1] = gram_acc[i];
+      }
     }
     if (tid < L) a.sG_part[cta * L + tid] = sg_acc;
   }
@@ -582,20 +633,18 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
   cluster_sync();
 }
 
-// H (FP64) += sum over clusters of the FP32 partial slices; colsum likewise.
-__global__ void tc_finish_kernel(const float* __restrict__ Hpart, const double* __restrict__ cs_part, int ncl,
-                                 int64_t n, int64_t npad, int L, double* __restrict__ H, double* __restrict__ colsum) {
+// H (FP64) += sum over clusters of the FP32 partial slices; column l of the partials
+// holds the column sums of A_hat.
+__global__ void tc_finish_kernel(const float* __restrict__ Hpart, int ncl, int64_t n, int64_t npad, int l, int L,
+                                 double* __restrict__ H, double* __restrict__ colsum) {
   const int64_t total = n * L;
   for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
        idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     double acc = 0.0;
     for (int c = 0; c < ncl; ++c) acc += static_cast<double>(Hpart[static_cast<int64_t>(c) * npad * L + idx]);
-    H[idx] += acc;
-    if (idx < n) {
-      double s = 0.0;
-      for (int c = 0; c < ncl; ++c) s += cs_part[static_cast<int64_t>(c) * npad + idx];
-      colsum[idx] += s;
-    }
+    const int col = static_cast<int>(idx % L);
+    if (col < l) H[idx] += acc;
+    else if (col == l) colsum[idx / L] += acc;
   }
 }
 
@@ -633,23 +682,36 @@ int grid_for(int64_t total, int threads) {
   return static_cast<int>(b < 1 ? 1 : b);
 }
 
+thread_local char g_tc_reason[192] = "";
+
 }  // namespace
 
+const char* tc_config_reason() { return g_tc_reason; }
+
 bool tc_config(int64_t n, int L, TcConfig* cfg) {
-  if (L > 64 || L % 16 != 0) return false;
+  snprintf(g_tc_reason, sizeof(g_tc_reason), "no cluster size fits");
+  if (L % 16 != 0 || L * (L + 1) / 2 > GRAM_PER_THREAD * TC_NT) {
+    snprintf(g_tc_reason, sizeof(g_tc_reason), "padded l = %d exceeds the Gram registers", L);
+    return false;
+  }
   for (int CS : {4, 8, 16}) {
     const int64_t w = ((n + CS - 1) / CS + 127) / 128 * 128;
-    if (w > 640) continue;
+    if (w > 64 * MAX_CHUNKS) continue;
     if ((1 + w / 128) * L > static_cast<int64_t>(TMEM_COLS)) continue;
     const TcLayout lay = tc_layout(L, static_cast<int>(w), CS);
     if (lay.total > 227u * 1024u) continue;
     cfg->CS = CS;
     cfg->w = static_cast<int>(w);
     cfg->smem = lay.total;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(lay.total));
-    cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e1 = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(lay.total));
+    cudaError_t e2 = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      snprintf(g_tc_reason, sizeof(g_tc_reason), "cluster %d: attributes: %s / %s", CS, cudaGetErrorString(e1),
+               cudaGetErrorString(e2));
+      cudaGetLastError();
+      continue;
+    }
     cudaLaunchConfig_t lc = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -662,7 +724,17 @@ bool tc_config(int64_t n, int L, TcConfig* cfg) {
     lc.attrs = at;
     lc.numAttrs = 1;
     int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, sketch_tc_kernel, &lc) != cudaSuccess || ncl < 1) {
+    const cudaError_t e3 = cudaOccupancyMaxActiveClusters(&ncl, sketch_tc_kernel, &lc);
+    if (e3 != cudaSuccess || ncl < 1) {
+      cudaFuncAttributes fa{};
+      cudaFuncGetAttributes(&fa, sketch_tc_kernel);
+      int nb = -1;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sketch_tc_kernel, TC_NT, lay.total);
+      snprintf(g_tc_reason, sizeof(g_tc_reason),
+               "cluster %d, w %lld, smem %u: occupancy %s, %d clusters (regs %d, max threads %d, static smem %zu, "
+               "blocks/SM %d)",
+               CS, (long long)w, lay.total, cudaGetErrorString(e3), ncl, fa.numRegs, fa.maxThreadsPerBlock,
+               fa.sharedSizeBytes, nb);
       cudaGetLastError();
       continue;
     }
@@ -706,7 +778,6 @@ cudaError_t tc_pass(const State& s, const TcWork& w, const TcPending& pend, cuda
   args.shift = s.shift;
   args.om16 = w.om16;
   args.Hpart = w.Hpart;
-  args.cs_part = w.cs_part;
   args.gram_part = w.gram_part;
   args.sG_part = w.sG_part;
   args.flags = s.flags;
@@ -749,8 +820,8 @@ cudaError_t tc_pass(const State& s, const TcWork& w, const TcPending& pend, cuda
 #endif
   const int64_t npad = static_cast<int64_t>(w.cfg.CS) * w.cfg.w;
   prof->begin(SPCA_K_H_FINISH, st);
-  tc_finish_kernel<<<grid_for(s.n * s.L, 256), 256, 0, st>>>(w.Hpart, w.cs_part, w.cfg.nclusters, s.n, npad, s.L,
-                                                             s.H, s.colsum);
+  tc_finish_kernel<<<grid_for(s.n * s.L, 256), 256, 0, st>>>(w.Hpart, w.cfg.nclusters, s.n, npad, s.l, s.L, s.H,
+                                                             s.colsum);
   prof->end(SPCA_K_H_FINISH, st);
   prof->begin(SPCA_K_GRAM_ACCUM, st);
   e = launch_gram_accum(w.gram_part, w.sG_part, w.cfg.nclusters * w.cfg.CS, s.L, s.gram, s.sG, st);

@@ -161,7 +161,7 @@ void free_all(spca_session* s) {
                   s->simt.gram_part, s->simt.sG_part, s->simt.Hpart, s->simt.cs_part, s->shift_part, s->fin.Hbar,
                   s->fin.gbar, s->fin.T, s->fin.X, s->fin.W, s->fin.lam, s->fin.Bt, s->fin.Cpart, s->fin.C,
                   s->fin.sig, s->fin.info, s->fin_sigma, s->fin_V, s->dstage[0], s->dstage[1],
-                  s->tcw.om16, s->tcw.Hpart, s->tcw.cs_part, s->tcw.gram_part, s->tcw.sG_part};
+                  s->tcw.om16, s->tcw.Hpart, s->tcw.gram_part, s->tcw.sG_part};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < 2; ++i) {
@@ -250,14 +250,17 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   if (o.math != SPCA_MATH_FP32 && o.math != SPCA_MATH_BF16)
     return fail(nullptr, SPCA_E_UNSUPPORTED, "math form %d is not available in this build", o.math);
   TcConfig tcfg{};
-  if (o.math == SPCA_MATH_BF16 && !tc_config(n, pad_l(static_cast<int>(l)), &tcfg))
+  // the tensor-core pass keeps one spare column (index l) for the column sums
+  const int L_tc = pad_l(static_cast<int>(l) + 1);
+  if (o.math == SPCA_MATH_BF16 && !tc_config(n, L_tc, &tcfg))
     return fail(nullptr, SPCA_E_UNSUPPORTED,
-                "the tensor-core pass needs l <= 64 and n <= 16 x 640 on a device with 16-CTA clusters "
-                "(n=%lld, l=%lld)", (long long)n, (long long)l);
+                "the tensor-core pass needs l <= 63 and n <= 16 x 640 on a device with 16-CTA clusters "
+                "(n=%lld, l=%lld): %s", (long long)n, (long long)l, tc_config_reason());
 
   s = new (std::nothrow) spca_session();
   if (!s) return fail(nullptr, SPCA_E_NOMEM, "host allocation failed");
-  s->n = n; s->k = k; s->p = p; s->l = static_cast<int>(l); s->L = pad_l(static_cast<int>(l)); s->seed = seed;
+  s->n = n; s->k = k; s->p = p; s->l = static_cast<int>(l); s->seed = seed;
+  s->L = (o.math == SPCA_MATH_BF16) ? L_tc : pad_l(static_cast<int>(l));
   s->opt = o;
   const int64_t mb = o.max_block_rows > 0 ? o.max_block_rows : kDefaultBlockRows;
   const int L = s->L;
@@ -314,7 +317,6 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
     const int64_t nctas = static_cast<int64_t>(tcfg.nclusters) * tcfg.CS;
     CC(dalloc(&t.om16, size_t(npad) * L));
     CC(dalloc(&t.Hpart, size_t(tcfg.nclusters) * npad * L));
-    CC(dalloc(&t.cs_part, size_t(tcfg.nclusters) * npad));
     CC(dalloc(&t.gram_part, size_t(nctas) * L * L));
     CC(dalloc(&t.sG_part, size_t(nctas) * L));
   }

@@ -89,8 +89,7 @@ struct TcConfig {
 struct TcWork {
   TcConfig cfg;
   __nv_bfloat16* om16;   // Omega, BF16, pre-swizzled 64-feature chunks (CS*w/64 chunks x L x 64)
-  float* Hpart;          // nclusters x (CS*w) x L
-  double* cs_part;       // nclusters x (CS*w)
+  float* Hpart;          // nclusters x (CS*w) x L; column l carries the column sums
   double* gram_part;     // nclusters*CS x L x L
   double* sG_part;       // nclusters*CS x L
 };
@@ -109,6 +108,7 @@ struct TcPending {
 
 // Whether (n, L) fits the fused kernel; fills the launch configuration.
 bool tc_config(int64_t n, int L, TcConfig* cfg);
+const char* tc_config_reason();   // why the last tc_config call said no
 cudaError_t launch_omega_bf16(uint64_t seed, int64_t n, int64_t npad, int l, int L, __nv_bfloat16* out,
                               cudaStream_t st, Prof* prof);
 cudaError_t tc_pass(const State& s, const TcWork& w, const TcPending& pend, cudaStream_t st, Prof* prof);
