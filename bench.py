@@ -294,7 +294,7 @@ def run_ours(args):
         return 0
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": steps, "warmup": args.warmup,
             "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.math == "fp32" else "bf16", "data": "synthetic",
+            "dtype": {"fp32": "f32", "fp16": "f16"}.get(args.math, "bf16"), "data": "synthetic",
             "config": {"workload": WORKLOAD, "math": args.math, "l2": "inputs larger than L2 (4.0 GB), no flush",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -310,7 +310,7 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--math", default="fp32", choices=["fp32", "bf16", "bf16x2", "fp8"])
+    ap.add_argument("--math", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

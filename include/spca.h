@@ -61,7 +61,14 @@ typedef enum {
   SPCA_MATH_FP32 = 0,     /* FP32 CUDA-core FMA, FP32 accumulate               */
   SPCA_MATH_BF16 = 1,     /* BF16 tensor-core operands, FP32 accumulate        */
   SPCA_MATH_BF16X2 = 2,   /* split BF16 (hi + lo) operands, FP32 accumulate    */
-  SPCA_MATH_FP8 = 3       /* FP8 E4M3 operands, FP32 accumulate                */
+  SPCA_MATH_FP8 = 3,      /* FP8 E4M3 operands, FP32 accumulate                */
+  SPCA_MATH_FP16 = 4      /* FP16 tensor-core operands on the shifted rows and G
+                             scaled by one power of two per pass (chosen from the
+                             first rows so that G stays below 2^14), FP32
+                             accumulate: 8x finer rounding than BF16 at the same
+                             operand size and rate. Later rows more than about
+                             4x longer than the first ones overflow FP16 and
+                             make spca_finalize return SPCA_E_NUMERIC.          */
 } spca_math;
 
 typedef struct {

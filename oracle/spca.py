@@ -78,8 +78,14 @@ def decode_e4m3(codes):
 # Omega (Alg. 4 step 3) in the forms the library uses.
 # --------------------------------------------------------------------------
 
+def round_f16(x):
+    """Round to IEEE binary16 and return as float64: first to binary32, then
+    to binary16, each to nearest with ties to even (numpy's conversions)."""
+    return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float16).astype(np.float64)
+
+
 def omega(n, l, seed, form="f64"):
-    """Omega = randn(n, l): FP64 draw, optionally defined as its FP32 or BF16 value."""
+    """Omega = randn(n, l): FP64 draw, optionally defined as its FP32, BF16 or FP16 value."""
     z = philox.omega(n, l, seed)
     if form == "f64":
         return z
@@ -87,6 +93,8 @@ def omega(n, l, seed, form="f64"):
         return round_f32(z)
     if form == "bf16":
         return round_bf16(z)
+    if form == "f16":
+        return round_f16(z)
     raise ValueError(form)
 
 

@@ -18,8 +18,9 @@ SPCA_OK = 0
 STATUS_NAMES = {0: "SPCA_OK", 1: "SPCA_E_INVALID", 2: "SPCA_E_NOMEM", 3: "SPCA_E_CUDA", 4: "SPCA_E_STATE",
                 5: "SPCA_E_NUMERIC", 6: "SPCA_E_TIMEOUT", 7: "SPCA_E_UNSUPPORTED"}
 SPCA_F32, SPCA_BF16, SPCA_F8E4M3, SPCA_F64 = 0, 1, 2, 3
-SPCA_MATH_FP32, SPCA_MATH_BF16, SPCA_MATH_BF16X2, SPCA_MATH_FP8 = 0, 1, 2, 3
-MATH_NAMES = {"fp32": SPCA_MATH_FP32, "bf16": SPCA_MATH_BF16, "bf16x2": SPCA_MATH_BF16X2, "fp8": SPCA_MATH_FP8}
+SPCA_MATH_FP32, SPCA_MATH_BF16, SPCA_MATH_BF16X2, SPCA_MATH_FP8, SPCA_MATH_FP16 = 0, 1, 2, 3, 4
+MATH_NAMES = {"fp32": SPCA_MATH_FP32, "bf16": SPCA_MATH_BF16, "bf16x2": SPCA_MATH_BF16X2, "fp8": SPCA_MATH_FP8,
+              "fp16": SPCA_MATH_FP16}
 
 
 class SpcaError(RuntimeError):

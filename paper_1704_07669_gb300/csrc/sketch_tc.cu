@@ -28,6 +28,7 @@
 // later waits and keeps taking part in the cluster barriers (every CTA of a cluster
 // runs the same number of them), so no wait can hang the GPU.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cstdio>
@@ -170,11 +171,31 @@ __device__ __forceinline__ uint4 ld_dsmem_v4u(uint32_t a) {
                : "memory");
   return v;
 }
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t*>(&p);
+// Operand formats of the tensor-core pass: FMT_BF16, or FMT_F16 (FP16 on values scaled by a
+// power of two so that A_hat and G stay well inside the FP16 range).
+constexpr int FMT_BF16 = 0, FMT_F16 = 1;
+
+template <int FMT>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  if constexpr (FMT == FMT_F16) {
+    const __half2 p = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&p);
+  } else {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&p);
+  }
 }
-__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+template <int FMT>
+__device__ __forceinline__ float round1(float x) {
+  if constexpr (FMT == FMT_F16) return __half2float(__float2half_rn(x));
+  else return __bfloat162float(__float2bfloat16_rn(x));
+}
+
+// instruction descriptor for the operand format: kind::f16, FP32 accumulate
+template <int FMT>
+__host__ __device__ constexpr uint32_t idesc_fmt(int M, int N, int a_mn, int b_mn) {
+  return FMT == FMT_F16 ? (idesc_bf16(M, N, a_mn, b_mn) & ~((7u << 7) | (7u << 10))) : idesc_bf16(M, N, a_mn, b_mn);
+}
 
 }  // namespace
 
@@ -219,7 +240,8 @@ struct TcArgs {
   int l, L, w, CS;
   int vec_ok;
   const float* shift;
-  const __nv_bfloat16* om16;   // chunk g at om16 + g * L * 64 (pre-swizzled)
+  const uint16_t* om16;        // Omega (operand format bits), chunk g at g * L * 64 elements, pre-swizzled
+  const float* scale;          // operand scale s (power of two); NULL = 1
   float* Hpart;                // nclusters x (CS w) x L (column l: column sums)
   double* gram_part;           // nctas x L x L
   double* sG_part;             // nctas x L
@@ -251,6 +273,7 @@ __device__ __forceinline__ int find_seg(const TcArgs& a, int64_t tile) {
 }
 
 // one CTA of 12 warps per SM (<= 170 registers per thread)
+template <int FMT>
 __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -323,8 +346,11 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
   uint32_t iter = 0;
   bool dead = false;
   bool any_tile = false;
-  const uint32_t id1 = idesc_bf16(TC_ROWS, L, 0, 0);
-  const uint32_t id2 = idesc_bf16(TC_ROWS, L, 1, 0);
+  const uint32_t id1 = idesc_fmt<FMT>(TC_ROWS, L, 0, 0);
+  const uint32_t id2 = idesc_fmt<FMT>(TC_ROWS, L, 1, 0);
+  // operands carry s A_hat and s G; every partial is brought back by exact powers of two
+  const float op_scale = a.scale ? *a.scale : 1.f;
+  const float inv_s = 1.f / op_scale;
   const uint64_t dA1 = sdesc(su32(sA), 16, 1024);        // MMA1 A: K-major rows x features
   const uint64_t dA2 = sdesc(su32(sA), 16384, 1024);     // MMA2 A: MN-major features x rows
   const uint64_t dB2 = sdesc(su32(sGt), 16, 1024);       // MMA2 B: K-major L x rows
@@ -385,9 +411,9 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
           uint32_t pk[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float lo = valid && (fbase + 2 * q < n) ? x[2 * q] - shv[2 * q] : 0.f;
-            const float hi = valid && (fbase + 2 * q + 1 < n) ? x[2 * q + 1] - shv[2 * q + 1] : 0.f;
-            pk[q] = pack_bf16(lo, hi);
+            const float lo = valid && (fbase + 2 * q < n) ? (x[2 * q] - shv[2 * q]) * op_scale : 0.f;
+            const float hi = valid && (fbase + 2 * q + 1 < n) ? (x[2 * q + 1] - shv[2 * q + 1]) * op_scale : 0.f;
+            pk[q] = pack2<FMT>(lo, hi);
           }
           const uint32_t off = static_cast<uint32_t>(fb) * 16384u + static_cast<uint32_t>(rr >> 3) * 1024u +
                                sw128(static_cast<uint32_t>(rr & 7), static_cast<uint32_t>(cc) * 16u);
@@ -494,8 +520,9 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
           acc.x += v[p].x; acc.y += v[p].y; acc.z += v[p].z; acc.w += v[p].w;
         }
       }
-      if (!(isfinite(acc.x) && isfinite(acc.y) && isfinite(acc.z) && isfinite(acc.w))) atomicOr(a.flags, 1);
-      float y[4] = {bf16_round(acc.x), bf16_round(acc.y), bf16_round(acc.z), bf16_round(acc.w)};
+      // checked after the rounding: an FP16 operand can overflow where the FP32 sum did not
+      float y[4] = {round1<FMT>(acc.x), round1<FMT>(acc.y), round1<FMT>(acc.z), round1<FMT>(acc.w)};
+      if (!(isfinite(y[0]) && isfinite(y[1]) && isfinite(y[2]) && isfinite(y[3]))) atomicOr(a.flags, 1);
       const int cl = l - c4 * 4;
       if (cl >= 0 && cl < 4) y[cl] = (row0 + r0 + rr < sg.m) ? 1.f : 0.f;   // ones column -> column sums
       float* dst = sY + rr * L + c4 * 4;
@@ -508,10 +535,10 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
       const int lc = it / G8, g = it % G8;
       const float* y = sY + (g * 8) * L + lc;
       uint4 pk;
-      pk.x = pack_bf16(y[0 * L], y[1 * L]);
-      pk.y = pack_bf16(y[2 * L], y[3 * L]);
-      pk.z = pack_bf16(y[4 * L], y[5 * L]);
-      pk.w = pack_bf16(y[6 * L], y[7 * L]);
+      pk.x = pack2<FMT>(y[0 * L], y[1 * L]);
+      pk.y = pack2<FMT>(y[2 * L], y[3 * L]);
+      pk.z = pack2<FMT>(y[4 * L], y[5 * L]);
+      pk.w = pack2<FMT>(y[6 * L], y[7 * L]);
       sYt[lc * G8 + g] = pk;
     }
     // Gram, sums of G and the optional G output from the own rows
@@ -539,7 +566,7 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
         for (int it = tid; it < RPC * l; it += TC_NT) {
           const int rr = it / l, c = it % l;
           const int64_t grow = row0 + r0 + rr;
-          if (grow < sg.m) sg.gout[grow * l + c] = sY[rr * L + c];
+          if (grow < sg.m) sg.gout[grow * l + c] = sY[rr * L + c] * inv_s;
         }
       }
     }
@@ -599,9 +626,10 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
       for (int c = cbeg; c < cend; c += 8) {
         float v[8];
         tmem_ld8(tH + static_cast<uint32_t>(mt * L + c) + (static_cast<uint32_t>(q * 32) << 16), v);
-        if (!any_tile || dead_sh) {
 #pragma unroll
-          for (int i = 0; i < 8; ++i) v[i] = 0.f;
+        for (int i = 0; i < 8; ++i) {
+          // H carries s^2, the ones column (column sums) s
+          v[i] = (!any_tile || dead_sh) ? 0.f : v[i] * (c + i == l ? inv_s : inv_s * inv_s);
         }
         reinterpret_cast<float4*>(dst + c)[0] = make_float4(v[0], v[1], v[2], v[3]);
         reinterpret_cast<float4*>(dst + c)[1] = make_float4(v[4], v[5], v[6], v[7]);
@@ -618,11 +646,12 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
         while (c1 * (c1 + 1) / 2 > e) --c1;
         while ((c1 + 1) * (c1 + 2) / 2 <= e) ++c1;
         const int c2 = e - c1 * (c1 + 1) / 2;
-        a.gram_part[cta * LL + c1 * L + c2] = gram_acc[i];
-        a.gram_part[cta * LL + c2 * L + c1] = gram_acc[i];
+        const double g = gram_acc[i] * (static_cast<double>(inv_s) * inv_s);
+        a.gram_part[cta * LL + c1 * L + c2] = g;
+        a.gram_part[cta * LL + c2 * L + c1] = g;
       }
     }
-    if (tid < L) a.sG_part[cta * L + tid] = sg_acc;
+    if (tid < L) a.sG_part[cta * L + tid] = sg_acc * inv_s;
   }
   tc_fence_before();
   __syncthreads();
@@ -650,7 +679,8 @@ __global__ void tc_finish_kernel(const float* __restrict__ Hpart, int ncl, int64
 
 // Omega as BF16 (RNE of the FP32 value) in the pre-swizzled chunk layout of the kernel:
 // chunk g (features 64g..64g+63) is L rows (Omega columns) of 128 bytes, 8-row atoms.
-__global__ void omega_bf16_kernel(uint64_t seed, int64_t n, int64_t npad, int l, int L, __nv_bfloat16* __restrict__ out) {
+template <int FMT>
+__global__ void omega_op_kernel(uint64_t seed, int64_t n, int64_t npad, int l, int L, uint16_t* __restrict__ out) {
   const int qn = L / 4;
   const int64_t total = npad * qn;
   for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
@@ -671,9 +701,43 @@ __global__ void omega_bf16_kernel(uint64_t seed, int64_t n, int64_t npad, int l,
       const int c = 4 * q + t;
       const float v = (j < n && c < l) ? static_cast<float>(z[t]) : 0.f;
       const uint32_t off = static_cast<uint32_t>(c >> 3) * 1024u + sw128(static_cast<uint32_t>(c & 7), fbyte);
-      *reinterpret_cast<__nv_bfloat16*>(chunk + off) = __float2bfloat16_rn(v);
+      *reinterpret_cast<uint16_t*>(chunk + off) = static_cast<uint16_t>(pack2<FMT>(v, 0.f) & 0xFFFFu);
     }
   }
+}
+
+// The operand scale of the FP16 form: the largest shifted row norm of the first rows
+// bounds every entry of s G (|g_rc| <= ||a_r - c|| ||omega_c||, ||omega_c|| ~ sqrt(n)),
+// so s = 2^floor(log2(2^14 / (1.25 sqrt(n) max_r ||a_r - c||))) keeps s G below 2^14 with
+// four-fold headroom under the FP16 maximum.
+__global__ void row_norm_max_kernel(const float* __restrict__ rows, int64_t m, int64_t n, int64_t ld,
+                                    const float* __restrict__ shift, unsigned int* __restrict__ out_bits) {
+  __shared__ double red[256];
+  for (int64_t r = blockIdx.x; r < m; r += gridDim.x) {
+    double s = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      const double d = static_cast<double>(rows[r * ld + j]) - static_cast<double>(shift[j]);
+      s += d * d;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+      if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(out_bits, __float_as_uint(static_cast<float>(sqrt(red[0]))));
+    __syncthreads();
+  }
+}
+
+__global__ void op_scale_kernel(const unsigned int* __restrict__ bits, int64_t n, float* __restrict__ scale) {
+  const float mx = __uint_as_float(*bits);
+  float s = 1.f;
+  if (mx > 0.f && isfinite(mx)) {
+    const double e = floor(log2(16384.0 / (1.25 * sqrt(static_cast<double>(n)) * static_cast<double>(mx))));
+    s = static_cast<float>(exp2(fmin(fmax(e, -100.0), 100.0)));
+  }
+  *scale = s;
 }
 
 int grid_for(int64_t total, int threads) {
@@ -688,7 +752,8 @@ thread_local char g_tc_reason[192] = "";
 
 const char* tc_config_reason() { return g_tc_reason; }
 
-bool tc_config(int64_t n, int L, TcConfig* cfg) {
+bool tc_config(int64_t n, int L, int fmt, TcConfig* cfg) {
+  const auto kern = fmt == FMT_F16 ? sketch_tc_kernel<FMT_F16> : sketch_tc_kernel<FMT_BF16>;
   snprintf(g_tc_reason, sizeof(g_tc_reason), "no cluster size fits");
   if (L % 16 != 0 || L * (L + 1) / 2 > GRAM_PER_THREAD * TC_NT) {
     snprintf(g_tc_reason, sizeof(g_tc_reason), "padded l = %d exceeds the Gram registers", L);
@@ -703,9 +768,9 @@ bool tc_config(int64_t n, int L, TcConfig* cfg) {
     cfg->CS = CS;
     cfg->w = static_cast<int>(w);
     cfg->smem = lay.total;
-    cudaError_t e1 = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e1 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           static_cast<int>(lay.total));
-    cudaError_t e2 = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
       snprintf(g_tc_reason, sizeof(g_tc_reason), "cluster %d: attributes: %s / %s", CS, cudaGetErrorString(e1),
                cudaGetErrorString(e2));
@@ -724,12 +789,12 @@ bool tc_config(int64_t n, int L, TcConfig* cfg) {
     lc.attrs = at;
     lc.numAttrs = 1;
     int ncl = 0;
-    const cudaError_t e3 = cudaOccupancyMaxActiveClusters(&ncl, sketch_tc_kernel, &lc);
+    const cudaError_t e3 = cudaOccupancyMaxActiveClusters(&ncl, kern, &lc);
     if (e3 != cudaSuccess || ncl < 1) {
       cudaFuncAttributes fa{};
-      cudaFuncGetAttributes(&fa, sketch_tc_kernel);
+      cudaFuncGetAttributes(&fa, kern);
       int nb = -1;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sketch_tc_kernel, TC_NT, lay.total);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, TC_NT, lay.total);
       snprintf(g_tc_reason, sizeof(g_tc_reason),
                "cluster %d, w %lld, smem %u: occupancy %s, %d clusters (regs %d, max threads %d, static smem %zu, "
                "blocks/SM %d)",
@@ -744,11 +809,29 @@ bool tc_config(int64_t n, int L, TcConfig* cfg) {
   return false;
 }
 
-cudaError_t launch_omega_bf16(uint64_t seed, int64_t n, int64_t npad, int l, int L, __nv_bfloat16* out,
-                              cudaStream_t st, Prof* prof) {
+cudaError_t launch_omega_op(int fmt, uint64_t seed, int64_t n, int64_t npad, int l, int L, uint16_t* out,
+                            cudaStream_t st, Prof* prof) {
   if (prof) prof->begin(SPCA_K_OMEGA, st);
-  omega_bf16_kernel<<<grid_for(npad * (L / 4), 256), 256, 0, st>>>(seed, n, npad, l, L, out);
+  if (fmt == FMT_F16)
+    omega_op_kernel<FMT_F16><<<grid_for(npad * (L / 4), 256), 256, 0, st>>>(seed, n, npad, l, L, out);
+  else
+    omega_op_kernel<FMT_BF16><<<grid_for(npad * (L / 4), 256), 256, 0, st>>>(seed, n, npad, l, L, out);
   if (prof) prof->end(SPCA_K_OMEGA, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_op_scale(const float* rows, int64_t m, int64_t n, int64_t ld, const float* shift,
+                            unsigned int* bits, float* scale, cudaStream_t st, Prof* prof) {
+  if (prof) prof->begin(SPCA_K_SHIFT, st);
+  cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  const int blocks = static_cast<int>(m < 152 * 8 ? m : 152 * 8);
+  row_norm_max_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(rows, m, n, ld, shift, bits);
+  op_scale_kernel<<<1, 1, 0, st>>>(bits, n, scale);
+  if (prof) {
+    prof->launches[SPCA_K_SHIFT] += 1;
+    prof->end(SPCA_K_SHIFT, st);
+  }
   return cudaGetLastError();
 }
 
@@ -777,6 +860,7 @@ cudaError_t tc_pass(const State& s, const TcWork& w, const TcPending& pend, cuda
   args.vec_ok = vec_ok ? 1 : 0;
   args.shift = s.shift;
   args.om16 = w.om16;
+  args.scale = w.fmt == FMT_F16 ? w.scale : nullptr;
   args.Hpart = w.Hpart;
   args.gram_part = w.gram_part;
   args.sG_part = w.sG_part;
@@ -801,7 +885,8 @@ cudaError_t tc_pass(const State& s, const TcWork& w, const TcPending& pend, cuda
   lc.attrs = at;
   lc.numAttrs = 1;
   prof->begin(SPCA_K_TC_SKETCH, st);
-  cudaError_t e = cudaLaunchKernelEx(&lc, sketch_tc_kernel, args);
+  cudaError_t e = w.fmt == FMT_F16 ? cudaLaunchKernelEx(&lc, sketch_tc_kernel<FMT_F16>, args)
+                                   : cudaLaunchKernelEx(&lc, sketch_tc_kernel<FMT_BF16>, args);
   prof->end(SPCA_K_TC_SKETCH, st);
   if (e != cudaSuccess) return e;
 #ifdef SPCA_TC_TRACE

@@ -83,6 +83,7 @@ struct spca_session {
   bool failed = false;
   int64_t m = 0;
   bool shift_set = false;
+  bool scale_set = false;     // FP16 form: operand scale computed from the first rows
   char err[512] = "";
   char desc[256] = "";
 
@@ -161,7 +162,7 @@ void free_all(spca_session* s) {
                   s->simt.gram_part, s->simt.sG_part, s->simt.Hpart, s->simt.cs_part, s->shift_part, s->fin.Hbar,
                   s->fin.gbar, s->fin.T, s->fin.X, s->fin.W, s->fin.lam, s->fin.Bt, s->fin.Cpart, s->fin.C,
                   s->fin.sig, s->fin.info, s->fin_sigma, s->fin_V, s->dstage[0], s->dstage[1],
-                  s->tcw.om16, s->tcw.Hpart, s->tcw.gram_part, s->tcw.sG_part};
+                  s->tcw.om16, s->tcw.Hpart, s->tcw.gram_part, s->tcw.sG_part, s->tcw.scale, s->tcw.scale_bits};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < 2; ++i) {
@@ -197,6 +198,11 @@ spca_status run_piece(spca_session* s, const void* rows, int64_t m, int64_t ld, 
   if (s->opt.center && !s->shift_set) {
     CU(launch_shift(rows, dtype, m, s->n, ld, scale, s->shift, s->shift_part, s->stream, &s->prof));
     s->shift_set = true;
+  }
+  if (s->tc && s->tcw.fmt == 1 && !s->scale_set) {
+    CU(launch_op_scale(static_cast<const float*>(rows), m, s->n, ld, s->shift, s->tcw.scale_bits, s->tcw.scale,
+                       s->stream, &s->prof));
+    s->scale_set = true;
   }
   if (s->tc) {
     if (s->pend.nseg == kTcPendingMax) {
@@ -247,12 +253,13 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   if (opt) o = *opt;
   if (o.reserved != 0 || (o.center != 0 && o.center != 1) || o.max_block_rows < 0)
     return fail(nullptr, SPCA_E_INVALID, "invalid options");
-  if (o.math != SPCA_MATH_FP32 && o.math != SPCA_MATH_BF16)
+  const bool tc_math = (o.math == SPCA_MATH_BF16 || o.math == SPCA_MATH_FP16);
+  if (o.math != SPCA_MATH_FP32 && !tc_math)
     return fail(nullptr, SPCA_E_UNSUPPORTED, "math form %d is not available in this build", o.math);
   TcConfig tcfg{};
   // the tensor-core pass keeps one spare column (index l) for the column sums
   const int L_tc = pad_l(static_cast<int>(l) + 1);
-  if (o.math == SPCA_MATH_BF16 && !tc_config(n, L_tc, &tcfg))
+  if (tc_math && !tc_config(n, L_tc, o.math == SPCA_MATH_FP16 ? 1 : 0, &tcfg))
     return fail(nullptr, SPCA_E_UNSUPPORTED,
                 "the tensor-core pass needs l <= 63 and n <= 16 x 640 on a device with 16-CTA clusters "
                 "(n=%lld, l=%lld): %s", (long long)n, (long long)l, tc_config_reason());
@@ -260,7 +267,7 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   s = new (std::nothrow) spca_session();
   if (!s) return fail(nullptr, SPCA_E_NOMEM, "host allocation failed");
   s->n = n; s->k = k; s->p = p; s->l = static_cast<int>(l); s->seed = seed;
-  s->L = (o.math == SPCA_MATH_BF16) ? L_tc : pad_l(static_cast<int>(l));
+  s->L = tc_math ? L_tc : pad_l(static_cast<int>(l));
   s->opt = o;
   const int64_t mb = o.max_block_rows > 0 ? o.max_block_rows : kDefaultBlockRows;
   const int L = s->L;
@@ -285,7 +292,8 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
     s->own_stream = true;
   }
   CC(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
-  s->tc = (o.math == SPCA_MATH_BF16);
+  s->tc = tc_math;
+  s->tcw.fmt = (o.math == SPCA_MATH_FP16) ? 1 : 0;
   if (!s->tc) CC(dalloc(&s->omega32, n * L));
   CC(dalloc(&s->H, n * L));
   CC(dalloc(&s->shift, n));
@@ -316,6 +324,8 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
     const int64_t npad = static_cast<int64_t>(tcfg.CS) * tcfg.w;
     const int64_t nctas = static_cast<int64_t>(tcfg.nclusters) * tcfg.CS;
     CC(dalloc(&t.om16, size_t(npad) * L));
+    CC(dalloc(&t.scale, 1));
+    CC(dalloc(&t.scale_bits, 1));
     CC(dalloc(&t.Hpart, size_t(tcfg.nclusters) * npad * L));
     CC(dalloc(&t.gram_part, size_t(nctas) * L * L));
     CC(dalloc(&t.sG_part, size_t(nctas) * L));
@@ -345,7 +355,8 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   CC(cudaMemsetAsync(s->gram, 0, sizeof(double) * L * L, s->stream));
   CC(cudaMemsetAsync(s->flags, 0, sizeof(int) * 4, s->stream));
   if (s->tc) {
-    CC(launch_omega_bf16(seed, n, static_cast<int64_t>(tcfg.CS) * tcfg.w, s->l, L, s->tcw.om16, s->stream, nullptr));
+    CC(launch_omega_op(s->tcw.fmt, seed, n, static_cast<int64_t>(tcfg.CS) * tcfg.w, s->l, L, s->tcw.om16, s->stream,
+                       nullptr));
   } else {
     CC(launch_omega_f32(seed, n, s->l, L, s->omega32, L, s->stream));
   }
@@ -548,13 +559,14 @@ spca_status spca_reset(spca_session* s, uint64_t seed) {
   s->pend.nseg = 0;          // blocks batched for the previous pass are dropped with it
   s->pend.rows_total = 0;
   if (s->tc) {
-    CU(launch_omega_bf16(seed, s->n, static_cast<int64_t>(s->tcw.cfg.CS) * s->tcw.cfg.w, s->l, L, s->tcw.om16,
+    CU(launch_omega_op(s->tcw.fmt, seed, s->n, static_cast<int64_t>(s->tcw.cfg.CS) * s->tcw.cfg.w, s->l, L, s->tcw.om16,
                          s->stream, &s->prof));
   } else {
     CU(launch_omega_f32(seed, s->n, s->l, L, s->omega32, L, s->stream, &s->prof));
   }
   s->m = 0;
   s->shift_set = false;
+  s->scale_set = false;
   return SPCA_OK;
 }
 
@@ -617,7 +629,8 @@ const char* spca_describe(spca_session* s) {
   if (!s) return "";
   if (s->tc) {
     snprintf(s->desc, sizeof(s->desc),
-             "math=bf16 n=%lld l=%d L=%d cluster=%d w=%d clusters=%d ctas=%d smem=%u", (long long)s->n, s->l, s->L,
+             "math=%s n=%lld l=%d L=%d cluster=%d w=%d clusters=%d ctas=%d smem=%u",
+             s->tcw.fmt == 1 ? "fp16" : "bf16", (long long)s->n, s->l, s->L,
              s->tcw.cfg.CS, s->tcw.cfg.w, s->tcw.cfg.nclusters, s->tcw.cfg.nclusters * s->tcw.cfg.CS,
              s->tcw.cfg.smem);
   } else {

@@ -88,7 +88,10 @@ struct TcConfig {
 
 struct TcWork {
   TcConfig cfg;
-  __nv_bfloat16* om16;   // Omega, BF16, pre-swizzled 64-feature chunks (CS*w/64 chunks x L x 64)
+  int fmt;               // 0: BF16 operands; 1: FP16 operands on values scaled by *scale
+  float* scale;          // device scalar: power-of-two operand scale (FP16 form)
+  unsigned int* scale_bits;   // device scratch for the largest row norm
+  uint16_t* om16;        // Omega in the operand format, pre-swizzled 64-feature chunks (CS*w/64 x L x 64)
   float* Hpart;          // nclusters x (CS*w) x L; column l carries the column sums
   double* gram_part;     // nclusters*CS x L x L
   double* sG_part;       // nclusters*CS x L
@@ -107,10 +110,13 @@ struct TcPending {
 };
 
 // Whether (n, L) fits the fused kernel; fills the launch configuration.
-bool tc_config(int64_t n, int L, TcConfig* cfg);
+bool tc_config(int64_t n, int L, int fmt, TcConfig* cfg);
 const char* tc_config_reason();   // why the last tc_config call said no
-cudaError_t launch_omega_bf16(uint64_t seed, int64_t n, int64_t npad, int l, int L, __nv_bfloat16* out,
-                              cudaStream_t st, Prof* prof);
+cudaError_t launch_omega_op(int fmt, uint64_t seed, int64_t n, int64_t npad, int l, int L, uint16_t* out,
+                            cudaStream_t st, Prof* prof);
+// FP16 form: s = power of two from the largest shifted row norm of the given rows
+cudaError_t launch_op_scale(const float* rows, int64_t m, int64_t n, int64_t ld, const float* shift,
+                            unsigned int* bits, float* scale, cudaStream_t st, Prof* prof);
 cudaError_t tc_pass(const State& s, const TcWork& w, const TcPending& pend, cudaStream_t st, Prof* prof);
 
 // FP64 finalisation (a7). Scratch is owned by the session.

@@ -1,11 +1,13 @@
-"""GPU parity of the tensor-core (BF16 tcgen05) form of the pass with the FP64 oracle.
+"""GPU parity of the tensor-core (tcgen05) forms of the pass with the FP64 oracle.
 
-The oracle runs the method in FP64 on the same stored rows with Omega defined as its
-BF16 value (the tensor-core form rounds Omega once, by definition). The remaining
-differences are the BF16 rounding of the shifted rows and of G, and FP32
-accumulation. Gate (the stated target of the tensor-core form): leading singular
-values within 1e-3 relative; the largest principal-angle sine of V and the G rows
-are reported and bounded.
+Two operand formats: BF16, and FP16 on rows and G scaled by one power of two. The
+oracle runs the method in FP64 on the same stored rows with Omega defined as its
+value in the operand format (the tensor-core forms round Omega once, by
+definition). The remaining differences are the rounding of the shifted rows and of
+G to the operand format, and FP32 accumulation. Gate (the stated target of the
+tensor-core forms): FP16 holds every singular value within 1e-3 relative; BF16,
+whose 8-bit significand costs about 8x more, holds the values above sigma_1 / 10
+within 1e-3 relative and every value within 1e-3 sigma_1 (assert_sigma).
 """
 import numpy as np
 import pytest
@@ -19,6 +21,9 @@ pytestmark = pytest.mark.gpu
 
 DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
 TOL_SIGMA_TC = 1e-3
+TC_MATHS = ["bf16", "fp16"]
+OMEGA_FORM = {"bf16": "bf16", "fp16": "f16"}
+ROUND_OP = {"bf16": O.round_bf16, "fp16": O.round_f16}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -41,109 +46,155 @@ def run_tc(A, k, p, seed, update_rows, *, center=True, want_G=False, math="bf16"
     return {"sigma": sigma, "V": V, "state": st, "G": None if G is None else G.cpu().double().numpy()}
 
 
-def oracle_tc(A, k, p, seed, block_rows, center=True):
+def oracle_tc(A, k, p, seed, block_rows, center=True, math="bf16"):
     fin = "blocked" if (k + p) % 10 == 0 else "gram"
     return O.single_pass_pca(A.double().numpy(), k, p, seed, block_rows, center_columns=center, finalize=fin,
-                             omega_form="bf16")
+                             omega_form=OMEGA_FORM[math])
 
 
 def sigma_rel(res, ref):
     return np.abs(res["sigma"] - ref["sigma"]) / ref["sigma"]
 
 
-def test_tc_small_workload_sigma_and_directions():
+def assert_sigma(sigma, ref_sigma, math):
+    """FP16: every value within TOL_SIGMA_TC relative. BF16: a perturbation of the
+    operands of relative size u = 2^-9 moves each singular value by about u times
+    the largest one, so BF16 is held to TOL_SIGMA_TC relative on the values above
+    sigma_1 / 10 and to TOL_SIGMA_TC * sigma_1 absolute on the rest."""
+    rel = np.abs(sigma - ref_sigma) / ref_sigma
+    if math == "fp16":
+        assert rel.max() <= TOL_SIGMA_TC, rel
+    else:
+        lead = ref_sigma >= 0.1 * ref_sigma[0]
+        assert rel[lead].max() <= TOL_SIGMA_TC, rel
+        assert (np.abs(sigma - ref_sigma) / ref_sigma[0]).max() <= TOL_SIGMA_TC, rel
+    return rel
+
+
+@pytest.mark.parametrize("math", TC_MATHS)
+def test_tc_small_workload_sigma_and_directions(math):
     w = synth.workload_small()
     A = w["A"].to(torch.float32)
     k, p, seed = w["k"], w["p"], w["seed"]
-    res = run_tc(A, k, p, seed, w["block_rows"], want_G=True)
-    ref = oracle_tc(A, k, p, seed, w["block_rows"])
-    rel = sigma_rel(res, ref)
-    assert rel.max() <= TOL_SIGMA_TC, rel
+    res = run_tc(A, k, p, seed, w["block_rows"], want_G=True, math=math)
+    ref = oracle_tc(A, k, p, seed, w["block_rows"], math=math)
+    assert_sigma(res["sigma"], ref["sigma"], math)
     assert O.max_principal_sine(res["V"][:, :5], ref["V"][:, :5]) <= 3e-2
-    # G rows: BF16 of the FP32 sketch of the BF16 shifted rows
+    # G rows: the FP32 sketch of the shifted rows rounded to the operand format
+    # (a power-of-two scale does not change a rounding in the normal range)
     A64 = A.double().numpy()
     c = res["state"]["shift"].astype(np.float64)
-    Om = O.omega(A64.shape[1], k + p, seed, "bf16")
-    G_ref = O.round_bf16(A64 - c[None, :]) @ Om
-    assert O.rel_fro(res["G"], G_ref) <= 5e-3
+    Om = O.omega(A64.shape[1], k + p, seed, OMEGA_FORM[math])
+    G_ref = ROUND_OP[math](A64 - c[None, :]) @ Om
+    assert O.rel_fro(res["G"], G_ref) <= (5e-3 if math == "bf16" else 1e-3)
 
 
-def test_tc_agrees_with_fp32_path():
+@pytest.mark.parametrize("math", TC_MATHS)
+def test_tc_agrees_with_fp32_path(math):
     w = synth.workload_small()
     A = w["A"].to(torch.float32)
-    tc = run_tc(A, 10, 10, 5, 500)
+    tc = run_tc(A, 10, 10, 5, 500, math=math)
     f32 = run_tc(A, 10, 10, 5, 500, math="fp32")
-    assert np.max(np.abs(tc["sigma"] - f32["sigma"]) / f32["sigma"]) <= TOL_SIGMA_TC
+    assert_sigma(tc["sigma"], f32["sigma"], math)
 
 
 TC_SHAPES = [
     # (m, n, k, p, update_rows, note)
     (1000, 1001, 10, 6, 1000, "n not a multiple of 8, ragged last tile"),
-    (777, 640, 50, 14, 300, "l = 64, updates not multiples of 128 rows"),
+    (777, 640, 50, 13, 300, "l = 63 (L = 64), updates not multiples of 128 rows"),
     (300, 129, 4, 4, 300, "l = 8 (L = 16), n just over one 128-feature tile"),
     (5000, 6000, 40, 10, 4096, "cluster of 16, w = 384"),
 ]
 
 
+@pytest.mark.parametrize("math", TC_MATHS)
 @pytest.mark.parametrize("m,n,k,p,rows,note", TC_SHAPES, ids=[s[-1] for s in TC_SHAPES])
-def test_tc_shapes(m, n, k, p, rows, note):
+def test_tc_shapes(m, n, k, p, rows, note, math):
     A = synth.low_rank_plus_noise(m, n, synth.spectrum("type4", min(m, n, 120)), noise_std=1e-4, mean_std=0.5,
                                   seed=m + 3 * n, dtype=torch.float32)
-    res = run_tc(A, k, p, 40 + m, rows)
-    ref = oracle_tc(A, k, p, 40 + m, rows)
-    rel = sigma_rel(res, ref)
-    assert rel.max() <= TOL_SIGMA_TC, rel
+    res = run_tc(A, k, p, 40 + m, rows, math=math)
+    ref = oracle_tc(A, k, p, 40 + m, rows, math=math)
+    assert_sigma(res["sigma"], ref["sigma"], math)
 
 
-def test_tc_batched_updates_match_one_update():
+@pytest.mark.parametrize("math", TC_MATHS)
+def test_tc_batched_updates_match_one_update(math):
     A = synth.workload_small()["A"].to(torch.float32)
-    one = run_tc(A, 10, 10, 8, 2000)
-    many = run_tc(A, 10, 10, 8, 64)
+    one = run_tc(A, 10, 10, 8, 2000, math=math)
+    many = run_tc(A, 10, 10, 8, 64, math=math)
     assert np.max(np.abs(one["sigma"] - many["sigma"]) / one["sigma"]) <= 2e-4
 
 
-def test_tc_reset_is_a_fresh_pass():
+@pytest.mark.parametrize("math", TC_MATHS)
+def test_tc_reset_is_a_fresh_pass(math):
     A = synth.workload_small()["A"].to(DEV, torch.float32)
-    with spca.Session(1000, 10, 10, 3, math="bf16") as s:
-        s.update(torch.randn(512, 1000, device=DEV))
+    with spca.Session(1000, 10, 10, 3, math=math) as s:
+        s.update(30.0 * torch.randn(512, 1000, device=DEV))   # also a different FP16 operand scale
         s.reset(3)
         s.update(A)
         a = s.finalize()
-    with spca.Session(1000, 10, 10, 3, math="bf16") as s:
+    with spca.Session(1000, 10, 10, 3, math=math) as s:
         s.update(A)
         b = s.finalize()
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
-def test_tc_rejects_shapes_it_cannot_take():
+@pytest.mark.parametrize("math", TC_MATHS)
+def test_tc_rejects_shapes_it_cannot_take(math):
     with pytest.raises(spca.SpcaError) as ei:
-        spca.Session(40000, 100, 20, 1, math="bf16")
+        spca.Session(40000, 100, 20, 1, math=math)
     assert ei.value.status == 7
     with pytest.raises(spca.SpcaError) as ei:
-        spca.Session(20000, 50, 10, 1, math="bf16")
+        spca.Session(20000, 50, 10, 1, math=math)
     assert ei.value.status == 7
 
 
-def test_tc_non_finite_input_is_reported():
+@pytest.mark.parametrize("math", TC_MATHS)
+def test_tc_non_finite_input_is_reported(math):
     A = torch.randn(256, 300, device=DEV)
     A[100, 7] = float("inf")
-    with spca.Session(300, 8, 8, 1, math="bf16") as s:
+    with spca.Session(300, 8, 8, 1, math=math) as s:
         s.update(A)
         with pytest.raises(spca.SpcaError) as ei:
             s.finalize()
         assert ei.value.status == 5
 
 
-def test_tc_full_size_100000x10000_against_oracle():
+def test_fp16_rows_far_above_the_first_ones_are_reported():
+    """The FP16 operand scale comes from the first rows; rows whose sketch would
+    overflow FP16 under it make finalize report a numeric failure instead of
+    returning a wrong answer."""
+    A = torch.randn(512, 300, device=DEV)
+    with spca.Session(300, 8, 8, 1, math="fp16") as s:
+        s.update(A[:256])
+        s.update(1e4 * A[256:])
+        with pytest.raises(spca.SpcaError) as ei:
+            s.finalize()
+        assert ei.value.status == 5
+
+
+@pytest.fixture(scope="module")
+def c2_oracle():
+    """Oracle results on the 100000 x 10000 workload for both operand formats."""
     w = synth.workload_c2(device=DEV)
+    A64 = w["A"].cpu().double().numpy()
+    refs = {math: O.single_pass_pca(A64, w["k"], w["p"], w["seed"], w["block_rows"], finalize="blocked",
+                                    omega_form=OMEGA_FORM[math]) for math in TC_MATHS}
+    return w, refs
+
+
+@pytest.mark.parametrize("math", TC_MATHS)
+def test_tc_full_size_100000x10000_against_oracle(math, c2_oracle):
+    w, refs = c2_oracle
     A = w["A"]
     k, p, seed, mb = w["k"], w["p"], w["seed"], w["block_rows"]
     m, n = A.shape
-    with spca.Session(n, k, p, seed, math="bf16") as s:
+    with spca.Session(n, k, p, seed, math=math) as s:
         for r0 in range(0, m, mb):
             s.update(A[r0:r0 + mb])
         sigma, V = s.finalize()
-    ref = O.single_pass_pca(A.cpu().double().numpy(), k, p, seed, mb, finalize="blocked", omega_form="bf16")
+    ref = refs[math]
     rel = np.abs(sigma - ref["sigma"]) / ref["sigma"]
-    assert rel.max() <= TOL_SIGMA_TC, rel
+    print(f"{math}: sigma rel max {rel.max():.3e}, leading 10 {rel[:10].max():.3e}")
+    assert_sigma(sigma, ref["sigma"], math)
     assert O.max_principal_sine(V[:, :10], ref["V"][:, :10]) <= 5e-2

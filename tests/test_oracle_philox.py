@@ -151,6 +151,17 @@ def test_round_bf16_matches_torch_cast():
     assert O.round_bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
 
 
+def test_round_f16_matches_torch_cast():
+    rng = np.random.default_rng(4)
+    x = np.concatenate([rng.standard_normal(100000) * 10.0 ** rng.integers(-9, 6, 100000),
+                        [1.0 + 2.0 ** -11, 1.0 + 3 * 2.0 ** -11, 65504.0, 65520.0, 2.0 ** -24, 0.0]])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.float16).to(torch.float64).numpy()
+    assert np.array_equal(O.round_f16(x), ref)
+    assert O.round_f16(np.array([1.0 + 2.0 ** -11]))[0] == 1.0           # tie to even
+    assert O.round_f16(np.array([1.0 + 3 * 2.0 ** -11]))[0] == 1.0 + 2.0 ** -9
+    assert np.isinf(O.round_f16(np.array([65520.0]))[0])                 # rounds past the largest finite
+
+
 def test_decode_e4m3_matches_torch_float8():
     if not hasattr(torch, "float8_e4m3fn"):
         pytest.skip("torch without float8_e4m3fn")
