@@ -237,6 +237,36 @@ spca_status spca_omega_words(uint64_t seed, int64_t n, int32_t l, uint32_t* out)
  */
 spca_status spca_omega(uint64_t seed, int64_t n, int32_t l, float* out);
 
+/*
+ * spca_shift_static - the centering shift c of Sec. 2.1 exactly as a session
+ * computes it from its first rows (FP32 of the FP64 column means of `rows`),
+ * without allocating anything. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory at that moment, such
+ * as a serving loop that has committed its device memory to admitted sessions,
+ * or one that must not call cudaMalloc/cudaFree because those calls
+ * synchronise the whole device and would stall every other session's work.
+ * The 64 partial column sums it needs live in a fixed device array compiled
+ * into the library (64 x SPCA_SHIFT_STATIC_MAX_N doubles, 8 MiB per device).
+ *   rows        device, m x n row-major, leading dimension ld >= n (elements),
+ *               element type dtype (spca_dtype)
+ *   block_scale SPCA_F8E4M3 only: host pointer to the block's FP32 scale
+ *   shift       device, n floats, overwritten
+ *   cuda_stream cudaStream_t to enqueue on (NULL = the legacy default stream);
+ *               the call returns once the two launches are enqueued
+ * Nothing has to start at zero: each partial is written before it is read.
+ * Errors: SPCA_E_INVALID (no CUDA call made) for m < 1, n < 1,
+ * n > SPCA_SHIFT_STATIC_MAX_N, ld < n, a NULL pointer, an unknown dtype or a
+ * missing or non-positive FP8 scale; SPCA_E_CUDA if the address lookup or a
+ * launch fails. The first call on each device looks the array's address up
+ * (cudaGetSymbolAddress with that device current), which may load the
+ * library's device code: make that first call before any stream capture.
+ * All calls on a device share the one array, so calls whose launches can
+ * overlap (other streams, other host threads) race on it: serialise them.
+ */
+#define SPCA_SHIFT_STATIC_MAX_N 16384
+spca_status spca_shift_static(const void* rows, int64_t m, int64_t n, int64_t ld, int32_t dtype,
+                              const float* block_scale, float* shift, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,7 @@ def lib():
             "spca_clear_profile": (i32, [vp]),
             "spca_omega_words": (i32, [u64, i64, i32, vp]),
             "spca_omega": (i32, [u64, i64, i32, vp]),
+            "spca_shift_static": (i32, [vp, i64, i64, i64, i32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -214,6 +215,18 @@ def spca_omega_words(seed, n, l, out):
 
 def spca_omega(seed, n, l, out):
     _check(lib().spca_omega(int(seed) & 0xFFFFFFFFFFFFFFFF, int(n), int(l), _ptr(out)[0]))
+
+
+def spca_shift_static(rows, shift, block_scale=None, stream=None):
+    """The allocation-free shift: shift[:] = FP32 of the FP64 column means of the
+    2-D device tensor ``rows`` (row stride = leading dimension), enqueued on
+    ``stream`` (a torch.cuda.Stream, a raw handle, or None for the default)."""
+    m, n = rows.shape
+    scale = None if block_scale is None else ctypes.c_float(float(block_scale))
+    bs = None if scale is None else ctypes.cast(ctypes.byref(scale), ctypes.c_void_p)
+    st = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(lib().spca_shift_static(_ptr(rows)[0], int(m), int(n), int(rows.stride(0)), _dtype_code(rows), bs,
+                                   _ptr(shift)[0], st))
 
 
 # ---------------------------------------------------------------- convenience wrapper

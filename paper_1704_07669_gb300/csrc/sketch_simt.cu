@@ -17,6 +17,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <mutex>
+
 #include "philox.cuh"
 #include "spca_internal.cuh"
 
@@ -579,6 +581,30 @@ cudaError_t launch_shift(const void* rows, int dtype, int64_t m, int64_t n, int6
     case SPCA_F8E4M3: return shift_t(static_cast<const __nv_fp8_e4m3*>(rows), m, n, ld, scale, shift, part, st, prof);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// Scratch of spca_shift_static: a file-scope device array, so that the entry point needs no
+// allocation. Every partial a call reads is written earlier in the same call, so the array
+// never needs clearing; concurrent calls on one device share it and must be serialised.
+static __device__ __align__(256) double g_shift_scratch[kShiftParts * SPCA_SHIFT_STATIC_MAX_N];
+
+cudaError_t shift_static_scratch(double** out) {
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static double* addr[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_shift_scratch);   // with device `dev` current
+    if (e != cudaSuccess) return e;
+    addr[dev] = static_cast<double*>(p);
+  }
+  *out = addr[dev];
+  return cudaSuccess;
 }
 
 cudaError_t simt_pass(const State& s, const SimtWork& w, const void* rows, int dtype, float scale, int64_t m,

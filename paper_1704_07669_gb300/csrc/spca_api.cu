@@ -648,6 +648,31 @@ spca_status spca_omega_words(uint64_t seed, int64_t n, int32_t l, uint32_t* out)
   return SPCA_OK;
 }
 
+spca_status spca_shift_static(const void* rows, int64_t m, int64_t n, int64_t ld, int32_t dtype,
+                              const float* block_scale, float* shift, void* cuda_stream) {
+  spca_session* s = nullptr;
+  if (!rows || !shift) return fail(nullptr, SPCA_E_INVALID, "spca_shift_static: NULL rows or shift");
+  if (m < 1 || n < 1 || ld < n)
+    return fail(nullptr, SPCA_E_INVALID, "spca_shift_static: need m >= 1, n >= 1, ld >= n (m=%lld n=%lld ld=%lld)",
+                (long long)m, (long long)n, (long long)ld);
+  if (n > SPCA_SHIFT_STATIC_MAX_N)
+    return fail(nullptr, SPCA_E_INVALID,
+                "spca_shift_static: n = %lld exceeds the fixed scratch (n <= %d); use a session instead",
+                (long long)n, SPCA_SHIFT_STATIC_MAX_N);
+  if (dtype_size(dtype) == 0) return fail(nullptr, SPCA_E_INVALID, "spca_shift_static: unknown dtype %d", dtype);
+  float scale = 1.0f;
+  if (dtype == SPCA_F8E4M3) {
+    if (!block_scale) return fail(nullptr, SPCA_E_INVALID, "spca_shift_static: FP8 rows need a block_scale");
+    scale = *block_scale;
+    if (!(scale > 0.0f)) return fail(nullptr, SPCA_E_INVALID, "spca_shift_static: block_scale must be positive");
+  }
+  double* scratch = nullptr;
+  CU(shift_static_scratch(&scratch));
+  Prof quiet;   // counts only: records no events and allocates nothing
+  CU(launch_shift(rows, dtype, m, n, ld, scale, shift, scratch, static_cast<cudaStream_t>(cuda_stream), &quiet));
+  return SPCA_OK;
+}
+
 spca_status spca_omega(uint64_t seed, int64_t n, int32_t l, float* out) {
   spca_session* s = nullptr;
   if (n < 1 || l < 1 || !out) return fail(nullptr, SPCA_E_INVALID, "bad arguments");

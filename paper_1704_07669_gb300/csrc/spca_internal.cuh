@@ -43,6 +43,10 @@ constexpr int kShiftParts = 64;
 cudaError_t launch_shift(const void* rows, int dtype, int64_t m, int64_t n, int64_t ld,
                          float scale, float* shift, double* part, cudaStream_t st, Prof* prof);
 
+// Address of the fixed scratch of spca_shift_static on the current device (kShiftParts x
+// SPCA_SHIFT_STATIC_MAX_N doubles); looked up once per device, then cached.
+cudaError_t shift_static_scratch(double** out);
+
 // FP32 SIMT pass over one piece of rows (a2-a5). Workspace pointers are owned by the session.
 struct SimtWork {
   float* Gpart;       // gp_rows x L (split partials, S x rows_padded)
