@@ -206,19 +206,24 @@ struct TcLayout {
   uint32_t a_bytes, ring_bytes, gt_bytes, shift_bytes, y_bytes, yt_bytes, bar_bytes, total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int L, int w, int CS) {
+// gs: 1, or 2 when G enters MMA2 as two 16-bit terms (hi + lo)
+__host__ __device__ inline TcLayout tc_layout(int L, int w, int CS, int gs) {
   TcLayout t;
   t.L = L; t.w = w; t.CS = CS; t.RPC = TC_ROWS / CS;
-  t.a_bytes = static_cast<uint32_t>(w) * 256u;                         // 128 rows x w BF16
+  t.a_bytes = static_cast<uint32_t>(w) * 256u;                         // 128 rows x w, 16-bit
   const uint32_t ring = OM_STAGES * static_cast<uint32_t>(L) * 128u;   // Omega chunks
   const uint32_t xch = TC_ROWS * static_cast<uint32_t>(L + 4) * 4u;   // D1 partial exchange (FP32, padded rows)
-  t.ring_bytes = ((ring > xch ? ring : xch) + 1023u) & ~1023u;
-  t.gt_bytes = 256u * static_cast<uint32_t>(L);                        // G^T: L x 128 rows BF16
+  t.gt_bytes = 256u * static_cast<uint32_t>(L * gs);                   // G^T: gs x L x 128 rows, 16-bit
+  // the Omega ring (MMA1), the exchange rows (cluster reduction) and the G^T operand (MMA2)
+  // are live in turn within a tile, so they share one region
+  uint32_t r = ring > xch ? ring : xch;
+  r = r > t.gt_bytes ? r : t.gt_bytes;
+  t.ring_bytes = (r + 1023u) & ~1023u;
   t.shift_bytes = ((static_cast<uint32_t>(w) * 4u) + 15u) & ~15u;
   t.y_bytes = ((static_cast<uint32_t>(t.RPC) * L * 4u) + 15u) & ~15u;  // own reduced rows, FP32
-  t.yt_bytes = static_cast<uint32_t>(L) * (t.RPC / 8) * 16u;            // same, packed BF16 [L][RPC/8]
+  t.yt_bytes = static_cast<uint32_t>(L * gs) * (t.RPC / 8) * 16u;       // same, packed 16-bit [gs][L][RPC/8]
   t.bar_bytes = 8u * (2 * OM_STAGES + MAX_CHUNKS + 2);
-  t.total = 1024u + t.a_bytes + t.ring_bytes + t.gt_bytes + t.shift_bytes + t.y_bytes + t.yt_bytes + t.bar_bytes;
+  t.total = 1024u + t.a_bytes + t.ring_bytes + t.shift_bytes + t.y_bytes + t.yt_bytes + t.bar_bytes;
   return t;
 }
 
@@ -239,6 +244,7 @@ struct TcArgs {
   int64_t n;
   int l, L, w, CS;
   int vec_ok;
+  int drain_every;             // tiles accumulated in TMEM before H is added to Hpart
   const float* shift;
   const uint16_t* om16;        // Omega (operand format bits), chunk g at g * L * 64 elements, pre-swizzled
   const float* scale;          // operand scale s (power of two); NULL = 1
@@ -278,13 +284,14 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int L = a.L, w = a.w, CS = a.CS, l = a.l;
-  const TcLayout lay = tc_layout(L, w, CS);
+  constexpr int GS = FMT == FMT_F16 ? 2 : 1;   // FP16 form: G = G_hi + G_lo in MMA2
+  const TcLayout lay = tc_layout(L, w, CS, GS);
   const int RPC = lay.RPC, G8 = RPC / 8;
   uint8_t* sA = base;
   uint8_t* sRing = sA + lay.a_bytes;
   float* sX = reinterpret_cast<float*>(sRing);              // exchange buffer (aliases the ring)
-  uint8_t* sGt = sRing + lay.ring_bytes;
-  float* sShift = reinterpret_cast<float*>(sGt + lay.gt_bytes);
+  uint8_t* sGt = sRing;                                     // G^T operand (aliases the ring too)
+  float* sShift = reinterpret_cast<float*>(sRing + lay.ring_bytes);
   float* sY = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(sShift) + lay.shift_bytes);
   uint4* sYt = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(sY) + lay.y_bytes);
   uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sYt) + lay.yt_bytes);
@@ -294,7 +301,6 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
   uint64_t* mma1_done = ablk + MAX_CHUNKS;
   uint64_t* mma2_done = mma1_done + 1;
   __shared__ uint32_t tmem_sh;
-  __shared__ int dead_sh;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -321,7 +327,6 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
     mbar_init(su32(mma1_done), 1);
     mbar_init(su32(mma2_done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    dead_sh = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_sh)),
@@ -346,6 +351,8 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
   uint32_t iter = 0;
   bool dead = false;
   bool any_tile = false;
+  bool zero_h = true;     // the next MMA2 starts a fresh TMEM accumulation of H
+  bool drained = false;   // this CTA's Hpart slice holds a partial already
   const uint32_t id1 = idesc_fmt<FMT>(TC_ROWS, L, 0, 0);
   const uint32_t id2 = idesc_fmt<FMT>(TC_ROWS, L, 1, 0);
   // operands carry s A_hat and s G; every partial is brought back by exact powers of two
@@ -520,9 +527,17 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
           acc.x += v[p].x; acc.y += v[p].y; acc.z += v[p].z; acc.w += v[p].w;
         }
       }
-      // checked after the rounding: an FP16 operand can overflow where the FP32 sum did not
-      float y[4] = {round1<FMT>(acc.x), round1<FMT>(acc.y), round1<FMT>(acc.z), round1<FMT>(acc.w)};
-      if (!(isfinite(y[0]) && isfinite(y[1]) && isfinite(y[2]) && isfinite(y[3]))) atomicOr(a.flags, 1);
+      // G' = the operand value(s) of G: one rounding, or hi + lo (hi + lo is exact in FP32)
+      const float ac[4] = {acc.x, acc.y, acc.z, acc.w};
+      float y[4];
+      bool fin = true;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float hi = round1<FMT>(ac[i]);
+        fin = fin && isfinite(hi);   // after the rounding: an FP16 operand can overflow where FP32 did not
+        y[i] = GS == 2 ? hi + round1<FMT>(ac[i] - hi) : hi;
+      }
+      if (!fin) atomicOr(a.flags, 1);
       const int cl = l - c4 * 4;
       if (cl >= 0 && cl < 4) y[cl] = (row0 + r0 + rr < sg.m) ? 1.f : 0.f;   // ones column -> column sums
       float* dst = sY + rr * L + c4 * 4;
@@ -530,16 +545,23 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
     }
     __syncthreads();
     TC_TRACE(5);
-    // publish the own rows packed as G^T chunks: 8 rows of one column in 16 bytes
+    // publish the own rows packed as G^T chunks: 8 rows of one column in 16 bytes (hi terms,
+    // then lo terms when split)
     for (int it = tid; it < L * G8; it += TC_NT) {
       const int lc = it / G8, g = it % G8;
       const float* y = sY + (g * 8) * L + lc;
-      uint4 pk;
-      pk.x = pack2<FMT>(y[0 * L], y[1 * L]);
-      pk.y = pack2<FMT>(y[2 * L], y[3 * L]);
-      pk.z = pack2<FMT>(y[4 * L], y[5 * L]);
-      pk.w = pack2<FMT>(y[6 * L], y[7 * L]);
-      sYt[lc * G8 + g] = pk;
+      float hi[8], lo[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        hi[r] = round1<FMT>(y[r * L]);
+        lo[r] = y[r * L] - hi[r];
+      }
+      sYt[lc * G8 + g] = make_uint4(pack2<FMT>(hi[0], hi[1]), pack2<FMT>(hi[2], hi[3]), pack2<FMT>(hi[4], hi[5]),
+                                    pack2<FMT>(hi[6], hi[7]));
+      if constexpr (GS == 2) {
+        sYt[(L + lc) * G8 + g] = make_uint4(pack2<FMT>(lo[0], lo[1]), pack2<FMT>(lo[2], lo[3]),
+                                            pack2<FMT>(lo[4], lo[5]), pack2<FMT>(lo[6], lo[7]));
+      }
     }
     // Gram, sums of G and the optional G output from the own rows
     {
@@ -552,7 +574,7 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
           while (c1 * (c1 + 1) / 2 > e) --c1;
           while ((c1 + 1) * (c1 + 2) / 2 <= e) ++c1;
           const int c2 = e - c1 * (c1 + 1) / 2;
-          float acc = 0.f;   // products of BF16 values are exact in FP32
+          float acc = 0.f;   // G' rows in FP32 (one 16-bit value, or hi + lo)
           for (int rr = 0; rr < RPC; ++rr) acc = fmaf(sY[rr * L + c1], sY[rr * L + c2], acc);
           gram_acc[i] += static_cast<double>(acc);
         }
@@ -573,12 +595,16 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
     TC_TRACE(6);
     cluster_sync();   // #2: every CTA's rows are published
     TC_TRACE(7);
-    // pull all 128 rows of G' into the own G^T operand tile (K-major, L x 128 rows)
-    for (int it = tid; it < L * (TC_ROWS / 8); it += TC_NT) {
-      const int lc = it / (TC_ROWS / 8), g = it % (TC_ROWS / 8);
+    // pull all 128 rows of G' into the own G^T operand tile (K-major, L x 128 rows; the lo
+    // terms follow the hi terms at +256 L bytes)
+    for (int it = tid; it < GS * L * (TC_ROWS / 8); it += TC_NT) {
+      const int h = it / (L * (TC_ROWS / 8));
+      const int rem = it - h * (L * (TC_ROWS / 8));
+      const int lc = rem / (TC_ROWS / 8), g = rem % (TC_ROWS / 8);
       const int p = g / G8, gl = g % G8;
-      const uint4 pk = ld_dsmem_v4u(mapa(su32(sYt + lc * G8 + gl), static_cast<uint32_t>(p)));
-      const uint32_t off = static_cast<uint32_t>(g >> 3) * (static_cast<uint32_t>(L) * 128u) +
+      const uint4 pk = ld_dsmem_v4u(mapa(su32(sYt + (h * L + lc) * G8 + gl), static_cast<uint32_t>(p)));
+      const uint32_t off = static_cast<uint32_t>(h) * (256u * static_cast<uint32_t>(L)) +
+                           static_cast<uint32_t>(g >> 3) * (static_cast<uint32_t>(L) * 128u) +
                            static_cast<uint32_t>(lc >> 3) * 1024u +
                            sw128(static_cast<uint32_t>(lc & 7), static_cast<uint32_t>(g & 7) * 16u);
       *reinterpret_cast<uint4*>(sGt + off) = pk;
@@ -595,8 +621,13 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
 #pragma unroll
           for (int ks = 0; ks < TC_ROWS / 16; ++ks) {
             const uint64_t ad = dA2 + ((static_cast<uint32_t>(2 * mt) * 16384u + static_cast<uint32_t>(ks) * 2048u) >> 4);
-            const uint64_t bd = dB2 + ((static_cast<uint32_t>(ks >> 2) * chunk_bytes + static_cast<uint32_t>(ks & 3) * 32u) >> 4);
-            mma_bf16(tH + static_cast<uint32_t>(mt * L), ad, bd, id2, (any_tile || ks > 0) ? 1u : 0u);
+#pragma unroll
+            for (int h = 0; h < GS; ++h) {
+              const uint64_t bd = dB2 + ((static_cast<uint32_t>(h) * 256u * static_cast<uint32_t>(L) +
+                                          static_cast<uint32_t>(ks >> 2) * chunk_bytes +
+                                          static_cast<uint32_t>(ks & 3) * 32u) >> 4);
+              mma_bf16(tH + static_cast<uint32_t>(mt * L), ad, bd, id2, (zero_h && ks == 0 && h == 0) ? 0u : 1u);
+            }
           }
         }
       }
@@ -607,34 +638,46 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
     __syncwarp();
     tc_fence_after();
     TC_TRACE(9);
+
+    // ------------------------------------------------ drain: Hpart += H (TMEM), every few tiles
+    // A TMEM accumulation rounds toward zero at every MMA; short accumulations keep H's
+    // error at the level of FP32 rounding. Hpart (L2-resident, FP32) is owned by this CTA
+    // for its features, so plain read-add-write in tile order is deterministic.
+    zero_h = ((iter + 1) % static_cast<uint32_t>(a.drain_every) == 0) || (tile + ncl >= a.ntiles);
+    if (zero_h) {
+      const int q = warp & 3, part = warp >> 2;   // three warps per TMEM lane quadrant
+      const int cpr = L / 8;                      // 8-column chunks per 128-feature tile
+      for (int ch = part; ch < (w / 128) * cpr; ch += TC_NT / 128) {
+        const int mt = ch / cpr, c = (ch - mt * cpr) * 8;
+        float v[8];
+        tmem_ld8(tH + static_cast<uint32_t>(mt * L + c) + (static_cast<uint32_t>(q * 32) << 16), v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] *= (c + i == l ? inv_s : inv_s * inv_s);   // H carries s^2, sums s
+        const int64_t feat = f0 + mt * 128 + q * 32 + lane;
+        float4* dst = reinterpret_cast<float4*>(a.Hpart + (static_cast<int64_t>(cid) * (CS * static_cast<int64_t>(w)) + feat) * L + c);
+        float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0;
+        if (drained) {
+          o0 = dst[0];
+          o1 = dst[1];
+        }
+        dst[0] = make_float4(o0.x + v[0], o0.y + v[1], o0.z + v[2], o0.w + v[3]);
+        dst[1] = make_float4(o1.x + v[4], o1.y + v[5], o1.z + v[6], o1.w + v[7]);
+      }
+      drained = true;
+      tc_fence_before();   // the loads above precede the next MMA2 that overwrites H
+    }
   }
 
   // ---------------------------------------------------------------- epilogue
   if (dead) {
     atomicOr(a.flags, 2);
-    dead_sh = 1;
   }
   __syncthreads();
   const int64_t npad = static_cast<int64_t>(CS) * w;
   const int64_t cta = static_cast<int64_t>(cid) * CS + rank;
-  if (warp < 8) {   // H slice: TMEM lanes = features of each 128-feature tile
-    const int q = warp & 3, half = warp >> 2;
-    for (int mt = 0; mt < w / 128; ++mt) {
-      const int64_t feat = f0 + mt * 128 + q * 32 + lane;
-      float* dst = a.Hpart + (static_cast<int64_t>(cid) * npad + feat) * L;
-      const int cbeg = half * (L / 2), cend = cbeg + L / 2;
-      for (int c = cbeg; c < cend; c += 8) {
-        float v[8];
-        tmem_ld8(tH + static_cast<uint32_t>(mt * L + c) + (static_cast<uint32_t>(q * 32) << 16), v);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          // H carries s^2, the ones column (column sums) s
-          v[i] = (!any_tile || dead_sh) ? 0.f : v[i] * (c + i == l ? inv_s : inv_s * inv_s);
-        }
-        reinterpret_cast<float4*>(dst + c)[0] = make_float4(v[0], v[1], v[2], v[3]);
-        reinterpret_cast<float4*>(dst + c)[1] = make_float4(v[4], v[5], v[6], v[7]);
-      }
-    }
+  if (!any_tile) {   // a cluster without tiles contributes a zero H slice
+    for (int64_t i = tid; i < static_cast<int64_t>(w) * L; i += TC_NT)
+      a.Hpart[(static_cast<int64_t>(cid) * npad + f0) * L + i] = 0.f;
   }
   {
     const int LL = L * L, LT = L * (L + 1) / 2;
@@ -763,7 +806,7 @@ bool tc_config(int64_t n, int L, int fmt, TcConfig* cfg) {
     const int64_t w = ((n + CS - 1) / CS + 127) / 128 * 128;
     if (w > 64 * MAX_CHUNKS) continue;
     if ((1 + w / 128) * L > static_cast<int64_t>(TMEM_COLS)) continue;
-    const TcLayout lay = tc_layout(L, static_cast<int>(w), CS);
+    const TcLayout lay = tc_layout(L, static_cast<int>(w), CS, fmt == FMT_F16 ? 2 : 1);
     if (lay.total > 227u * 1024u) continue;
     cfg->CS = CS;
     cfg->w = static_cast<int>(w);
@@ -858,6 +901,7 @@ cudaError_t tc_pass(const State& s, const TcWork& w, const TcPending& pend, cuda
   args.w = w.cfg.w;
   args.CS = w.cfg.CS;
   args.vec_ok = vec_ok ? 1 : 0;
+  args.drain_every = w.fmt == FMT_F16 ? 2 : 4;   // 32 MMAs per TMEM accumulation of H either way
   args.shift = s.shift;
   args.om16 = w.om16;
   args.scale = w.fmt == FMT_F16 ? w.scale : nullptr;
