@@ -755,12 +755,12 @@ __global__ void omega_op_kernel(uint64_t seed, int64_t n, int64_t npad, int l, i
 // four-fold headroom under the FP16 maximum.
 __global__ void row_norm_max_kernel(const float* __restrict__ rows, int64_t m, int64_t n, int64_t ld,
                                     const float* __restrict__ shift, unsigned int* __restrict__ out_bits) {
-  __shared__ double red[256];
+  __shared__ float red[256];   // only a power of two is taken from the result: FP32 suffices
   for (int64_t r = blockIdx.x; r < m; r += gridDim.x) {
-    double s = 0.0;
+    float s = 0.f;
     for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-      const double d = static_cast<double>(rows[r * ld + j]) - static_cast<double>(shift[j]);
-      s += d * d;
+      const float d = rows[r * ld + j] - shift[j];
+      s = fmaf(d, d, s);
     }
     red[threadIdx.x] = s;
     __syncthreads();
@@ -768,7 +768,7 @@ __global__ void row_norm_max_kernel(const float* __restrict__ rows, int64_t m, i
       if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
       __syncthreads();
     }
-    if (threadIdx.x == 0) atomicMax(out_bits, __float_as_uint(static_cast<float>(sqrt(red[0]))));
+    if (threadIdx.x == 0) atomicMax(out_bits, __float_as_uint(sqrtf(red[0])));
     __syncthreads();
   }
 }

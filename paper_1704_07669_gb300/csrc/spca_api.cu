@@ -333,7 +333,13 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   CC(dalloc(&s->shift_part, size_t(kShiftParts) * n));
 
   FinalWork& f = s->fin;
-  f.nparts = 64;
+  // partial C = B B^T per block of the n x l product: about 8 MiB of them, at least 4
+  // (the eigensolver reuses the space as scratch)
+  {
+    const int64_t per = int64_t(L) * L * int64_t(sizeof(double));
+    int64_t np = (int64_t(8) << 20) / per;
+    f.nparts = static_cast<int>(np < 4 ? 4 : (np > 304 ? 304 : np));
+  }
   CC(dalloc(&f.Hbar, size_t(n) * L));
   CC(dalloc(&f.gbar, size_t(L) * L));
   CC(dalloc(&f.T, size_t(L) * L));
