@@ -4,7 +4,10 @@ A step is one whole pass of the method over the 100000 x 10000 FP32
 low-rank-plus-noise workload (k = 50, p = 10, 4096-row blocks, column centring):
 Omega regenerated (spca_reset), 25 row blocks folded in (spca_update) and the
 FP64 finalisation (spca_finalize). The data (4.0 GB) is larger than L2, so no
-L2 flush is needed between steps.
+L2 flush is needed between steps. The timed form is the FP16 tensor-core pass
+(G split into two FP16 terms), the one that holds every sigma within 1e-3 of
+the oracle; the FP32 and BF16 forms are measured on the same data and reported
+under "forms".
 
 Prints one JSON line. `value` is GB/s of A (as stored) per second of device
 time; `e2e` is the same metric through the C ABI with host (pinned) buffers and
@@ -176,6 +179,90 @@ def run_reference(args):
     return 0
 
 
+def roofline_for(math_name, prof, bytes_total, rows_total, pk):
+    """Roofline of the dominant kernel of the pass for one arithmetic form."""
+    l = K + P
+    if math_name == "fp32":
+        # the FP32 path is bound by the FMA pipe: each contraction is 2 m n l flops per pass
+        dom = max(("g_partial", "h_partial"), key=lambda k_: prof[k_][0])
+        dom_ms, dom_launches = prof[dom]
+        flops = 2.0 * rows_total * N * l
+        achieved = flops / (dom_ms * 1e-3) / 1e12
+        alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "traffic": None, "kernel": dom, "kernel_avg_ms": dom_ms / max(dom_launches, 1),
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"}
+    # the fused tensor-core kernel reads every byte of A once: HBM-bound
+    dom = "tc_sketch"
+    dom_ms, dom_launches = prof[dom]
+    achieved = bytes_total / (dom_ms * 1e-3) / 1e9
+    traffic = None
+    rec = traffic_record(math_name)
+    if rec is not None:
+        traffic = rec["dram_bytes_per_row"] * rows_total / max(dom_launches, 1)
+    return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "kernel": dom,
+            "kernel_avg_ms": dom_ms / max(dom_launches, 1),
+            "peak_note": f"HBM copy bandwidth ({pk['source']}), algorithmic bytes = A read once per pass",
+            "algorithmic_bytes_per_launch": bytes_total / max(dom_launches, 1)}
+
+
+def traffic_record(math_name):
+    """DRAM bytes per row of the fused kernel from a committed ncu capture, if it was taken on
+    the kernel source as it is now (the record stores the source's SHA-256)."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "tc_sketch_traffic.json")))[math_name]
+        src = open(os.path.join(ROOT, "paper_1704_07669_gb300", "csrc", "sketch_tc.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+            return None
+        return rec
+    except Exception:
+        return None
+
+
+def run_form(spca, math_name, A, seed, stream, steps_arg, warmup, ws):
+    """Time whole passes (reset, all row blocks, finalize) of one arithmetic form."""
+    m = A.shape[0]
+    dev = A.device
+    sess = spca.Session(N, K, P, seed, math=math_name, stream=stream)
+    sigma_d = torch.zeros(K, dtype=torch.float64, device=dev)
+    V_d = torch.zeros((K, N), dtype=torch.float64, device=dev)
+
+    def step():
+        spca.spca_reset(sess.handle, seed)
+        for r0 in range(0, m, BLOCK):
+            spca.spca_update(sess.handle, A[r0:r0 + BLOCK])
+        spca.spca_finalize(sess.handle, sigma_d, V_d, out_on_device=True)
+
+    for _ in range(max(warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    steps = steps_arg
+    if steps is None:
+        t0 = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        steps = max(10, int(math.ceil(3.0 / max(dt, 1e-4))))
+    spca.spca_clear_profile(sess.handle)
+    spca.spca_set_profiling(sess.handle, True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    spca.spca_set_profiling(sess.handle, False)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ws)
+    prof = sess.profile()
+    return sess, step, {"ms": ms, "steps": steps, "prof": prof, "sigma": sigma_d.cpu().numpy()}
+
+
 def run_ours(args):
     import paper_1704_07669_gb300 as spca
     from paper_1704_07669_gb300 import build as spca_build
@@ -187,80 +274,36 @@ def run_ours(args):
     spca_build.build()
     spca.lib()
     pk = peaks()
+    m = args.m
 
-    w = synth.workload_c2(device=dev, seed=synth.SEED_BASE + 1 + rank)
+    w = synth.workload_c2(m=m, device=dev, seed=synth.SEED_BASE + 1 + rank)
     A = w["A"]
     seed = w["seed"]
     stream = torch.cuda.Stream(device=dev)
-    sess = spca.Session(N, K, P, seed, math=args.math, stream=stream)
-    sigma_d = torch.zeros(K, dtype=torch.float64, device=dev)
-    V_d = torch.zeros((K, N), dtype=torch.float64, device=dev)
-    torch.cuda.synchronize()
+    bytes_A = m * N * 4
 
-    def step():
-        spca.spca_reset(sess.handle, seed)
-        for r0 in range(0, M, BLOCK):
-            spca.spca_update(sess.handle, A[r0:r0 + BLOCK])
-        spca.spca_finalize(sess.handle, sigma_d, V_d, out_on_device=True)
+    # the other arithmetic forms, measured first on the same data (reported under "forms")
+    forms = {}
+    for other in [f for f in args.forms.split(",") if f and f != args.math]:
+        s_o, _, r_o = run_form(spca, other, A, seed, stream, args.steps, args.warmup, ws)
+        s_o.close()
+        forms[other] = {"value": ws * bytes_A * r_o["steps"] / (r_o["ms"] * 1e-3) / 1e9, "unit": "GB/s",
+                        "ms_per_step": r_o["ms"] / r_o["steps"], "steps": r_o["steps"],
+                        "roofline": roofline_for(other, r_o["prof"], bytes_A * r_o["steps"], m * r_o["steps"], pk),
+                        "finalize_ms_per_step": r_o["prof"]["finalize"][0] / r_o["steps"]}
 
-    for _ in range(max(args.warmup, 1)):
-        step()
-    torch.cuda.synchronize()
-    steps = args.steps
-    if steps is None:
-        t0 = time.perf_counter()
-        step()
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        steps = max(10, int(math.ceil(3.0 / max(dt, 1e-4))))
-
-    spca.spca_clear_profile(sess.handle)
-    spca.spca_set_profiling(sess.handle, True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
         time.sleep(0.3)
-        barrier(ws)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(steps):
-            step()
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        barrier(ws)
-    spca.spca_set_profiling(sess.handle, False)
-    ms = ev0.elapsed_time(ev1)
-    ms = max_over_ranks(ms, ws)
-    prof = sess.profile()
+        sess, step, res = run_form(spca, args.math, A, seed, stream, args.steps, args.warmup, ws)
+    ms, steps, prof = res["ms"], res["steps"], res["prof"]
     launches = int(sum(v[1] for v in prof.values()))
-    bytes_A = M * N * 4
     value = ws * bytes_A * steps / (ms * 1e-3) / 1e9
-
-    l = K + P
-    if args.math == "fp32":
-        # roofline of the dominant kernel: the FP32 FMA pipe (each contraction is 2 m n l flops per pass)
-        dom = max(("g_partial", "h_partial"), key=lambda k_: prof[k_][0])
-        dom_ms, dom_launches = prof[dom]
-        flops_total = 2.0 * M * N * l * steps
-        achieved = flops_total / (dom_ms * 1e-3) / 1e12
-        alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": achieved / alu_peak, "traffic": None, "kernel": dom,
-                    "kernel_avg_ms": dom_ms / max(dom_launches, 1),
-                    "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"}
-    else:
-        # the fused tensor-core kernel reads every byte of A once: HBM-bound
-        dom = "tc_sketch"
-        dom_ms, dom_launches = prof[dom]
-        achieved = bytes_A * steps / (dom_ms * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": dom,
-                    "kernel_avg_ms": dom_ms / max(dom_launches, 1),
-                    "peak_note": f"HBM copy bandwidth ({pk['source']}), algorithmic bytes = A read once"}
-    kernels = {k_: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps} for k_, v in prof.items()}
+    roofline = roofline_for(args.math, prof, bytes_A * steps, m * steps, pk)
+    kernels = {k_: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps} for k_, v in prof.items()
+               if v[1]}
 
     # end to end through the C ABI: pinned host rows copied inside the timed region, results read back
-    A_host = torch.empty((M, N), dtype=torch.float32, pin_memory=True)
+    A_host = torch.empty((m, N), dtype=torch.float32, pin_memory=True)
     A_host.copy_(A)
     sig_h = np.zeros(K)
     V_h = np.zeros((K, N))
@@ -269,7 +312,7 @@ def run_ours(args):
 
     def e2e_step():
         spca.spca_reset(sess.handle, seed)
-        for r0 in range(0, M, BLOCK):
+        for r0 in range(0, m, BLOCK):
             spca.spca_update(sess.handle, rows_np[r0:r0 + BLOCK])
         spca.spca_finalize(sess.handle, sig_h, V_h, out_on_device=False)
 
@@ -286,20 +329,22 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        sample_rows = 8 * BLOCK
+        sample_rows = min(8 * BLOCK, m)
         cpu = cpu_baseline(A[:sample_rows].cpu().numpy(), seed, "first 8 row blocks of the timed matrix")
 
     sess.close()
     if rank != 0:
         return 0
+    workload = WORKLOAD if m == M else WORKLOAD.replace("100000x", f"{m}x")
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": steps, "warmup": args.warmup,
             "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "fp16": "f16"}.get(args.math, "bf16"), "data": "synthetic",
-            "config": {"workload": WORKLOAD, "math": args.math, "l2": "inputs larger than L2 (4.0 GB), no flush",
+            "config": {"workload": workload, "math": args.math,
+                       "l2": f"inputs larger than L2 ({bytes_A / 1e9:.1f} GB), no flush",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks.summary(), "kernels": kernels, "peaks_source": pk["source"],
-            "tflops": 4.0 * M * N * l * steps * ws / (ms * 1e-3) / 1e12}
+            "clocks": clocks.summary(), "kernels": kernels, "forms": forms, "peaks_source": pk["source"],
+            "tflops": 4.0 * m * N * (K + P) * steps * ws / (ms * 1e-3) / 1e12}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -310,7 +355,11 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--math", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--math", default="fp16", choices=["fp32", "bf16", "fp16"],
+                    help="arithmetic of the timed pass (default: the FP16 tensor-core form, split G)")
+    ap.add_argument("--forms", default="fp32,bf16",
+                    help="other forms measured on the same data and reported under 'forms' ('' for none)")
+    ap.add_argument("--m", type=int, default=M, help="rows of the workload (profiling runs use fewer)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
