@@ -159,9 +159,14 @@ spca_status spca_get_state(spca_session* s, double* H_bar, double* gram_bar,
 
 /*
  * spca_merge - dst += src for two sessions that saw disjoint row sets of the
- * same data stream (same n, k, p, seed, centering and shift). The sketch is a
- * sum over rows (Eq. 11), so the merged session equals one session that saw
- * both row sets. Both sessions must be on the same device. Synchronises src.
+ * same data (same n, k, p, seed, math form and centering). The sketch is a sum
+ * over rows (Eq. 11), so the merged session equals one session that saw both
+ * row sets. With centering, each session subtracts the shift c of its own first
+ * rows; src's sums are rebased onto dst's shift while adding (delta = c_src -
+ * c_dst, gamma = Omega^T delta: H += H_s + s_s gamma^T + delta sG_s^T +
+ * m_s delta gamma^T, and likewise for the Gram matrix and the sums). A dst
+ * without rows takes src's shift. Both sessions must be on the same device.
+ * Synchronises both streams. src is not modified.
  * Errors: SPCA_E_INVALID (mismatch), SPCA_E_CUDA, SPCA_E_STATE.
  */
 spca_status spca_merge(spca_session* dst, const spca_session* src);

@@ -16,6 +16,7 @@
 // the FP32 FMA pipe (4 m n l flops against m n element reads).
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
+#include <cuda_fp16.h>
 
 #include <mutex>
 
@@ -472,6 +473,76 @@ __global__ void merge_kernel(double* __restrict__ H, const double* __restrict__ 
   }
 }
 
+// Shift rebase of a merge. Sessions that saw different first rows subtract different
+// shifts: src accumulated A_s = A - 1 c_s^T, dst wants A - 1 c_d^T = A_s + 1 delta^T with
+// delta = c_s - c_d, hence G_d = G_s + 1 gamma^T with gamma = Omega^T delta (Omega as the
+// pass used it: FP32, or rounded to BF16 / FP16). Summing over the m_s rows of src:
+//   H_d = H_s + s_s gamma^T + delta sG_s^T + m_s delta gamma^T
+//   Gram_d = Gram_s + sG_s gamma^T + gamma sG_s^T + m_s gamma gamma^T
+//   s_d = s_s + m_s delta,  sG_d = sG_s + m_s gamma
+// (s = column sums of the shifted rows, sG = column sums of G; Eq. 11 is a sum over rows).
+// gamma_c, one block per column c < l, Omega regenerated from the seed, FP64 sums in a fixed
+// order. fmt: 0 FP32, 1 BF16, 2 FP16.
+__global__ void rebase_gamma_kernel(uint64_t seed, int64_t n, int fmt, const float* __restrict__ c_src,
+                                    const float* __restrict__ c_dst, double* __restrict__ gamma) {
+  __shared__ double red[256];
+  const int c = blockIdx.x;
+  double acc = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const double d = static_cast<double>(c_src[j]) - static_cast<double>(c_dst[j]);
+    if (d == 0.0) continue;
+    const U32x4 wv = omega_words_at(seed, j, static_cast<uint32_t>(c / 4), 0u);
+    double z[4];
+    box_muller(wv.x, wv.y, z[0], z[1]);
+    box_muller(wv.z, wv.w, z[2], z[3]);
+    const float f = static_cast<float>(z[c & 3]);
+    double v = f;
+    if (fmt == 1) v = __bfloat162float(__float2bfloat16_rn(f));
+    if (fmt == 2) v = __half2float(__float2half_rn(f));
+    acc = fma(v, d, acc);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) gamma[c] = red[0];
+}
+
+__global__ void merge_rebase_kernel(double* __restrict__ H, const double* __restrict__ Hs, double* __restrict__ colsum,
+                                    const double* __restrict__ colsum_s, double* __restrict__ gram,
+                                    const double* __restrict__ gram_s, double* __restrict__ sG,
+                                    const double* __restrict__ sG_s, const float* __restrict__ c_src,
+                                    const float* __restrict__ c_dst, const double* __restrict__ gamma, double m_s,
+                                    int64_t n, int l, int L) {
+  const int64_t total = n * L > static_cast<int64_t>(L) * L ? n * L : static_cast<int64_t>(L) * L;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (idx < n * L) {
+      const int64_t j = idx / L;
+      const int c = static_cast<int>(idx - j * L);
+      double v = Hs[idx];
+      if (c < l) {
+        const double d = static_cast<double>(c_src[j]) - static_cast<double>(c_dst[j]);
+        v += colsum_s[j] * gamma[c] + d * sG_s[c] + m_s * d * gamma[c];
+      }
+      H[idx] += v;
+    }
+    if (idx < n) {
+      const double d = static_cast<double>(c_src[idx]) - static_cast<double>(c_dst[idx]);
+      colsum[idx] += colsum_s[idx] + m_s * d;
+    }
+    if (idx < static_cast<int64_t>(L) * L) {
+      const int a = static_cast<int>(idx / L), b = static_cast<int>(idx % L);
+      double v = gram_s[idx];
+      if (a < l && b < l) v += sG_s[a] * gamma[b] + gamma[a] * sG_s[b] + m_s * gamma[a] * gamma[b];
+      gram[idx] += v;
+    }
+    if (idx < L) sG[idx] += sG_s[idx] + (idx < l ? m_s * gamma[idx] : 0.0);
+  }
+}
+
 int grid_for(int64_t total, int threads) {
   int64_t b = (total + threads - 1) / threads;
   if (b > 152 * 32) b = 152 * 32;
@@ -628,6 +699,16 @@ cudaError_t launch_merge(const State& dst, const State& src, cudaStream_t st) {
   const int64_t total = dst.n > dst.L ? dst.n * dst.L : static_cast<int64_t>(dst.L) * dst.L;
   merge_kernel<<<grid_for(total, 256), 256, 0, st>>>(dst.H, src.H, dst.colsum, src.colsum, dst.gram,
                                                               src.gram, dst.sG, src.sG, dst.n, dst.L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_rebase(const State& dst, const State& src, uint64_t seed, int fmt, int64_t m_src,
+                                double* gamma, cudaStream_t st) {
+  rebase_gamma_kernel<<<dst.l, 256, 0, st>>>(seed, dst.n, fmt, src.shift, dst.shift, gamma);
+  const int64_t total = dst.n * dst.L > int64_t(dst.L) * dst.L ? dst.n * dst.L : int64_t(dst.L) * dst.L;
+  merge_rebase_kernel<<<grid_for(total, 256), 256, 0, st>>>(dst.H, src.H, dst.colsum, src.colsum, dst.gram,
+                                                             src.gram, dst.sG, src.sG, src.shift, dst.shift, gamma,
+                                                             static_cast<double>(m_src), dst.n, dst.l, dst.L);
   return cudaGetLastError();
 }
 

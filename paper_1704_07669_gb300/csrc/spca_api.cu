@@ -521,19 +521,7 @@ spca_status spca_merge(spca_session* dst, const spca_session* src) {
   if (src->n != dst->n || src->k != dst->k || src->p != dst->p || src->seed != dst->seed ||
       src->opt.center != dst->opt.center || src->device != dst->device)
     return fail(s, SPCA_E_INVALID, "sessions differ in n, k, p, seed, centering or device");
-  if (dst->opt.center && src->m > 0) {
-    if (!dst->shift_set) return fail(s, SPCA_E_INVALID, "dst has no shift yet; update it first");
-    // shifts must agree exactly for the sums to combine
-    float* a = new (std::nothrow) float[dst->n];
-    float* b = new (std::nothrow) float[dst->n];
-    if (!a || !b) { delete[] a; delete[] b; return fail(s, SPCA_E_NOMEM, "host allocation failed"); }
-    cudaError_t e1 = cudaMemcpy(a, dst->shift, sizeof(float) * dst->n, cudaMemcpyDeviceToHost);
-    cudaError_t e2 = cudaMemcpy(b, src->shift, sizeof(float) * dst->n, cudaMemcpyDeviceToHost);
-    const bool same = (e1 == cudaSuccess && e2 == cudaSuccess) && std::memcmp(a, b, sizeof(float) * dst->n) == 0;
-    delete[] a; delete[] b;
-    if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(s, SPCA_E_CUDA, "shift copy failed");
-    if (!same) return fail(s, SPCA_E_INVALID, "sessions use different shifts; give both the same first rows");
-  }
+  if (src->opt.math != dst->opt.math) return fail(s, SPCA_E_INVALID, "sessions differ in math form");
   CU(cudaSetDevice(dst->device));
   st = flush_tc(dst);
   if (st != SPCA_OK) return st;
@@ -544,7 +532,22 @@ spca_status spca_merge(spca_session* dst, const spca_session* src) {
     if (st != SPCA_OK) return fail(s, st, "flushing src failed: %s", ms->err);
   }
   CU(cudaStreamSynchronize(src->stream));
-  CU(launch_merge(dst->state(), src->state(), dst->stream));
+  if (dst->opt.center && src->shift_set && !dst->shift_set) {
+    // dst has seen no rows: it takes src's shift (and operand scale) with its sums
+    CU(cudaMemcpyAsync(dst->shift, src->shift, sizeof(float) * dst->n, cudaMemcpyDeviceToDevice, dst->stream));
+    dst->shift_set = true;
+    if (dst->tc && dst->tcw.fmt == 1 && src->scale_set) {
+      CU(cudaMemcpyAsync(dst->tcw.scale, src->tcw.scale, sizeof(float), cudaMemcpyDeviceToDevice, dst->stream));
+      dst->scale_set = true;
+    }
+  }
+  if (dst->opt.center && src->shift_set && src->m > 0) {
+    // src's sums refer to its own shift: rebase them onto dst's while adding
+    const int fmt = dst->tc ? (dst->tcw.fmt == 1 ? 2 : 1) : 0;
+    CU(launch_merge_rebase(dst->state(), src->state(), dst->seed, fmt, src->m, dst->fin.lam, dst->stream));
+  } else {
+    CU(launch_merge(dst->state(), src->state(), dst->stream));
+  }
   CU(cudaStreamSynchronize(dst->stream));
   dst->m += src->m;
   return SPCA_OK;

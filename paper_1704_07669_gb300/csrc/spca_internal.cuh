@@ -77,6 +77,10 @@ cudaError_t simt_pass(const State& s, const SimtWork& w, const void* rows, int d
 
 // Merge: dst += src (H, colsum, sG, gram).
 cudaError_t launch_merge(const State& dst, const State& src, cudaStream_t st);
+// Merge with the shift rebase from src's shift to dst's (fmt: 0 FP32, 1 BF16, 2 FP16 Omega);
+// gamma: l doubles of scratch.
+cudaError_t launch_merge_rebase(const State& dst, const State& src, uint64_t seed, int fmt, int64_t m_src,
+                                double* gamma, cudaStream_t st);
 
 // gram += sum of `parts` partial Gram matrices (fixed order), sG likewise.
 cudaError_t launch_gram_accum(const double* gram_part, const double* sG_part, int parts, int L, double* gram,
