@@ -128,12 +128,14 @@ def cpu_baseline(A_sample_f32, seed, what):
 # ------------------------------------------------------------------------------------------ arms
 
 def dist_setup():
+    """Rank layout from the torchrun environment; one process per GPU, replicas of the pass."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return ws, rank, local
 
 
@@ -144,10 +146,12 @@ def barrier(ws):
 
 
 def max_over_ranks(x, ws):
+    """The largest of each rank's x (the job's time is its slowest rank's)."""
     if ws == 1:
         return x
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
