@@ -34,6 +34,21 @@ class Options(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
 
 
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("device_bytes", ctypes.c_size_t), ("math", ctypes.c_int32), ("max_sessions", ctypes.c_int32),
+                ("max_block_rows", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("updates_done", ctypes.c_int64), ("finalizes_done", ctypes.c_int64),
+                ("sessions_admitted", ctypes.c_int64), ("sessions_waiting", ctypes.c_int64),
+                ("update_p50_ms", ctypes.c_double), ("update_p99_ms", ctypes.c_double),
+                ("finalize_p50_ms", ctypes.c_double), ("finalize_p99_ms", ctypes.c_double),
+                ("rows_bytes", ctypes.c_double), ("active_seconds", ctypes.c_double),
+                ("device_bytes_in_use", ctypes.c_size_t), ("device_bytes_budget", ctypes.c_size_t)]
+
+
+SPCA_SERVER_AUTO_MATH = -1
 _LIB = None
 
 
@@ -69,6 +84,16 @@ def lib():
             "spca_omega_words": (i32, [u64, i64, i32, vp]),
             "spca_omega": (i32, [u64, i64, i32, vp]),
             "spca_shift_static": (i32, [vp, i64, i64, i64, i32, vp, vp, vp]),
+            "spca_server_default_options": (None, [ctypes.POINTER(ServerOptions)]),
+            "spca_server_create": (i32, [ctypes.POINTER(ServerOptions), ctypes.POINTER(vp)]),
+            "spca_server_open": (i32, [vp, i64, i32, i32, u64, ctypes.POINTER(i32)]),
+            "spca_server_update": (i32, [vp, i32, vp, i64, i64, ctypes.POINTER(u64)]),
+            "spca_server_finalize": (i32, [vp, i32, vp, vp, ctypes.POINTER(u64)]),
+            "spca_server_wait": (i32, [vp, u64, ctypes.c_double]),
+            "spca_server_close": (i32, [vp, i32]),
+            "spca_server_get_stats": (i32, [vp, ctypes.POINTER(ServerStats)]),
+            "spca_server_destroy": (i32, [vp]),
+            "spca_server_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -275,6 +300,77 @@ class Session:
     def close(self):
         if self.handle:
             spca_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- serving loop (include/spca_server.h)
+
+def _check_srv(status):
+    if status != SPCA_OK:
+        msg = lib().spca_server_last_error()
+        raise SpcaError(status, msg.decode() if msg else "")
+
+
+class Server:
+    """Thin wrapper of the spca_server_* calls: sessions resident on the device, requests queued
+    from any thread, completed by the library's worker thread."""
+
+    def __init__(self, device_bytes=0, math=SPCA_SERVER_AUTO_MATH, max_sessions=1024, max_block_rows=4096):
+        opt = ServerOptions()
+        lib().spca_server_default_options(ctypes.byref(opt))
+        opt.device_bytes = int(device_bytes)
+        opt.math = MATH_NAMES[math] if isinstance(math, str) else int(math)
+        opt.max_sessions = int(max_sessions)
+        opt.max_block_rows = int(max_block_rows)
+        h = ctypes.c_void_p()
+        _check_srv(lib().spca_server_create(ctypes.byref(opt), ctypes.byref(h)))
+        self.handle = h.value
+
+    def open(self, n, k, p, seed):
+        sid = ctypes.c_int32(-1)
+        _check_srv(lib().spca_server_open(self.handle, int(n), int(k), int(p), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                          ctypes.byref(sid)))
+        return sid.value
+
+    def update(self, sid, rows):
+        """Queue a block of device-resident FP32 rows (a 2-D CUDA tensor); returns a ticket."""
+        t = ctypes.c_uint64(0)
+        _check_srv(lib().spca_server_update(self.handle, int(sid), _ptr(rows)[0], int(rows.shape[0]),
+                                            int(rows.stride(0)), ctypes.byref(t)))
+        return t.value
+
+    def finalize(self, sid, sigma, V):
+        """Queue a finalisation into host numpy buffers sigma (k) and V (k x n, i.e. n x k column-major)."""
+        t = ctypes.c_uint64(0)
+        _check_srv(lib().spca_server_finalize(self.handle, int(sid), _ptr(sigma)[0], _ptr(V)[0], ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket, timeout_s=-1.0):
+        _check_srv(lib().spca_server_wait(self.handle, int(ticket), float(timeout_s)))
+
+    def close_session(self, sid):
+        _check_srv(lib().spca_server_close(self.handle, int(sid)))
+
+    def stats(self):
+        st = ServerStats()
+        _check_srv(lib().spca_server_get_stats(self.handle, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            lib().spca_server_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

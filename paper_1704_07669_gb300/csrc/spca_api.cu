@@ -227,6 +227,81 @@ spca_status run_piece(spca_session* s, const void* rows, int64_t m, int64_t ld, 
 
 }  // namespace
 
+namespace spca {
+
+// Device bytes that spca_create allocates for these parameters (each allocation rounded up
+// to 512 bytes); the serving loop admits sessions against this figure.
+size_t session_footprint(int64_t n, int k, int p, int math, int64_t max_block_rows) {
+  const int l = k + p;
+  const bool tc = (math == SPCA_MATH_BF16 || math == SPCA_MATH_FP16);
+  const int L = tc ? pad_l(l + 1) : pad_l(l);
+  TcConfig cfg{};
+  if (tc && !tc_config(n, L, math == SPCA_MATH_FP16 ? 1 : 0, &cfg)) return 0;
+  const int64_t mb = max_block_rows > 0 ? max_block_rows : kDefaultBlockRows;
+  size_t b = 0;
+  auto add = [&](int64_t count, size_t es) {
+    const size_t bytes = size_t(count < 1 ? 1 : count) * es;
+    b += (bytes + 511) & ~size_t(511);
+  };
+  if (!tc) add(n * L, 4);
+  add(n * L, 8); add(n, 4); add(n, 8); add(L, 8); add(int64_t(L) * L, 8); add(4, 4);
+  if (!tc) {
+    const int64_t mb_pad = ((mb + 127) / 128) * 128;
+    const int64_t gp_rows = mb_pad > 65536 ? mb_pad : 65536;
+    int64_t tmax = (int64_t(16) << 20) / (n * L);
+    const int64_t T = tmax < 1 ? 1 : (tmax > 16 ? 16 : tmax);
+    const int64_t groups = (mb + 31) / 32;
+    add(gp_rows * L, 4); add(mb * L, 4); add(groups * L * L, 8); add(groups * L, 8); add(T * n * L, 4); add(T * n, 4);
+  } else {
+    const int64_t npad = int64_t(cfg.CS) * cfg.w, nctas = int64_t(cfg.nclusters) * cfg.CS;
+    add(npad * L, 2); add(1, 4); add(1, 4); add(int64_t(cfg.nclusters) * npad * L, 4); add(nctas * L * L, 8);
+    add(nctas * L, 8);
+  }
+  add(int64_t(kShiftParts) * n, 8);
+  const int64_t per = int64_t(L) * L * 8;
+  int64_t np = (int64_t(8) << 20) / per;
+  np = np < 4 ? 4 : (np > 304 ? 304 : np);
+  add(n * L, 8); for (int i = 0; i < 4; ++i) add(int64_t(L) * L, 8);
+  add(L, 8); add(n * L, 8); add(np * L * L, 8); add(int64_t(L) * L, 8); add(L, 8); add(8, 4); add(k, 8); add(n * k, 8);
+  return b;
+}
+
+cudaStream_t session_stream(spca_session* s) { return s->stream; }
+
+// Launch the tensor-core blocks batched so far, without waiting.
+spca_status session_flush(spca_session* s) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  CU(cudaSetDevice(s->device));
+  return flush_tc(s);
+}
+
+// Enqueue the finalisation: sigma, V (device) and the flags word (pinned host) are written
+// when the session stream reaches them; session_flags_status interprets the flags then.
+spca_status session_finalize_async(spca_session* s, double* sigma_dev, double* V_dev, int* flags_host) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  if (s->m < 1) return fail(s, SPCA_E_NUMERIC, "no rows accumulated yet");
+  CU(cudaSetDevice(s->device));
+  st = flush_tc(s);
+  if (st != SPCA_OK) return st;
+  CU(finalize_run(s->state(), s->fin, s->opt.center ? s->m : 0, s->k, sigma_dev, V_dev, s->stream, &s->prof, s->m,
+                  s->opt.center != 0));
+  CU(cudaMemcpyAsync(flags_host, s->flags, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  return SPCA_OK;
+}
+
+spca_status session_flags_status(spca_session* s, int flags) {
+  if (flags & 2) return fail(s, SPCA_E_TIMEOUT, "a bounded device wait gave up during the pass");
+  if (flags & 1) return fail(s, SPCA_E_NUMERIC, "non-finite values (NaN/Inf) reached the sketch");
+  return SPCA_OK;
+}
+
+int session_k(const spca_session* s) { return s->k; }
+int64_t session_n(const spca_session* s) { return s->n; }
+
+}  // namespace spca
+
 extern "C" {
 
 void spca_default_options(spca_options* opt) {

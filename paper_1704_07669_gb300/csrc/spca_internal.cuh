@@ -152,4 +152,13 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k,
 
 cudaError_t centered_state(const State& s, const FinalWork& f, int64_t m, cudaStream_t st);
 
+// ---------------------------------------------------------------- hooks for the serving loop
+size_t session_footprint(int64_t n, int k, int p, int math, int64_t max_block_rows);   // 0: does not fit
+cudaStream_t session_stream(spca_session* s);
+spca_status session_flush(spca_session* s);
+spca_status session_finalize_async(spca_session* s, double* sigma_dev, double* V_dev, int* flags_host);
+spca_status session_flags_status(spca_session* s, int flags);
+int session_k(const spca_session* s);
+int64_t session_n(const spca_session* s);
+
 }  // namespace spca
