@@ -267,6 +267,100 @@ def run_form(spca, math_name, A, seed, stream, steps_arg, warmup, ws):
     return sess, step, {"ms": ms, "steps": steps, "prof": prof, "sigma": sigma_d.cpu().numpy()}
 
 
+SERVING = "64 sessions, n log-uniform in [512, 32768], l in {20, 40, 80, 140} (k = l - 10), FP32 row blocks " \
+          "of 256-4096 rows (uniform), low-rank-plus-noise per session seed, Poisson arrivals"
+
+
+def run_serving(spca, dev, seconds=4.0, load=0.5, seed=17040769 + 4):
+    """The serving loop under a stated load: first the saturation throughput (every block of a
+    fixed plan queued at once), then Poisson arrivals at `load` x that rate for `seconds`,
+    then one finalisation per session. Returns p50/p99 latencies and throughput."""
+    rng = np.random.default_rng(seed)
+    S = 64
+    ns = np.exp(rng.uniform(np.log(512), np.log(32768), S)).astype(np.int64)
+    ls = rng.choice([20, 40, 80, 140], S)
+    gen = torch.Generator(device=dev)
+    pools = []
+    for i in range(S):
+        n, l = int(ns[i]), int(ls[i])
+        gen.manual_seed(seed * 100 + i)
+        r = l + 20
+        U = torch.randn(4096, r, generator=gen, device=dev) / 64.0
+        V = torch.randn(int(n), r, generator=gen, device=dev) / math.sqrt(n)
+        sig = 10.0 ** (-torch.arange(r, device=dev, dtype=torch.float32) / 20.0)
+        A = (U * sig) @ V.T
+        A += 1e-4 / (64.0 + math.sqrt(n)) * torch.randn(4096, int(n), generator=gen, device=dev)
+        A += torch.randn(1, int(n), generator=gen, device=dev)
+        pools.append(A.contiguous())
+    torch.cuda.synchronize()
+
+    def block(i):
+        b = int(rng.integers(256, 4097))
+        return pools[i][:b], 4.0 * b * int(ns[i])
+
+    out = {"workload": SERVING, "sessions": S}
+    with spca.Server(max_block_rows=4096) as sv:
+        # saturation: 8 blocks per session queued at once (a server of its own)
+        ids = [sv.open(int(ns[i]), int(ls[i]) - 10, 10, 900 + i) for i in range(S)]
+        for i in range(S):   # admit every session before the clock starts
+            sv.wait(sv.update(ids[i], pools[i][:256]), 300.0)
+        plan = [i for i in range(S) for _ in range(8)]
+        rng.shuffle(plan)
+        t0 = time.perf_counter()
+        nbytes = 0.0
+        tickets = []
+        for i in plan:
+            rows, b = block(i)
+            nbytes += b
+            tickets.append(sv.update(ids[i], rows))
+        for t in tickets:
+            sv.wait(t, 300.0)
+        sat = nbytes / (time.perf_counter() - t0) / 1e9
+    mean_bytes = nbytes / len(plan)
+    rate = load * sat * 1e9 / mean_bytes          # requests per second
+    with spca.Server(max_block_rows=4096) as sv:
+        ids = [sv.open(int(ns[i]), int(ls[i]) - 10, 10, 900 + i) for i in range(S)]
+        for i in range(S):
+            sv.wait(sv.update(ids[i], pools[i][:256]), 300.0)
+        base = sv.stats()
+        # Poisson arrivals at `load` of saturation
+        tickets = []
+        t_next = time.perf_counter()
+        t_end = t_next + seconds
+        nbytes = 0.0
+        t0 = time.perf_counter()
+        while t_next < t_end:
+            while time.perf_counter() < t_next:
+                pass
+            i = int(rng.integers(0, S))
+            rows, b = block(i)
+            nbytes += b
+            tickets.append(sv.update(ids[i], rows))
+            t_next += rng.exponential(1.0 / rate)
+        for t in tickets:
+            sv.wait(t, 300.0)
+        wall = time.perf_counter() - t0
+        fins = []
+        for i in range(S):
+            k = int(ls[i]) - 10
+            sig_h, V_h = np.zeros(k), np.zeros((k, int(ns[i])))
+            fins.append((sig_h, V_h, sv.finalize(ids[i], sig_h, V_h)))
+        for f in fins:
+            sv.wait(f[2], 300.0)
+        st = sv.stats()
+    n_upd = st["updates_done"] - base["updates_done"]
+    out.update({"saturation_GBps": sat, "offered_load": f"{load:.0%} of saturation, Poisson, {rate:.0f} blocks/s",
+                "updates": int(n_upd), "achieved_GBps": nbytes / wall / 1e9,
+                "update_p50_ms": st["update_p50_ms"], "update_p99_ms": st["update_p99_ms"],
+                "finalize_p50_ms": st["finalize_p50_ms"], "finalize_p99_ms": st["finalize_p99_ms"],
+                "latency_note": "percentiles over the Poisson phase (plus one 256-row admission block per "
+                                "session before it) and the final finalize of every session",
+                "tc_sessions": int(sum(1 for i in range(S) if int(ls[i]) + 1 <= 64 and int(ns[i]) <= 10240)),
+                "device_budget_bytes": st["device_bytes_budget"]})
+    del pools
+    return out
+
+
 def run_ours(args):
     import paper_1704_07669_gb300 as spca
     from paper_1704_07669_gb300 import build as spca_build
@@ -331,6 +425,10 @@ def run_ours(args):
     e2e = {"value": ws * bytes_A * e2e_steps / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": bytes_A,
            "d2h_bytes_per_step": 8 * (K + K * N)}
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = run_serving(spca, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         sample_rows = min(8 * BLOCK, m)
@@ -347,7 +445,8 @@ def run_ours(args):
                        "l2": f"inputs larger than L2 ({bytes_A / 1e9:.1f} GB), no flush",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks.summary(), "kernels": kernels, "forms": forms, "peaks_source": pk["source"],
+            "clocks": clocks.summary(), "kernels": kernels, "forms": forms, "serving": serving,
+            "peaks_source": pk["source"],
             "tflops": 4.0 * m * N * (K + P) * steps * ws / (ms * 1e-3) / 1e12}
     print(json.dumps(line), flush=True)
     return 0
@@ -365,6 +464,7 @@ def main():
                     help="other forms measured on the same data and reported under 'forms' ('' for none)")
     ap.add_argument("--m", type=int, default=M, help="rows of the workload (profiling runs use fewer)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         if args.steps is None:
