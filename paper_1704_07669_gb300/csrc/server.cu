@@ -96,6 +96,7 @@ struct spca_server {
   int64_t updates_done = 0, finalizes_done = 0, admitted = 0, waiting = 0;
   double rows_bytes = 0.0, active_s = 0.0;
   bool stop = false;
+  char worker_err[256] = "";       // text of the last failed request (guarded by mu)
   std::deque<int32_t> admission;   // worker
   std::vector<cudaEvent_t> events;  // worker: free events
   std::thread worker;
@@ -347,6 +348,16 @@ void spca_server::run() {
         t.done = true;
         t.st = d.second;
       }
+      for (auto& d : done) {
+        if (d.second == SPCA_OK) continue;
+        // the failing session's own message, if it has one
+        for (const Slot& sl : slots)
+          if (sl.s && spca_last_error(sl.s)[0]) {
+            std::snprintf(worker_err, sizeof(worker_err), "%s", spca_last_error(sl.s));
+            break;
+          }
+        if (!worker_err[0]) std::snprintf(worker_err, sizeof(worker_err), "request failed (status %d)", d.second);
+      }
     }
     if (!done.empty()) cv_done.notify_all();
   }
@@ -505,7 +516,7 @@ spca_status spca_server_wait(spca_server* sv, uint64_t ticket, double timeout_s)
   }
   const spca_status st = sv->tickets[ticket].st;
   sv->tickets.erase(ticket);
-  if (st != SPCA_OK) srv_fail(st, "request failed");
+  if (st != SPCA_OK) srv_fail(st, sv->worker_err[0] ? sv->worker_err : "request failed");
   return st;
 }
 

@@ -1,0 +1,690 @@
+// The streaming pass on the tensor cores, pipelined across row tiles (Alg. 4 steps 5-7,
+// Eq. 11). Same decomposition as sketch_tc.cu - a cluster of CS CTAs splits the n features
+// (w per CTA), clusters walk 128-row tiles, the CS partials of A_hat Omega are reduced over
+// distributed shared memory - but no CTA holds its 128 x w operand tile for the whole tile:
+//  - phase 1 of tile i streams the slice of A from HBM (TMA, FP32, 64 features x 128 rows
+//    per stage), converter warps subtract c, scale and round into a 16-bit operand buffer
+//    (two 64-feature blocks), and MMA1 accumulates D1 = A_hat Omega in TMEM;
+//  - phase 2 of tile i streams the same slice again - now from L2 - once G(i) is known, and
+//    MMA2 accumulates H += A_hat^T G' per 128-feature unit;
+//  - a reduce group of four warps turns D1(i) into G'(i) (cluster reduction, rounding,
+//    Gram matrix, sums, G^T operand) while the other warps already stream tile i+1: phase 1
+//    of tile i+1 runs before phase 2 of tile i, so the latency of the reduction overlaps the
+//    loads. D1 is double-buffered in TMEM.
+// Roles (384 threads): warps 0-3 reduce group (TMEM lane quadrants 0-3), warps 4-9
+// converters, warp 10 TMA producer, warp 11 MMA issuer. CTAs signal one another with
+// mbarriers in shared memory (remote arrives at cluster scope), not with cluster-wide
+// barriers, so that no role waits for another's unrelated work. Every wait is bounded; a
+// thread that gives up sets flags[0] bit 2 and skips its later waits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <cstring>
+
+#include "spca_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace spca {
+
+namespace {
+
+constexpr int T3_ROWS = 128;
+constexpr int T3_NT = 384;
+constexpr int RG_THREADS = 128;     // warps 0-3
+constexpr int CV_WARP0 = 4, CV_WARPS = 6;
+constexpr int PROD_WARP = 10, MMA3_WARP = 11;
+constexpr int NSTAGE = 2;
+constexpr uint32_t STAGE_BYTES = T3_ROWS * 64 * 4;   // FP32: 128 rows x 64 features
+constexpr uint32_t BLOCK16 = T3_ROWS * 64 * 2;       // 16-bit: 128 rows x 64 features
+constexpr int T3_MAX_UNITS = 6;                      // w <= 768
+constexpr int GRAM3 = (64 * 65 / 2 + RG_THREADS - 1) / RG_THREADS;   // lower-triangle entries per thread
+constexpr uint32_t TMEM3_COLS = 512;
+constexpr int T3_MAX_SEGS = 48;
+
+}  // namespace
+
+struct Tc3Layout {
+  int RPC;
+  uint32_t stage, pair, om, xch, gt, pub, shift, sy, bars, total;
+};
+
+// gs: 1, or 2 when G enters MMA2 as hi + lo
+__host__ __device__ inline Tc3Layout tc3_layout(int L, int w, int CS, int gs) {
+  Tc3Layout t;
+  t.RPC = T3_ROWS / CS;
+  uint32_t o = 0;
+  t.stage = o; o += NSTAGE * STAGE_BYTES;
+  t.pair = o; o += 2 * 2 * BLOCK16;                                     // two slots of two blocks
+  t.om = o; o += 2u * static_cast<uint32_t>(L) * 128u;                  // Omega: two 64-feature chunks
+  t.xch = o; o += ((T3_ROWS * static_cast<uint32_t>(L + 4) * 4u) + 1023u) & ~1023u;
+  t.gt = o; o += 256u * static_cast<uint32_t>(L * gs);                  // G^T: gs x L x 128 rows
+  t.pub = o; o += 2u * static_cast<uint32_t>(L * gs) * (t.RPC / 8) * 16u;   // two tile parities
+  t.shift = o; o += ((static_cast<uint32_t>(w) * 4u) + 15u) & ~15u;
+  t.sy = o; o += ((static_cast<uint32_t>(t.RPC) * L * 4u) + 15u) & ~15u;
+  t.bars = o; o += 8u * 32u;
+  t.total = o + 1024u;
+  return t;
+}
+
+struct Tc3Seg {
+  int64_t m;
+  float* gout;
+  int64_t tile0;
+};
+
+struct Tc3Args {
+  CUtensorMap maps[T3_MAX_SEGS];   // per row block: FP32 rows, box 64 features x 128 rows
+  Tc3Seg seg[T3_MAX_SEGS];
+  int nseg;
+  int64_t ntiles;
+  int64_t n;
+  int l, L, w, CS;
+  int drain_every;
+  const float* shift;
+  const uint16_t* om16;
+  const float* scale;
+  float* Hpart;
+  double* gram_part;
+  double* sG_part;
+  int* flags;
+};
+
+namespace {
+
+__device__ __forceinline__ int find_seg3(const Tc3Args& a, int64_t tile) {
+  int sgi = 0;
+  while (sgi + 1 < a.nseg && a.seg[sgi + 1].tile0 <= tile) ++sgi;
+  return sgi;
+}
+
+// barrier slots
+enum {
+  B_STAGE_FULL = 0,                    // [NSTAGE]
+  B_STAGE_EMPTY = B_STAGE_FULL + NSTAGE,
+  B_PAIR_FULL = B_STAGE_EMPTY + NSTAGE,   // [2]
+  B_PAIR_EMPTY = B_PAIR_FULL + 2,
+  B_OM_FULL = B_PAIR_EMPTY + 2,
+  B_OM_EMPTY,
+  B_D1_FULL,                           // [2]
+  B_D1_EMPTY = B_D1_FULL + 2,          // [2]
+  B_G_READY = B_D1_EMPTY + 2,
+  B_MMA2_DONE,
+  B_XCH_READY,
+  B_XCH_FREE,
+  B_PUB_READY,                         // [2]
+  B_FINAL = B_PUB_READY + 2,           // the MMA issuer's last commit
+  B_COUNT
+};
+
+// tile i of this cluster is a drain tile: H leaves TMEM after its MMA2
+__device__ __forceinline__ bool drain_tile(int i, int nt, int every) { return ((i + 1) % every == 0) || (i == nt - 1); }
+
+template <int FMT>
+__global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_constant__ Tc3Args a) {
+  constexpr int GS = FMT == FMT_F16 ? 2 : 1;
+  extern __shared__ __align__(1024) uint8_t smem3[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem3) + 1023) & ~uintptr_t(1023));
+  const int L = a.L, w = a.w, CS = a.CS, l = a.l;
+  const Tc3Layout lay = tc3_layout(L, w, CS, GS);
+  const int RPC = lay.RPC, G8 = RPC / 8;
+  const float* sStage = reinterpret_cast<const float*>(base + lay.stage);
+  uint8_t* sPair = base + lay.pair;
+  uint8_t* sOm = base + lay.om;
+  float* sX = reinterpret_cast<float*>(base + lay.xch);
+  uint8_t* sGt = base + lay.gt;
+  uint4* sPub = reinterpret_cast<uint4*>(base + lay.pub);
+  float* sShift = reinterpret_cast<float*>(base + lay.shift);
+  float* sY = reinterpret_cast<float*>(base + lay.sy);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + lay.bars);
+  auto bar = [&](int i) { return su32(&bars[i]); };
+  __shared__ uint32_t tmem_sh;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const uint32_t rank = cluster_rank();
+  const uint32_t cid = cluster_id();
+  const uint32_t ncl = cluster_count();
+  const int64_t n = a.n;
+  const int64_t f0 = static_cast<int64_t>(rank) * w;
+  const int U = w / 128;
+  const int xld = L + 4;
+  const uint32_t chunk_bytes = static_cast<uint32_t>(L) * 128u;
+  const int64_t g0 = f0 / 64;
+  const int nt = cid < a.ntiles ? static_cast<int>((a.ntiles - 1 - cid) / ncl + 1) : 0;   // local tiles
+  const float op_scale = a.scale ? *a.scale : 1.f;
+  const float inv_s = 1.f / op_scale;
+
+  for (int i = tid; i < w; i += T3_NT) sShift[i] = (f0 + i < n) ? a.shift[f0 + i] : 0.f;
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(bar(B_STAGE_FULL + s), 1);
+      mbar_init(bar(B_STAGE_EMPTY + s), CV_WARPS);
+    }
+    for (int p = 0; p < 2; ++p) {
+      mbar_init(bar(B_PAIR_FULL + p), CV_WARPS);
+      mbar_init(bar(B_PAIR_EMPTY + p), 1);
+      mbar_init(bar(B_D1_FULL + p), 1);
+      mbar_init(bar(B_D1_EMPTY + p), RG_THREADS);
+      mbar_init(bar(B_PUB_READY + p), static_cast<uint32_t>(CS));
+    }
+    mbar_init(bar(B_OM_FULL), 1);
+    mbar_init(bar(B_OM_EMPTY), 1);
+    mbar_init(bar(B_G_READY), RG_THREADS);
+    mbar_init(bar(B_MMA2_DONE), 1);
+    mbar_init(bar(B_XCH_READY), static_cast<uint32_t>(CS));
+    mbar_init(bar(B_XCH_FREE), static_cast<uint32_t>(CS));
+    mbar_init(bar(B_FINAL), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_sh)),
+                 "r"(TMEM3_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();   // every peer's barriers are initialised before the first remote arrive
+  tc_fence_after();
+  const uint32_t tmem = tmem_sh;
+  const uint32_t tH = tmem + 2u * static_cast<uint32_t>(L);   // D1 buffers at columns [0, 2L)
+  bool dead = false;
+
+  if (warp == PROD_WARP) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t sc = 0, fills[NSTAGE] = {0, 0}, om_fills = 0;
+      for (int i = -1; i < nt; ++i) {
+        for (int ph = 0; ph < 2; ++ph) {
+          const int ti = ph == 0 ? i + 1 : i;
+          if (ti < 0 || ti >= nt) continue;
+          const int64_t tile = cid + static_cast<int64_t>(ti) * ncl;
+          const int sgi = find_seg3(a, tile);
+          const void* tmap = &a.maps[sgi];
+          const int32_t y0 = static_cast<int32_t>((tile - a.seg[sgi].tile0) * T3_ROWS);
+          for (int u = 0; u < U; ++u) {
+            for (int b = 0; b < 2; ++b) {
+              const int s = static_cast<int>(sc % NSTAGE);
+              if (fills[s] > 0 && !dead && !mbar_wait(bar(B_STAGE_EMPTY + s), (fills[s] - 1) & 1u)) dead = true;
+              mbar_expect_tx(bar(B_STAGE_FULL + s), STAGE_BYTES);
+              tma_load_2d(su32(sStage) + s * STAGE_BYTES, tmap, static_cast<int32_t>(f0 + 64 * (2 * u + b)), y0,
+                          bar(B_STAGE_FULL + s));
+              ++fills[s];
+              ++sc;
+            }
+            if (ph == 0) {   // Omega chunks of this unit for MMA1 (one slot: after the rows are on their way)
+              if (om_fills > 0 && !dead && !mbar_wait(bar(B_OM_EMPTY), (om_fills - 1) & 1u)) dead = true;
+              mbar_expect_tx(bar(B_OM_FULL), 2 * chunk_bytes);
+              for (int c = 0; c < 2; ++c)
+                bulk_g2s(su32(sOm) + c * chunk_bytes, a.om16 + (g0 + 2 * u + c) * static_cast<int64_t>(L) * 64,
+                         chunk_bytes, bar(B_OM_FULL));
+              ++om_fills;
+            }
+          }
+        }
+      }
+      // let the last copies land before the CTA may exit
+      for (int s = 0; s < NSTAGE; ++s)
+        if (fills[s] > 0) mbar_wait(bar(B_STAGE_FULL + s), (fills[s] - 1) & 1u);
+      if (om_fills > 0) mbar_wait(bar(B_OM_FULL), (om_fills - 1) & 1u);
+    }
+  } else if (warp >= CV_WARP0 && warp < CV_WARP0 + CV_WARPS) {
+    // ------------------------------------------------------------ converters
+    const int cw = warp - CV_WARP0;
+    uint32_t sc = 0, units = 0;
+    for (int i = -1; i < nt; ++i) {
+      for (int ph = 0; ph < 2; ++ph) {
+        const int ti = ph == 0 ? i + 1 : i;
+        if (ti < 0 || ti >= nt) continue;
+        const int64_t tile = cid + static_cast<int64_t>(ti) * ncl;
+        const int sgi = find_seg3(a, tile);
+        const int64_t row0 = (tile - a.seg[sgi].tile0) * T3_ROWS;
+        const int64_t mseg = a.seg[sgi].m;
+        for (int u = 0; u < U; ++u) {
+          const uint32_t p = units & 1u;
+          if (units >= 2 && !dead && !mbar_wait(bar(B_PAIR_EMPTY + p), ((units >> 1) - 1) & 1u)) dead = true;
+          uint8_t* slot = sPair + p * 2 * BLOCK16;
+          for (int b = 0; b < 2; ++b) {
+            const int s = static_cast<int>(sc % NSTAGE);
+            if (!dead && !mbar_wait(bar(B_STAGE_FULL + s), (sc / NSTAGE) & 1u)) dead = true;
+            const float* src = sStage + s * (STAGE_BYTES / 4);
+            const int fb = 2 * u + b;
+            // lane: features 4 (lane % 16) .. +3 of row 2 k + lane / 16; (x - c) s = fma(x, s, -c s)
+            // rounds once like the subtraction does (s is a power of two)
+            const int fl = 4 * (lane & 15);
+            const float4 sh = *reinterpret_cast<const float4*>(sShift + fb * 64 + fl);
+            const float4 cs = make_float4(-sh.x * op_scale, -sh.y * op_scale, -sh.z * op_scale, -sh.w * op_scale);
+            for (int r = 2 * cw + (lane >> 4); r < T3_ROWS; r += 2 * CV_WARPS) {
+              const float4 x = *reinterpret_cast<const float4*>(src + r * 64 + fl);
+              const bool valid = row0 + r < mseg;
+              const float v0 = valid ? fmaf(x.x, op_scale, cs.x) : 0.f;
+              const float v1 = valid ? fmaf(x.y, op_scale, cs.y) : 0.f;
+              const float v2 = valid ? fmaf(x.z, op_scale, cs.z) : 0.f;
+              const float v3 = valid ? fmaf(x.w, op_scale, cs.w) : 0.f;
+              const uint32_t off = static_cast<uint32_t>(b) * BLOCK16 + static_cast<uint32_t>(r >> 3) * 1024u +
+                                   sw128(static_cast<uint32_t>(r & 7), static_cast<uint32_t>(fl) * 2u);
+              *reinterpret_cast<uint2*>(slot + off) = make_uint2(pack2<FMT>(v0, v1), pack2<FMT>(v2, v3));
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(B_STAGE_EMPTY + s));
+            ++sc;
+          }
+          fence_async_cta();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(B_PAIR_FULL + p));
+          ++units;
+        }
+      }
+    }
+  } else if (warp == MMA3_WARP) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t id1 = idesc_fmt<FMT>(T3_ROWS, L, 0, 0);
+      const uint32_t id2 = idesc_fmt<FMT>(T3_ROWS, L, 1, 0);
+      uint32_t units = 0, om_uses = 0;
+      tc_fence_after();
+      for (int i = -1; i < nt; ++i) {
+        for (int ph = 0; ph < 2; ++ph) {
+          const int ti = ph == 0 ? i + 1 : i;
+          if (ti < 0 || ti >= nt) continue;
+          const uint32_t d1 = tmem + static_cast<uint32_t>((ti & 1) * L);
+          if (ph == 0 && ti >= 2 && !dead && !mbar_wait(bar(B_D1_EMPTY + (ti & 1)), ((ti >> 1) - 1) & 1u)) dead = true;
+          if (ph == 1 && !dead && !mbar_wait(bar(B_G_READY), static_cast<uint32_t>(ti) & 1u)) dead = true;
+          const bool zero_h = ti == 0 || drain_tile(ti - 1, nt, a.drain_every);
+          tc_fence_after();
+          for (int u = 0; u < U; ++u) {
+            const uint32_t p = units & 1u;
+            if (!dead && !mbar_wait(bar(B_PAIR_FULL + p), (units >> 1) & 1u)) dead = true;
+            const uint32_t slot = su32(sPair) + p * 2 * BLOCK16;
+            if (ph == 0) {
+              if (!dead && !mbar_wait(bar(B_OM_FULL), om_uses & 1u)) dead = true;
+              tc_fence_after();
+              if (!dead) {
+                const uint64_t dA = sdesc(slot, 16, 1024);
+                const uint64_t dB = sdesc(su32(sOm), 16, 1024);
+#pragma unroll
+                for (int b = 0; b < 2; ++b)
+#pragma unroll
+                  for (int kk = 0; kk < 4; ++kk)
+                    mma_bf16(d1, dA + ((static_cast<uint32_t>(b) * BLOCK16 + kk * 32u) >> 4),
+                             dB + ((static_cast<uint32_t>(b) * chunk_bytes + kk * 32u) >> 4), id1,
+                             (u | b | kk) != 0 ? 1u : 0u);
+              }
+              mma_commit(bar(B_OM_EMPTY));
+              ++om_uses;
+            } else {
+              tc_fence_after();
+              if (!dead) {
+                const uint64_t dA2 = sdesc(slot, BLOCK16, 1024);    // MN-major: features x rows
+                const uint64_t dB2 = sdesc(su32(sGt), 16, 1024);   // K-major: L x rows
+#pragma unroll
+                for (int ks = 0; ks < T3_ROWS / 16; ++ks)
+#pragma unroll
+                  for (int h = 0; h < GS; ++h)
+                    mma_bf16(tH + static_cast<uint32_t>(u * L), dA2 + ((static_cast<uint32_t>(ks) * 2048u) >> 4),
+                             dB2 + ((static_cast<uint32_t>(h) * 256u * static_cast<uint32_t>(L) +
+                                     static_cast<uint32_t>(ks >> 2) * chunk_bytes +
+                                     static_cast<uint32_t>(ks & 3) * 32u) >> 4),
+                             id2, (zero_h && ks == 0 && h == 0) ? 0u : 1u);
+              }
+            }
+            mma_commit(bar(B_PAIR_EMPTY + p));
+            ++units;
+          }
+          mma_commit(ph == 0 ? bar(B_D1_FULL + (ti & 1)) : bar(B_MMA2_DONE));
+        }
+      }
+      // every MMA of this CTA has completed before TMEM is released
+      mma_commit(bar(B_FINAL));
+      mbar_wait(bar(B_FINAL), 0);
+    }
+  } else {
+    // ------------------------------------------------------------ reduce group (warps 0-3)
+    const int q = warp;   // TMEM lane quadrant
+    const int LT = L * (L + 1) / 2;
+    double gram_acc[GRAM3];
+#pragma unroll
+    for (int g = 0; g < GRAM3; ++g) gram_acc[g] = 0.0;
+    double sg_acc = 0.0;
+    bool drained = false;
+    const int r0 = static_cast<int>(rank) * RPC;
+    auto drain_h = [&]() {
+      const int cpr = L / 8;
+      for (int ch = 0; ch < U * cpr; ++ch) {
+        const int mt = ch / cpr, c = (ch - mt * cpr) * 8;
+        float v[8];
+        tmem_ld8(tH + static_cast<uint32_t>(mt * L + c) + (static_cast<uint32_t>(q * 32) << 16), v);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] *= (c + e == l ? inv_s : inv_s * inv_s);   // H carries s^2, sums s
+        const int64_t feat = f0 + mt * 128 + q * 32 + lane;
+        float4* dst = reinterpret_cast<float4*>(a.Hpart + (static_cast<int64_t>(cid) * (CS * static_cast<int64_t>(w)) +
+                                                            feat) * L + c);
+        float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0;
+        if (drained) {
+          o0 = dst[0];
+          o1 = dst[1];
+        }
+        dst[0] = make_float4(o0.x + v[0], o0.y + v[1], o0.z + v[2], o0.w + v[3]);
+        dst[1] = make_float4(o1.x + v[4], o1.y + v[5], o1.z + v[6], o1.w + v[7]);
+      }
+      drained = true;
+      tc_fence_before();
+    };
+    for (int i = 0; i < nt; ++i) {
+      const int64_t tile = cid + static_cast<int64_t>(i) * ncl;
+      const int sgi = find_seg3(a, tile);
+      const int64_t row0 = (tile - a.seg[sgi].tile0) * T3_ROWS;
+      const int64_t mseg = a.seg[sgi].m;
+      // 1. own D1 partial -> exchange rows; tell every peer
+      if (!dead && !mbar_wait(bar(B_D1_FULL + (i & 1)), static_cast<uint32_t>(i >> 1) & 1u)) dead = true;
+      if (i >= 1 && !dead && !mbar_wait_cluster(bar(B_XCH_FREE), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
+      tc_fence_after();
+      {
+        const int row = q * 32 + lane;
+        const uint32_t d1 = tmem + static_cast<uint32_t>((i & 1) * L);
+        for (int c = 0; c < L; c += 8) {
+          float v[8];
+          tmem_ld8(d1 + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c), v);
+          float4* dst = reinterpret_cast<float4*>(sX + row * xld + c);
+          dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+          dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(bar(B_D1_EMPTY + (i & 1)));
+      named_bar(1, RG_THREADS);
+      if (warp == 0 && lane < CS) {
+        fence_acq_rel_cluster();
+        mbar_arrive_cluster(mapa(bar(B_XCH_READY), static_cast<uint32_t>(lane)));
+      }
+      // 2. reduce the own rows over the cluster, round, Gram and sums, publish
+      if (!dead && !mbar_wait_cluster(bar(B_XCH_READY), static_cast<uint32_t>(i) & 1u)) dead = true;
+      for (int it = tid; it < RPC * (L / 4); it += RG_THREADS) {
+        const int rr = it / (L / 4), c4 = it % (L / 4);
+        const uint32_t laddr = su32(sX + (r0 + rr) * xld + c4 * 4);
+        float4 v[16];
+#pragma unroll
+        for (int pp = 0; pp < 16; ++pp)
+          if (pp < CS) v[pp] = ld_dsmem_v4f(mapa(laddr, static_cast<uint32_t>(pp)));
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int pp = 0; pp < 16; ++pp)
+          if (pp < CS) {
+            acc.x += v[pp].x; acc.y += v[pp].y; acc.z += v[pp].z; acc.w += v[pp].w;
+          }
+        const float ac[4] = {acc.x, acc.y, acc.z, acc.w};
+        float y[4];
+        bool fin = true;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float hi = round1<FMT>(ac[e]);
+          fin = fin && isfinite(hi);
+          y[e] = GS == 2 ? hi + round1<FMT>(ac[e] - hi) : hi;
+        }
+        if (!fin) atomicOr(a.flags, 1);
+        const int cl = l - c4 * 4;
+        if (cl >= 0 && cl < 4) y[cl] = (row0 + r0 + rr < mseg) ? 1.f : 0.f;   // ones column -> column sums
+        float* dst = sY + rr * L + c4 * 4;
+        dst[0] = y[0]; dst[1] = y[1]; dst[2] = y[2]; dst[3] = y[3];
+      }
+      named_bar(1, RG_THREADS);
+      if (warp == 0 && lane < CS) {   // every peer may overwrite its exchange rows now
+        fence_acq_rel_cluster();
+        mbar_arrive_cluster(mapa(bar(B_XCH_FREE), static_cast<uint32_t>(lane)));
+      }
+      uint4* pub = sPub + (i & 1) * (GS * L * G8);
+      for (int it = tid; it < L * G8; it += RG_THREADS) {
+        const int lc = it / G8, g = it % G8;
+        const float* yv = sY + (g * 8) * L + lc;
+        float hi[8], lo[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          hi[r] = round1<FMT>(yv[r * L]);
+          lo[r] = yv[r * L] - hi[r];
+        }
+        pub[lc * G8 + g] = make_uint4(pack2<FMT>(hi[0], hi[1]), pack2<FMT>(hi[2], hi[3]), pack2<FMT>(hi[4], hi[5]),
+                                      pack2<FMT>(hi[6], hi[7]));
+        if constexpr (GS == 2) {
+          pub[(L + lc) * G8 + g] = make_uint4(pack2<FMT>(lo[0], lo[1]), pack2<FMT>(lo[2], lo[3]),
+                                              pack2<FMT>(lo[4], lo[5]), pack2<FMT>(lo[6], lo[7]));
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < GRAM3; ++g) {
+        const int e = tid + RG_THREADS * g;
+        if (e < LT) {
+          int c1 = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) - 1.f) * 0.5f);
+          while (c1 * (c1 + 1) / 2 > e) --c1;
+          while ((c1 + 1) * (c1 + 2) / 2 <= e) ++c1;
+          const int c2 = e - c1 * (c1 + 1) / 2;
+          float acc = 0.f;
+          for (int rr = 0; rr < RPC; ++rr) acc = fmaf(sY[rr * L + c1], sY[rr * L + c2], acc);
+          gram_acc[g] += static_cast<double>(acc);
+        }
+      }
+      if (tid < L) {
+        double acc = 0.0;
+        for (int rr = 0; rr < RPC; ++rr) acc += static_cast<double>(sY[rr * L + tid]);
+        sg_acc += acc;
+      }
+      if (a.seg[sgi].gout != nullptr) {
+        for (int it = tid; it < RPC * l; it += RG_THREADS) {
+          const int rr = it / l, c = it % l;
+          const int64_t grow = row0 + r0 + rr;
+          if (grow < mseg) a.seg[sgi].gout[grow * l + c] = sY[rr * L + c] * inv_s;
+        }
+      }
+      named_bar(1, RG_THREADS);
+      if (warp == 0 && lane < CS) {
+        fence_acq_rel_cluster();
+        mbar_arrive_cluster(mapa(bar(B_PUB_READY + (i & 1)), static_cast<uint32_t>(lane)));
+      }
+      // 3. the previous tile's MMA2 is done: drain H if due, then pull G'(i) into the operand
+      if (!dead && !mbar_wait_cluster(bar(B_PUB_READY + (i & 1)), static_cast<uint32_t>(i >> 1) & 1u)) dead = true;
+      if (i >= 1) {
+        if (!dead && !mbar_wait(bar(B_MMA2_DONE), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
+        tc_fence_after();
+        if (drain_tile(i - 1, nt, a.drain_every)) drain_h();
+      }
+      for (int it = tid; it < GS * L * (T3_ROWS / 8); it += RG_THREADS) {
+        const int h = it / (L * (T3_ROWS / 8));
+        const int rem = it - h * (L * (T3_ROWS / 8));
+        const int lc = rem / (T3_ROWS / 8), g = rem % (T3_ROWS / 8);
+        const int pp = g / G8, gl = g % G8;
+        const uint4 pk = ld_dsmem_v4u(
+            mapa(su32(sPub + (i & 1) * (GS * L * G8) + (h * L + lc) * G8 + gl), static_cast<uint32_t>(pp)));
+        const uint32_t off = static_cast<uint32_t>(h) * (256u * static_cast<uint32_t>(L)) +
+                             static_cast<uint32_t>(g >> 3) * chunk_bytes + static_cast<uint32_t>(lc >> 3) * 1024u +
+                             sw128(static_cast<uint32_t>(lc & 7), static_cast<uint32_t>(g & 7) * 16u);
+        *reinterpret_cast<uint4*>(sGt + off) = pk;
+      }
+      fence_async_cta();
+      mbar_arrive(bar(B_G_READY));
+    }
+    // the last tile's MMA2, then its drain
+    if (nt > 0) {
+      if (!dead && !mbar_wait(bar(B_MMA2_DONE), static_cast<uint32_t>(nt - 1) & 1u)) dead = true;
+      tc_fence_after();
+      drain_h();
+    } else {
+      for (int64_t e = tid; e < static_cast<int64_t>(w) * L; e += RG_THREADS)
+        a.Hpart[(static_cast<int64_t>(cid) * CS * w + f0) * L + e] = 0.f;
+    }
+    const int LL = L * L;
+    const int64_t cta = static_cast<int64_t>(cid) * CS + rank;
+#pragma unroll
+    for (int g = 0; g < GRAM3; ++g) {
+      const int e = tid + RG_THREADS * g;
+      if (e < LT) {
+        int c1 = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) - 1.f) * 0.5f);
+        while (c1 * (c1 + 1) / 2 > e) --c1;
+        while ((c1 + 1) * (c1 + 2) / 2 <= e) ++c1;
+        const int c2 = e - c1 * (c1 + 1) / 2;
+        const double gv = gram_acc[g] * (static_cast<double>(inv_s) * inv_s);
+        a.gram_part[cta * LL + c1 * L + c2] = gv;
+        a.gram_part[cta * LL + c2 * L + c1] = gv;
+      }
+    }
+    if (tid < L) a.sG_part[cta * L + tid] = sg_acc * inv_s;
+  }
+  if (dead) atomicOr(a.flags, 2);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM3_COLS));
+  }
+  cluster_sync();   // no CTA leaves while a peer may still read its shared memory
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+thread_local char g_tc3_reason[192] = "";
+
+}  // namespace
+
+const char* tc3_config_reason() { return g_tc3_reason; }
+
+bool tc3_config(int64_t n, int L, int fmt, TcConfig* cfg) {
+  const auto kern = fmt == FMT_F16 ? sketch_tc3_kernel<FMT_F16> : sketch_tc3_kernel<FMT_BF16>;
+  const int gs = fmt == FMT_F16 ? 2 : 1;
+  snprintf(g_tc3_reason, sizeof(g_tc3_reason), "no cluster size fits");
+  if (!encode_fn()) {
+    snprintf(g_tc3_reason, sizeof(g_tc3_reason), "cuTensorMapEncodeTiled is not available");
+    return false;
+  }
+  if (L % 16 != 0 || L > 64) {
+    snprintf(g_tc3_reason, sizeof(g_tc3_reason), "padded l = %d exceeds 64", L);
+    return false;
+  }
+  for (int CS : {1, 2, 4, 8, 16}) {
+    int64_t w = (n + CS - 1) / CS;
+    w = ((w + 127) / 128) * 128;
+    if (w / 128 > T3_MAX_UNITS || 2 * L + (w / 128) * L > static_cast<int64_t>(TMEM3_COLS)) continue;
+    const Tc3Layout lay = tc3_layout(L, static_cast<int>(w), CS, gs);
+    if (lay.total > 227u * 1024u) continue;
+    cfg->CS = CS;
+    cfg->w = static_cast<int>(w);
+    cfg->smem = lay.total;
+    // the kernel's limit is per function, shared by every session: set it to the device's
+    // maximum rather than to this configuration's need, which another session may exceed
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa0{};
+    cudaFuncGetAttributes(&fa0, kern);
+    optin -= static_cast<int>(fa0.sharedSizeBytes);   // the static shared memory counts against the limit
+    if (optin < static_cast<int>(lay.total)) continue;
+    cudaError_t e1 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(static_cast<unsigned>(CS), 1, 1);
+    lc.blockDim = dim3(T3_NT, 1, 1);
+    lc.dynamicSmemBytes = lay.total;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = static_cast<unsigned>(CS);
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &lc) != cudaSuccess || ncl < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    cfg->nclusters = ncl;
+    return true;
+  }
+  return false;
+}
+
+// One launch of the pipelined pass over the pending row blocks; false in *used when a block
+// cannot be described by a tensor map (base not 16-byte aligned or ld not a multiple of 4),
+// in which case nothing is launched and the caller takes the other kernel.
+cudaError_t tc3_pass(const State& s, const TcWork& w, const TcPending& pend, cudaStream_t st, Prof* prof,
+                     bool* used) {
+  *used = false;
+  if (pend.nseg == 0) {
+    *used = true;
+    return cudaSuccess;
+  }
+  static_assert(kTcPendingMax <= T3_MAX_SEGS, "segment capacity");
+  Tc3Args args;
+  std::memset(&args, 0, sizeof(args));
+  const TcConfig& cfg = w.cfg3;
+  int64_t tiles = 0;
+  for (int i = 0; i < pend.nseg; ++i) {
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(pend.rows[i]);
+    if ((addr & 15u) != 0 || (pend.ld[i] % 4) != 0) return cudaSuccess;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(s.n), static_cast<cuuint64_t>(pend.m[i])};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(pend.ld[i]) * 4};
+    cuuint32_t box[2] = {64, T3_ROWS};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode_fn()(&args.maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                                   const_cast<float*>(pend.rows[i]), dims, strides, box, estr,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaSuccess;
+    args.seg[i].m = pend.m[i];
+    args.seg[i].gout = pend.gout[i];
+    args.seg[i].tile0 = tiles;
+    tiles += (pend.m[i] + T3_ROWS - 1) / T3_ROWS;
+  }
+  args.nseg = pend.nseg;
+  args.ntiles = tiles;
+  args.n = s.n;
+  args.l = s.l;
+  args.L = s.L;
+  args.w = cfg.w;
+  args.CS = cfg.CS;
+  args.drain_every = w.fmt == FMT_F16 ? 2 : 4;   // 32 MMAs per TMEM accumulation of H either way
+  args.shift = s.shift;
+  args.om16 = w.om16;
+  args.scale = w.fmt == FMT_F16 ? w.scale : nullptr;
+  args.Hpart = w.Hpart;
+  args.gram_part = w.gram_part;
+  args.sG_part = w.sG_part;
+  args.flags = s.flags;
+
+  cudaLaunchConfig_t lc = {};
+  const int64_t ncl = tiles < cfg.nclusters ? tiles : cfg.nclusters;
+  lc.gridDim = dim3(static_cast<unsigned>(ncl * cfg.CS), 1, 1);
+  lc.blockDim = dim3(T3_NT, 1, 1);
+  lc.dynamicSmemBytes = cfg.smem;
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = static_cast<unsigned>(cfg.CS);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  prof->begin(SPCA_K_TC_SKETCH, st);
+  cudaError_t e = w.fmt == FMT_F16 ? cudaLaunchKernelEx(&lc, sketch_tc3_kernel<FMT_F16>, args)
+                                   : cudaLaunchKernelEx(&lc, sketch_tc3_kernel<FMT_BF16>, args);
+  prof->end(SPCA_K_TC_SKETCH, st);
+  if (e != cudaSuccess) return e;
+  *used = true;
+  e = launch_tc_finish(s, w, static_cast<int>(ncl), cfg.CS * static_cast<int64_t>(cfg.w),
+                       static_cast<int>(ncl) * cfg.CS, st, prof);
+  return e;
+}
+
+}  // namespace spca

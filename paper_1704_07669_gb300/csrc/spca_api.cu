@@ -28,6 +28,13 @@ size_t dtype_size(int dtype) {
   }
 }
 
+// features covered by the pre-swizzled Omega: the larger padding of the two kernels
+int64_t tc_npad(const TcWork& t) {
+  const int64_t a = static_cast<int64_t>(t.cfg.CS) * t.cfg.w;
+  const int64_t b = t.v3 ? static_cast<int64_t>(t.cfg3.CS) * t.cfg3.w : 0;
+  return a > b ? a : b;
+}
+
 }  // namespace
 
 namespace spca {
@@ -185,7 +192,9 @@ spca_status check_usable(spca_session* s) {
 // Launch the tensor-core pass over the row blocks batched so far.
 spca_status flush_tc(spca_session* s) {
   if (!s->tc || s->pend.nseg == 0) return SPCA_OK;
-  CU(tc_pass(s->state(), s->tcw, s->pend, s->stream, &s->prof));
+  bool used = false;
+  if (s->tcw.v3) CU(tc3_pass(s->state(), s->tcw, s->pend, s->stream, &s->prof, &used));
+  if (!used) CU(tc_pass(s->state(), s->tcw, s->pend, s->stream, &s->prof));
   s->pend.nseg = 0;
   s->pend.rows_total = 0;
   return SPCA_OK;
@@ -253,8 +262,15 @@ size_t session_footprint(int64_t n, int k, int p, int math, int64_t max_block_ro
     const int64_t groups = (mb + 31) / 32;
     add(gp_rows * L, 4); add(mb * L, 4); add(groups * L * L, 8); add(groups * L, 8); add(T * n * L, 4); add(T * n, 4);
   } else {
-    const int64_t npad = int64_t(cfg.CS) * cfg.w, nctas = int64_t(cfg.nclusters) * cfg.CS;
-    add(npad * L, 2); add(1, 4); add(1, 4); add(int64_t(cfg.nclusters) * npad * L, 4); add(nctas * L * L, 8);
+    TcWork t{};
+    t.cfg = cfg;
+    t.v3 = tc3_config(n, L, math == SPCA_MATH_FP16 ? 1 : 0, &t.cfg3);
+    const int64_t npad = tc_npad(t);
+    const int64_t hp = int64_t(cfg.nclusters) * cfg.CS * cfg.w;
+    const int64_t hp3 = t.v3 ? int64_t(t.cfg3.nclusters) * t.cfg3.CS * t.cfg3.w : 0;
+    int64_t nctas = int64_t(cfg.nclusters) * cfg.CS;
+    if (t.v3 && int64_t(t.cfg3.nclusters) * t.cfg3.CS > nctas) nctas = int64_t(t.cfg3.nclusters) * t.cfg3.CS;
+    add(npad * L, 2); add(1, 4); add(1, 4); add((hp > hp3 ? hp : hp3) * L, 4); add(nctas * L * L, 8);
     add(nctas * L, 8);
   }
   add(int64_t(kShiftParts) * n, 8);
@@ -396,12 +412,17 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   } else {
     TcWork& t = s->tcw;
     t.cfg = tcfg;
-    const int64_t npad = static_cast<int64_t>(tcfg.CS) * tcfg.w;
-    const int64_t nctas = static_cast<int64_t>(tcfg.nclusters) * tcfg.CS;
+    // the pipelined kernel where it fits (its partials and Omega padding may differ in size)
+    t.v3 = tc3_config(n, L, s->tcw.fmt, &t.cfg3);
+    const int64_t npad = tc_npad(t);
+    const int64_t hp = static_cast<int64_t>(tcfg.nclusters) * tcfg.CS * tcfg.w;
+    const int64_t hp3 = t.v3 ? static_cast<int64_t>(t.cfg3.nclusters) * t.cfg3.CS * t.cfg3.w : 0;
+    int64_t nctas = static_cast<int64_t>(tcfg.nclusters) * tcfg.CS;
+    if (t.v3 && int64_t(t.cfg3.nclusters) * t.cfg3.CS > nctas) nctas = int64_t(t.cfg3.nclusters) * t.cfg3.CS;
     CC(dalloc(&t.om16, size_t(npad) * L));
     CC(dalloc(&t.scale, 1));
     CC(dalloc(&t.scale_bits, 1));
-    CC(dalloc(&t.Hpart, size_t(tcfg.nclusters) * npad * L));
+    CC(dalloc(&t.Hpart, size_t(hp > hp3 ? hp : hp3) * L));
     CC(dalloc(&t.gram_part, size_t(nctas) * L * L));
     CC(dalloc(&t.sG_part, size_t(nctas) * L));
   }
@@ -436,7 +457,7 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   CC(cudaMemsetAsync(s->gram, 0, sizeof(double) * L * L, s->stream));
   CC(cudaMemsetAsync(s->flags, 0, sizeof(int) * 4, s->stream));
   if (s->tc) {
-    CC(launch_omega_op(s->tcw.fmt, seed, n, static_cast<int64_t>(tcfg.CS) * tcfg.w, s->l, L, s->tcw.om16, s->stream,
+    CC(launch_omega_op(s->tcw.fmt, seed, n, tc_npad(s->tcw), s->l, L, s->tcw.om16, s->stream,
                        nullptr));
   } else {
     CC(launch_omega_f32(seed, n, s->l, L, s->omega32, L, s->stream));
@@ -643,7 +664,7 @@ spca_status spca_reset(spca_session* s, uint64_t seed) {
   s->pend.nseg = 0;          // blocks batched for the previous pass are dropped with it
   s->pend.rows_total = 0;
   if (s->tc) {
-    CU(launch_omega_op(s->tcw.fmt, seed, s->n, static_cast<int64_t>(s->tcw.cfg.CS) * s->tcw.cfg.w, s->l, L, s->tcw.om16,
+    CU(launch_omega_op(s->tcw.fmt, seed, s->n, tc_npad(s->tcw), s->l, L, s->tcw.om16,
                          s->stream, &s->prof));
   } else {
     CU(launch_omega_f32(seed, s->n, s->l, L, s->omega32, L, s->stream, &s->prof));
@@ -713,10 +734,12 @@ const char* spca_describe(spca_session* s) {
   if (!s) return "";
   if (s->tc) {
     snprintf(s->desc, sizeof(s->desc),
-             "math=%s n=%lld l=%d L=%d cluster=%d w=%d clusters=%d ctas=%d smem=%u",
-             s->tcw.fmt == 1 ? "fp16" : "bf16", (long long)s->n, s->l, s->L,
-             s->tcw.cfg.CS, s->tcw.cfg.w, s->tcw.cfg.nclusters, s->tcw.cfg.nclusters * s->tcw.cfg.CS,
-             s->tcw.cfg.smem);
+             "math=%s kernel=%s n=%lld l=%d L=%d cluster=%d w=%d clusters=%d ctas=%d smem=%u",
+             s->tcw.fmt == 1 ? "fp16" : "bf16", s->tcw.v3 ? "pipelined" : "resident", (long long)s->n, s->l, s->L,
+             s->tcw.v3 ? s->tcw.cfg3.CS : s->tcw.cfg.CS, s->tcw.v3 ? s->tcw.cfg3.w : s->tcw.cfg.w,
+             s->tcw.v3 ? s->tcw.cfg3.nclusters : s->tcw.cfg.nclusters,
+             s->tcw.v3 ? s->tcw.cfg3.nclusters * s->tcw.cfg3.CS : s->tcw.cfg.nclusters * s->tcw.cfg.CS,
+             s->tcw.v3 ? s->tcw.cfg3.smem : s->tcw.cfg.smem);
   } else {
     snprintf(s->desc, sizeof(s->desc), "math=fp32 n=%lld l=%d L=%d max_block_rows=%lld row_splits<=%d",
              (long long)s->n, s->l, s->L, (long long)s->simt.mb, s->simt.T);

@@ -95,7 +95,9 @@ struct TcConfig {
 };
 
 struct TcWork {
-  TcConfig cfg;
+  TcConfig cfg;          // the kernel holding each tile's operand (sketch_tc.cu)
+  TcConfig cfg3;         // the pipelined kernel (sketch_tc3.cu), used when v3 is set
+  bool v3;
   int fmt;               // 0: BF16 operands; 1: FP16 operands on values scaled by *scale
   float* scale;          // device scalar: power-of-two operand scale (FP16 form)
   unsigned int* scale_bits;   // device scratch for the largest row norm
@@ -126,6 +128,15 @@ cudaError_t launch_omega_op(int fmt, uint64_t seed, int64_t n, int64_t npad, int
 cudaError_t launch_op_scale(const float* rows, int64_t m, int64_t n, int64_t ld, const float* shift,
                             unsigned int* bits, float* scale, cudaStream_t st, Prof* prof);
 cudaError_t tc_pass(const State& s, const TcWork& w, const TcPending& pend, cudaStream_t st, Prof* prof);
+// H partials -> FP64 state and Gram partials -> state, for a launch of ncl clusters
+cudaError_t launch_tc_finish(const State& s, const TcWork& w, int ncl, int64_t npad, int nctas, cudaStream_t st,
+                             Prof* prof);
+// the pipelined kernel: configuration, and one pass (sets *used = false, launching nothing,
+// when a row block cannot be read through a tensor map)
+bool tc3_config(int64_t n, int L, int fmt, TcConfig* cfg);
+const char* tc3_config_reason();
+cudaError_t tc3_pass(const State& s, const TcWork& w, const TcPending& pend, cudaStream_t st, Prof* prof,
+                     bool* used);
 
 // FP64 finalisation (a7). Scratch is owned by the session.
 struct FinalWork {
