@@ -195,10 +195,8 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
   const uint32_t tD1 = tmem;
   const uint32_t tH = tmem + static_cast<uint32_t>(L);
 
-  double gram_acc[GRAM_PER_THREAD];
-#pragma unroll
-  for (int i = 0; i < GRAM_PER_THREAD; ++i) gram_acc[i] = 0.0;
-  double sg_acc = 0.0;
+  F2Acc gram_acc[GRAM_PER_THREAD];
+  F2Acc sg_acc;
 
   // MMA-thread state
   uint32_t fills[OM_STAGES] = {0, 0, 0, 0};
@@ -394,7 +392,9 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
       }
       if (!fin) atomicOr(a.flags, 1);
       const int cl = l - c4 * 4;
-      if (cl >= 0 && cl < 4) y[cl] = (row0 + r0 + rr < sg.m) ? 1.f : 0.f;   // ones column -> column sums
+#pragma unroll
+      for (int e = 0; e < 4; ++e)   // ones column -> column sums
+        if (e == cl) y[e] = (row0 + r0 + rr < sg.m) ? 1.f : 0.f;
       float* dst = sY + rr * L + c4 * 4;
       dst[0] = y[0]; dst[1] = y[1]; dst[2] = y[2]; dst[3] = y[3];
     }
@@ -431,13 +431,11 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
           const int c2 = e - c1 * (c1 + 1) / 2;
           float acc = 0.f;   // G' rows in FP32 (one 16-bit value, or hi + lo)
           for (int rr = 0; rr < RPC; ++rr) acc = fmaf(sY[rr * L + c1], sY[rr * L + c2], acc);
-          gram_acc[i] += static_cast<double>(acc);
+          gram_acc[i].add(acc);
         }
       }
       if (tid < L) {
-        double acc = 0.0;
-        for (int rr = 0; rr < RPC; ++rr) acc += static_cast<double>(sY[rr * L + tid]);
-        sg_acc += acc;
+        for (int rr = 0; rr < RPC; ++rr) sg_acc.add(sY[rr * L + tid]);
       }
       if (sg.gout != nullptr) {
         for (int it = tid; it < RPC * l; it += TC_NT) {
@@ -510,13 +508,13 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
         for (int i = 0; i < 8; ++i) v[i] *= (c + i == l ? inv_s : inv_s * inv_s);   // H carries s^2, sums s
         const int64_t feat = f0 + mt * 128 + q * 32 + lane;
         float4* dst = reinterpret_cast<float4*>(a.Hpart + (static_cast<int64_t>(cid) * (CS * static_cast<int64_t>(w)) + feat) * L + c);
-        float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0;
-        if (drained) {
-          o0 = dst[0];
-          o1 = dst[1];
+        if (drained) {   // added in L2; this thread is the only writer of these entries
+          red_add_v4(reinterpret_cast<float*>(dst), v[0], v[1], v[2], v[3]);
+          red_add_v4(reinterpret_cast<float*>(dst + 1), v[4], v[5], v[6], v[7]);
+        } else {
+          dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+          dst[1] = make_float4(v[4], v[5], v[6], v[7]);
         }
-        dst[0] = make_float4(o0.x + v[0], o0.y + v[1], o0.z + v[2], o0.w + v[3]);
-        dst[1] = make_float4(o1.x + v[4], o1.y + v[5], o1.z + v[6], o1.w + v[7]);
       }
       drained = true;
       tc_fence_before();   // the loads above precede the next MMA2 that overwrites H
@@ -544,12 +542,12 @@ __global__ void __launch_bounds__(TC_NT, 1) sketch_tc_kernel(const __grid_consta
         while (c1 * (c1 + 1) / 2 > e) --c1;
         while ((c1 + 1) * (c1 + 2) / 2 <= e) ++c1;
         const int c2 = e - c1 * (c1 + 1) / 2;
-        const double g = gram_acc[i] * (static_cast<double>(inv_s) * inv_s);
+        const double g = gram_acc[i].value() * (static_cast<double>(inv_s) * inv_s);
         a.gram_part[cta * LL + c1 * L + c2] = g;
         a.gram_part[cta * LL + c2 * L + c1] = g;
       }
     }
-    if (tid < L) a.sG_part[cta * L + tid] = sg_acc * inv_s;
+    if (tid < L) a.sG_part[cta * L + tid] = sg_acc.value() * inv_s;
   }
   tc_fence_before();
   __syncthreads();

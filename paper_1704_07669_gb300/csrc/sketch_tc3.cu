@@ -38,7 +38,8 @@ constexpr int NSTAGE = 2;
 constexpr uint32_t STAGE_BYTES = T3_ROWS * 64 * 4;   // FP32: 128 rows x 64 features
 constexpr uint32_t BLOCK16 = T3_ROWS * 64 * 2;       // 16-bit: 128 rows x 64 features
 constexpr int T3_MAX_UNITS = 6;                      // w <= 768
-constexpr int GRAM3 = (64 * 65 / 2 + RG_THREADS - 1) / RG_THREADS;   // lower-triangle entries per thread
+constexpr uint32_t GT_CHUNK = 128u * 128u;   // G^T operand chunk: 128 rows (hi, lo, zero) x 64 tile rows
+constexpr int T3_GRAM_PER_THREAD = 4;        // G'^T G' entries per reduce-group thread
 constexpr uint32_t TMEM3_COLS = 512;
 constexpr int T3_MAX_SEGS = 48;
 
@@ -58,7 +59,7 @@ __host__ __device__ inline Tc3Layout tc3_layout(int L, int w, int CS, int gs) {
   t.pair = o; o += 2 * 2 * BLOCK16;                                     // two slots of two blocks
   t.om = o; o += 2u * static_cast<uint32_t>(L) * 128u;                  // Omega: two 64-feature chunks
   t.xch = o; o += ((T3_ROWS * static_cast<uint32_t>(L + 4) * 4u) + 1023u) & ~1023u;
-  t.gt = o; o += 256u * static_cast<uint32_t>(L * gs);                  // G^T: gs x L x 128 rows
+  t.gt = o; o += 2u * GT_CHUNK;   // G^T: two chunks of 64 tile rows; rows [0,L) hi, [L,2L) lo, rest 0
   t.pub = o; o += 2u * static_cast<uint32_t>(L * gs) * (t.RPC / 8) * 16u;   // two tile parities
   t.shift = o; o += ((static_cast<uint32_t>(w) * 4u) + 15u) & ~15u;
   t.sy = o; o += ((static_cast<uint32_t>(t.RPC) * L * 4u) + 15u) & ~15u;
@@ -88,7 +89,23 @@ struct Tc3Args {
   double* gram_part;
   double* sG_part;
   int* flags;
+  unsigned long long* trace;   // phase timestamps of cluster 0, CTA 0 (builds with SPCA_TC_TRACE only)
 };
+
+#ifdef SPCA_TC_TRACE
+#define T3_TRACE(ti, slot)                                                               \
+  do {                                                                                    \
+    if (rank == 0 && cid == 0 && (ti) >= 0 && (ti) < 8 && a.trace) {                      \
+      unsigned long long t_;                                                              \
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                              \
+      a.trace[(ti) * 16 + (slot)] = t_;                                                   \
+    }                                                                                     \
+  } while (0)
+#else
+#define T3_TRACE(ti, slot) \
+  do {                     \
+  } while (0)
+#endif
 
 namespace {
 
@@ -156,6 +173,9 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
   const float inv_s = 1.f / op_scale;
 
   for (int i = tid; i < w; i += T3_NT) sShift[i] = (f0 + i < n) ? a.shift[f0 + i] : 0.f;
+  // the rows of the G^T chunks that no pull writes (lo terms when not split, padding) stay 0
+  for (uint32_t i = tid; i < 2u * GT_CHUNK / 16u; i += T3_NT) reinterpret_cast<uint4*>(sGt)[i] = make_uint4(0, 0, 0, 0);
+  fence_async_cta();   // the tensor cores read these zeros
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(bar(B_STAGE_FULL + s), 1);
@@ -202,6 +222,7 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
           const int sgi = find_seg3(a, tile);
           const void* tmap = &a.maps[sgi];
           const int32_t y0 = static_cast<int32_t>((tile - a.seg[sgi].tile0) * T3_ROWS);
+          T3_TRACE(ti, ph);
           for (int u = 0; u < U; ++u) {
             for (int b = 0; b < 2; ++b) {
               const int s = static_cast<int>(sc % NSTAGE);
@@ -274,6 +295,7 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
           if (lane == 0) mbar_arrive(bar(B_PAIR_FULL + p));
           ++units;
         }
+        if (cw == 0 && lane == 0) T3_TRACE(ti, 2 + ph);
       }
     }
   } else if (warp == MMA3_WARP) {
@@ -322,8 +344,8 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
 #pragma unroll
                   for (int h = 0; h < GS; ++h)
                     mma_bf16(tH + static_cast<uint32_t>(u * L), dA2 + ((static_cast<uint32_t>(ks) * 2048u) >> 4),
-                             dB2 + ((static_cast<uint32_t>(h) * 256u * static_cast<uint32_t>(L) +
-                                     static_cast<uint32_t>(ks >> 2) * chunk_bytes +
+                             dB2 + ((static_cast<uint32_t>(h) * static_cast<uint32_t>(L) * 128u +
+                                     static_cast<uint32_t>(ks >> 2) * GT_CHUNK +
                                      static_cast<uint32_t>(ks & 3) * 32u) >> 4),
                              id2, (zero_h && ks == 0 && h == 0) ? 0u : 1u);
               }
@@ -332,6 +354,7 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
             ++units;
           }
           mma_commit(ph == 0 ? bar(B_D1_FULL + (ti & 1)) : bar(B_MMA2_DONE));
+          T3_TRACE(ti, 4 + ph);
         }
       }
       // every MMA of this CTA has completed before TMEM is released
@@ -341,11 +364,30 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
   } else {
     // ------------------------------------------------------------ reduce group (warps 0-3)
     const int q = warp;   // TMEM lane quadrant
-    const int LT = L * (L + 1) / 2;
-    double gram_acc[GRAM3];
+    F2Acc sg_acc;
+    // G'^T G' (columns < l, lower triangle): after the pull every CTA holds all 128 rows of the
+    // tile, so the cluster splits the entries - this thread takes e = rank 128 + tid + k 128 CS.
+    // Products of the 16-bit terms are exact in FP32 and summed as double-float pairs.
+    const int LTl = l * (l + 1) / 2;
+    F2Acc gram_acc[T3_GRAM_PER_THREAD];
+    int gc1[T3_GRAM_PER_THREAD], gc2[T3_GRAM_PER_THREAD];
 #pragma unroll
-    for (int g = 0; g < GRAM3; ++g) gram_acc[g] = 0.0;
-    double sg_acc = 0.0;
+    for (int k = 0; k < T3_GRAM_PER_THREAD; ++k) {
+      const int e = static_cast<int>(rank) * RG_THREADS + tid + k * RG_THREADS * CS;
+      int c1 = 0, c2 = 0;
+      if (e < LTl) {
+        c1 = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) - 1.f) * 0.5f);
+        while (c1 * (c1 + 1) / 2 > e) --c1;
+        while ((c1 + 1) * (c1 + 2) / 2 <= e) ++c1;
+        c2 = e - c1 * (c1 + 1) / 2;
+      }
+      gc1[k] = e < LTl ? c1 : -1;
+      gc2[k] = c2;
+    }
+    auto gt_off = [&](int h, int lc, int g) {
+      return static_cast<uint32_t>(g >> 3) * GT_CHUNK + static_cast<uint32_t>((h * L + lc) >> 3) * 1024u +
+             sw128(static_cast<uint32_t>(lc & 7), static_cast<uint32_t>(g & 7) * 16u);
+    };
     bool drained = false;
     const int r0 = static_cast<int>(rank) * RPC;
     auto drain_h = [&]() {
@@ -359,13 +401,13 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
         const int64_t feat = f0 + mt * 128 + q * 32 + lane;
         float4* dst = reinterpret_cast<float4*>(a.Hpart + (static_cast<int64_t>(cid) * (CS * static_cast<int64_t>(w)) +
                                                             feat) * L + c);
-        float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0;
-        if (drained) {
-          o0 = dst[0];
-          o1 = dst[1];
+        if (drained) {   // added in L2; this thread is the only writer of these entries
+          red_add_v4(reinterpret_cast<float*>(dst), v[0], v[1], v[2], v[3]);
+          red_add_v4(reinterpret_cast<float*>(dst + 1), v[4], v[5], v[6], v[7]);
+        } else {
+          dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+          dst[1] = make_float4(v[4], v[5], v[6], v[7]);
         }
-        dst[0] = make_float4(o0.x + v[0], o0.y + v[1], o0.z + v[2], o0.w + v[3]);
-        dst[1] = make_float4(o1.x + v[4], o1.y + v[5], o1.z + v[6], o1.w + v[7]);
       }
       drained = true;
       tc_fence_before();
@@ -377,6 +419,7 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
       const int64_t mseg = a.seg[sgi].m;
       // 1. own D1 partial -> exchange rows; tell every peer
       if (!dead && !mbar_wait(bar(B_D1_FULL + (i & 1)), static_cast<uint32_t>(i >> 1) & 1u)) dead = true;
+      if (tid == 0) T3_TRACE(i, 6);
       if (i >= 1 && !dead && !mbar_wait_cluster(bar(B_XCH_FREE), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
       tc_fence_after();
       {
@@ -398,20 +441,25 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
         mbar_arrive_cluster(mapa(bar(B_XCH_READY), static_cast<uint32_t>(lane)));
       }
       // 2. reduce the own rows over the cluster, round, Gram and sums, publish
+      if (tid == 0) T3_TRACE(i, 10);
       if (!dead && !mbar_wait_cluster(bar(B_XCH_READY), static_cast<uint32_t>(i) & 1u)) dead = true;
+      if (tid == 0) T3_TRACE(i, 7);
       for (int it = tid; it < RPC * (L / 4); it += RG_THREADS) {
         const int rr = it / (L / 4), c4 = it % (L / 4);
         const uint32_t laddr = su32(sX + (r0 + rr) * xld + c4 * 4);
-        float4 v[16];
-#pragma unroll
-        for (int pp = 0; pp < 16; ++pp)
-          if (pp < CS) v[pp] = ld_dsmem_v4f(mapa(laddr, static_cast<uint32_t>(pp)));
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int pp = 0; pp < 16; ++pp)
-          if (pp < CS) {
-            acc.x += v[pp].x; acc.y += v[pp].y; acc.z += v[pp].z; acc.w += v[pp].w;
-          }
+        for (int half = 0; half < 2; ++half) {   // eight peer loads in flight, then add in peer order
+          float4 v[8];
+#pragma unroll
+          for (int q8 = 0; q8 < 8; ++q8)
+            if (half * 8 + q8 < CS) v[q8] = ld_dsmem_v4f(mapa(laddr, static_cast<uint32_t>(half * 8 + q8)));
+#pragma unroll
+          for (int q8 = 0; q8 < 8; ++q8)
+            if (half * 8 + q8 < CS) {
+              acc.x += v[q8].x; acc.y += v[q8].y; acc.z += v[q8].z; acc.w += v[q8].w;
+            }
+        }
         const float ac[4] = {acc.x, acc.y, acc.z, acc.w};
         float y[4];
         bool fin = true;
@@ -423,11 +471,14 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
         }
         if (!fin) atomicOr(a.flags, 1);
         const int cl = l - c4 * 4;
-        if (cl >= 0 && cl < 4) y[cl] = (row0 + r0 + rr < mseg) ? 1.f : 0.f;   // ones column -> column sums
+#pragma unroll
+        for (int e = 0; e < 4; ++e)   // ones column -> column sums
+          if (e == cl) y[e] = (row0 + r0 + rr < mseg) ? 1.f : 0.f;
         float* dst = sY + rr * L + c4 * 4;
         dst[0] = y[0]; dst[1] = y[1]; dst[2] = y[2]; dst[3] = y[3];
       }
       named_bar(1, RG_THREADS);
+      if (tid == 0) T3_TRACE(i, 12);
       if (warp == 0 && lane < CS) {   // every peer may overwrite its exchange rows now
         fence_acq_rel_cluster();
         mbar_arrive_cluster(mapa(bar(B_XCH_FREE), static_cast<uint32_t>(lane)));
@@ -449,23 +500,16 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
                                               pack2<FMT>(lo[4], lo[5]), pack2<FMT>(lo[6], lo[7]));
         }
       }
-#pragma unroll
-      for (int g = 0; g < GRAM3; ++g) {
-        const int e = tid + RG_THREADS * g;
-        if (e < LT) {
-          int c1 = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) - 1.f) * 0.5f);
-          while (c1 * (c1 + 1) / 2 > e) --c1;
-          while ((c1 + 1) * (c1 + 2) / 2 <= e) ++c1;
-          const int c2 = e - c1 * (c1 + 1) / 2;
-          float acc = 0.f;
-          for (int rr = 0; rr < RPC; ++rr) acc = fmaf(sY[rr * L + c1], sY[rr * L + c2], acc);
-          gram_acc[g] += static_cast<double>(acc);
-        }
+      if (tid == 0) T3_TRACE(i, 13);
+      named_bar(1, RG_THREADS);
+      if (warp == 0 && lane < CS) {
+        fence_acq_rel_cluster();
+        mbar_arrive_cluster(mapa(bar(B_PUB_READY + (i & 1)), static_cast<uint32_t>(lane)));
       }
+      // sums of G and the G output of the own rows: off the path to G^T, done while the peers
+      // publish (sY stays valid until this group writes the next tile's rows)
       if (tid < L) {
-        double acc = 0.0;
-        for (int rr = 0; rr < RPC; ++rr) acc += static_cast<double>(sY[rr * L + tid]);
-        sg_acc += acc;
+        for (int rr = 0; rr < RPC; ++rr) sg_acc.add(sY[rr * L + tid]);
       }
       if (a.seg[sgi].gout != nullptr) {
         for (int it = tid; it < RPC * l; it += RG_THREADS) {
@@ -474,32 +518,67 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
           if (grow < mseg) a.seg[sgi].gout[grow * l + c] = sY[rr * L + c] * inv_s;
         }
       }
-      named_bar(1, RG_THREADS);
-      if (warp == 0 && lane < CS) {
-        fence_acq_rel_cluster();
-        mbar_arrive_cluster(mapa(bar(B_PUB_READY + (i & 1)), static_cast<uint32_t>(lane)));
-      }
+      if (tid == 0) T3_TRACE(i, 14);
       // 3. the previous tile's MMA2 is done: drain H if due, then pull G'(i) into the operand
+      if (tid == 0) T3_TRACE(i, 11);
       if (!dead && !mbar_wait_cluster(bar(B_PUB_READY + (i & 1)), static_cast<uint32_t>(i >> 1) & 1u)) dead = true;
+      if (tid == 0) T3_TRACE(i, 8);
       if (i >= 1) {
         if (!dead && !mbar_wait(bar(B_MMA2_DONE), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
         tc_fence_after();
         if (drain_tile(i - 1, nt, a.drain_every)) drain_h();
       }
-      for (int it = tid; it < GS * L * (T3_ROWS / 8); it += RG_THREADS) {
-        const int h = it / (L * (T3_ROWS / 8));
-        const int rem = it - h * (L * (T3_ROWS / 8));
-        const int lc = rem / (T3_ROWS / 8), g = rem % (T3_ROWS / 8);
-        const int pp = g / G8, gl = g % G8;
-        const uint4 pk = ld_dsmem_v4u(
-            mapa(su32(sPub + (i & 1) * (GS * L * G8) + (h * L + lc) * G8 + gl), static_cast<uint32_t>(pp)));
-        const uint32_t off = static_cast<uint32_t>(h) * (256u * static_cast<uint32_t>(L)) +
-                             static_cast<uint32_t>(g >> 3) * chunk_bytes + static_cast<uint32_t>(lc >> 3) * 1024u +
-                             sw128(static_cast<uint32_t>(lc & 7), static_cast<uint32_t>(g & 7) * 16u);
-        *reinterpret_cast<uint4*>(sGt + off) = pk;
+      {
+        const int total = GS * L * (T3_ROWS / 8);
+        for (int it0 = tid; it0 < total; it0 += 4 * RG_THREADS) {   // four remote loads in flight
+          uint4 pk[4];
+          uint32_t off[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int it = it0 + j * RG_THREADS;
+            off[j] = 0xFFFFFFFFu;
+            if (it < total) {
+              const int h = it / (L * (T3_ROWS / 8));
+              const int rem = it - h * (L * (T3_ROWS / 8));
+              const int lc = rem / (T3_ROWS / 8), g = rem % (T3_ROWS / 8);
+              const int pp = g / G8, gl = g % G8;
+              pk[j] = ld_dsmem_v4u(
+                  mapa(su32(sPub + (i & 1) * (GS * L * G8) + (h * L + lc) * G8 + gl), static_cast<uint32_t>(pp)));
+              off[j] = static_cast<uint32_t>(g >> 3) * GT_CHUNK + static_cast<uint32_t>((h * L + lc) >> 3) * 1024u +
+                       sw128(static_cast<uint32_t>(lc & 7), static_cast<uint32_t>(g & 7) * 16u);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (off[j] != 0xFFFFFFFFu) *reinterpret_cast<uint4*>(sGt + off[j]) = pk[j];
+        }
       }
       fence_async_cta();
       mbar_arrive(bar(B_G_READY));
+      if (tid == 0) T3_TRACE(i, 9);
+      named_bar(1, RG_THREADS);   // the whole G^T tile is in place
+      // this thread's entries of G'^T G' over the tile's 128 rows
+#pragma unroll
+      for (int k = 0; k < T3_GRAM_PER_THREAD; ++k) {
+        if (gc1[k] < 0) continue;
+        for (int g = 0; g < T3_ROWS / 8; ++g) {
+          float x1[GS][8], x2[GS][8];
+#pragma unroll
+          for (int h = 0; h < GS; ++h) {
+            unpack8<FMT>(*reinterpret_cast<const uint4*>(sGt + gt_off(h, gc1[k], g)), x1[h]);
+            unpack8<FMT>(*reinterpret_cast<const uint4*>(sGt + gt_off(h, gc2[k], g)), x2[h]);
+          }
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            gram_acc[k].add(x1[0][r] * x2[0][r]);
+            if constexpr (GS == 2) {
+              gram_acc[k].add(x1[0][r] * x2[1][r]);
+              gram_acc[k].add(x1[1][r] * x2[0][r]);
+              gram_acc[k].add(x1[1][r] * x2[1][r]);
+            }
+          }
+        }
+      }
     }
     // the last tile's MMA2, then its drain
     if (nt > 0) {
@@ -512,20 +591,19 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
     }
     const int LL = L * L;
     const int64_t cta = static_cast<int64_t>(cid) * CS + rank;
+    for (int e = tid; e < LL; e += RG_THREADS) a.gram_part[cta * LL + e] = 0.0;
+    named_bar(1, RG_THREADS);
+    {
+      const double s2 = static_cast<double>(inv_s) * inv_s;
 #pragma unroll
-    for (int g = 0; g < GRAM3; ++g) {
-      const int e = tid + RG_THREADS * g;
-      if (e < LT) {
-        int c1 = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) - 1.f) * 0.5f);
-        while (c1 * (c1 + 1) / 2 > e) --c1;
-        while ((c1 + 1) * (c1 + 2) / 2 <= e) ++c1;
-        const int c2 = e - c1 * (c1 + 1) / 2;
-        const double gv = gram_acc[g] * (static_cast<double>(inv_s) * inv_s);
-        a.gram_part[cta * LL + c1 * L + c2] = gv;
-        a.gram_part[cta * LL + c2 * L + c1] = gv;
+      for (int k = 0; k < T3_GRAM_PER_THREAD; ++k) {
+        if (gc1[k] < 0) continue;
+        const double v = gram_acc[k].value() * s2;
+        a.gram_part[cta * LL + gc1[k] * L + gc2[k]] = v;
+        a.gram_part[cta * LL + gc2[k] * L + gc1[k]] = v;
       }
     }
-    if (tid < L) a.sG_part[cta * L + tid] = sg_acc * inv_s;
+    if (tid < L) a.sG_part[cta * L + tid] = sg_acc.value() * inv_s;
   }
   if (dead) atomicOr(a.flags, 2);
   tc_fence_before();
@@ -572,7 +650,10 @@ bool tc3_config(int64_t n, int L, int fmt, TcConfig* cfg) {
   for (int CS : {1, 2, 4, 8, 16}) {
     int64_t w = (n + CS - 1) / CS;
     w = ((w + 127) / 128) * 128;
+    // TMEM: two D1 buffers and H (w / 128 tiles of L columns); the cluster's 128 CS reduce
+    // threads take at most T3_GRAM_PER_THREAD entries of G'^T G' each
     if (w / 128 > T3_MAX_UNITS || 2 * L + (w / 128) * L > static_cast<int64_t>(TMEM3_COLS)) continue;
+    if (static_cast<int64_t>(CS) * RG_THREADS * T3_GRAM_PER_THREAD < static_cast<int64_t>(L) * (L + 1) / 2) continue;
     const Tc3Layout lay = tc3_layout(L, static_cast<int>(w), CS, gs);
     if (lay.total > 227u * 1024u) continue;
     cfg->CS = CS;
@@ -662,6 +743,13 @@ cudaError_t tc3_pass(const State& s, const TcWork& w, const TcPending& pend, cud
   args.gram_part = w.gram_part;
   args.sG_part = w.sG_part;
   args.flags = s.flags;
+  args.trace = nullptr;
+#ifdef SPCA_TC_TRACE
+  static unsigned long long* dtrace = nullptr;
+  if (!dtrace) cudaMalloc(&dtrace, sizeof(unsigned long long) * 8 * 16);
+  cudaMemsetAsync(dtrace, 0, sizeof(unsigned long long) * 8 * 16, st);
+  args.trace = dtrace;
+#endif
 
   cudaLaunchConfig_t lc = {};
   const int64_t ncl = tiles < cfg.nclusters ? tiles : cfg.nclusters;
@@ -682,6 +770,23 @@ cudaError_t tc3_pass(const State& s, const TcWork& w, const TcPending& pend, cud
   prof->end(SPCA_K_TC_SKETCH, st);
   if (e != cudaSuccess) return e;
   *used = true;
+#ifdef SPCA_TC_TRACE
+  {
+    unsigned long long h[8 * 16];
+    cudaStreamSynchronize(st);
+    cudaMemcpy(h, dtrace, sizeof(h), cudaMemcpyDeviceToHost);
+    const unsigned long long t0 = h[0];
+    static const char* names[15] = {"prodP1", "prodP2", "cvP1end", "cvP2end", "mma1", "mma2", "rgD1",
+                                    "rgXchRdy", "rgPubRdy", "rgG", "rgXchSent", "rgPubSent", "rgReduced",
+                                    "rgPublished", "rgGramDone"};
+    for (int t = 0; t < 8; ++t) {
+      fprintf(stderr, "tc3 tile %d:", t);
+      for (int p = 0; p < 15; ++p)
+        if (h[t * 16 + p]) fprintf(stderr, " %s=%.1f", names[p], (double)(h[t * 16 + p] - t0) / 1000.0);
+      fprintf(stderr, " us\n");
+    }
+  }
+#endif
   e = launch_tc_finish(s, w, static_cast<int>(ncl), cfg.CS * static_cast<int64_t>(cfg.w),
                        static_cast<int>(ncl) * cfg.CS, st, prof);
   return e;

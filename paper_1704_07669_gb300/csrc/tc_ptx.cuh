@@ -10,7 +10,7 @@
 namespace spca {
 namespace {
 
-constexpr uint32_t WAIT_LIMIT = 1u << 20;   // tries per wait; a thread that gives up skips later waits
+constexpr uint32_t WAIT_LIMIT = 1u << 21;   // polls per wait; a thread that gives up skips later waits
 
 // ------------------------------------------------------------------ PTX wrappers
 
@@ -61,9 +61,20 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Waits poll a few times, then back off with growing sleeps (up to ~0.5 us): warps that wait
+// long - converters behind a cluster reduction, the MMA issuer behind G - must not take the
+// issue slots and shared-memory bandwidth the working warps need. Bounded: at most
+// WAIT_LIMIT polls (well under a second in all).
+__device__ __forceinline__ uint32_t wait_backoff(uint32_t it) {
+  if (it < 32) return 0;
+  const uint32_t k = (it - 32) >> 3;
+  return 32u << (k < 4 ? k : 4);
+}
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
-  for (uint32_t it = 0; it < WAIT_LIMIT; ++it)
+  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
     if (mbar_try(a, parity)) return true;
+    if (const uint32_t ns = wait_backoff(it)) __nanosleep(ns);
+  }
   return false;
 }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
@@ -151,10 +162,50 @@ __device__ __forceinline__ float round1(float x) {
   else return __bfloat162float(__float2bfloat16_rn(x));
 }
 
+// the eight 16-bit values of a 16-byte chunk as floats
+template <int FMT>
+__device__ __forceinline__ void unpack8(uint4 v, float* out) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if constexpr (FMT == FMT_F16) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
+      out[2 * i] = f.x;
+      out[2 * i + 1] = f.y;
+    } else {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
+      out[2 * i] = f.x;
+      out[2 * i + 1] = f.y;
+    }
+  }
+}
+
 // instruction descriptor for the operand format: kind::f16, FP32 accumulate
 template <int FMT>
 __host__ __device__ constexpr uint32_t idesc_fmt(int M, int N, int a_mn, int b_mn) {
   return FMT == FMT_F16 ? (idesc_bf16(M, N, a_mn, b_mn) & ~((7u << 7) | (7u << 10))) : idesc_bf16(M, N, a_mn, b_mn);
+}
+
+// Double-float accumulator (hi + lo, Knuth's TwoSum): the per-tile sums of the Gram matrix and
+// of G stay on the FP32 pipe. FP64 arithmetic on this GPU is slow enough that a few FP64
+// adds per tile per thread stalled a whole warp group for microseconds.
+struct F2Acc {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = hi + x;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo += e;
+  }
+  __device__ __forceinline__ double value() const { return static_cast<double>(hi) + static_cast<double>(lo); }
+};
+
+// *p += v (four floats) in L2, without returning anything: the adding thread does not wait
+// for the old value
+__device__ __forceinline__ void red_add_v4(float* p, float a0, float a1, float a2, float a3) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a0), "f"(a1), "f"(a2), "f"(a3)
+               : "memory");
 }
 
 // ---- used by the pipelined kernel: tensor-map loads, cluster-scope mbarrier signalling
@@ -181,8 +232,10 @@ __device__ __forceinline__ bool mbar_try_cluster(uint32_t a, uint32_t parity) {
   return ok != 0;
 }
 __device__ __forceinline__ bool mbar_wait_cluster(uint32_t a, uint32_t parity) {
-  for (uint32_t it = 0; it < WAIT_LIMIT; ++it)
+  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
     if (mbar_try_cluster(a, parity)) return true;
+    if (const uint32_t ns = wait_backoff(it)) __nanosleep(ns);
+  }
   return false;
 }
 __device__ __forceinline__ void fence_acq_rel_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
