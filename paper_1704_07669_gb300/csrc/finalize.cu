@@ -15,8 +15,8 @@
 //     lam > l eps lam_max, and set T = diag(lam_r)^-1/2 W_r^T.
 //  3. Bt = H_bar T^T (n x r), i.e. B^T, and C = B B^T (r x r) in one sweep over n.
 //  4. SVD of B through C = W_B diag(sigma^2) W_B^T (Jacobi with the parallel
-//     ordering: an FP32 solve, then an FP64 polish of W_B^T C W_B, see
-//     eig_f32_kernel); V = B^T W_B diag(1/sigma), the leading k columns
+//     ordering: an FP32 solve, then a polish of W_B^T C W_B with an FP64 diagonal,
+//     see eig_f32_kernel); V = B^T W_B diag(1/sigma), the leading k columns
 //     (Alg. 4 steps 17-19).
 //  5. Each v_i scaled by +-1 so that its largest-magnitude entry (lowest index
 //     on ties) is positive.
@@ -58,16 +58,32 @@ __global__ void center_gram_kernel(const double* __restrict__ gram, const double
 }
 
 // For a block of BT_ROWS features: Bt[j][i] = sum_c T[i][c] Hbar[j][c] (i < r), and the
-// partial C_p = sum_j Bt[j]^T Bt[j] of this block (lower triangle, ld L).
+// partial C_p = sum_j Bt[j]^T Bt[j] of this block (lower triangle, ld L). FP64 issues at a
+// small fraction of the FP32 rate here, so the kernel is built around the FP64 pipe: T^T is
+// staged in shared memory (when it fits) so that lanes over i read consecutive words, each
+// thread keeps BT_ROWS / 4 independent accumulators, and the lower triangle of C_p is
+// packed so that no lane idles over the upper half.
 __global__ void __launch_bounds__(256) bt_and_c_kernel(const double* __restrict__ Hbar, const double* __restrict__ T,
                                                        const int* __restrict__ info, int64_t n, int l, int L,
-                                                       double* __restrict__ Bt, double* __restrict__ Cpart) {
+                                                       int stage_t, double* __restrict__ Bt,
+                                                       double* __restrict__ Cpart) {
   extern __shared__ double sm[];
   double* sH = sm;                  // BT_ROWS x L
   double* sB = sm + BT_ROWS * L;    // BT_ROWS x L
+  double* sT = sB + BT_ROWS * L;    // L x L when staged: sT[c * L + i] = T[i][c]
+  constexpr int G = 256 / 64;       // row groups; thread = (row group, column i mod 64)
+  constexpr int RPT = BT_ROWS / G;  // rows per thread
   const int r = info[0];
+  const int tri = r * (r + 1) / 2;
   double* out = Cpart + static_cast<int64_t>(blockIdx.x) * L * L;
   for (int e = threadIdx.x; e < L * L; e += blockDim.x) out[e] = 0.0;
+  if (stage_t) {
+    for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
+      const int i = e / L, c = e - i * L;
+      sT[c * L + i] = T[e];
+    }
+  }
+  const int grp = threadIdx.x >> 6, il = threadIdx.x & 63;
   const int64_t nblk = (n + BT_ROWS - 1) / BT_ROWS;
   for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
     const int64_t j0 = blk * BT_ROWS;
@@ -77,60 +93,128 @@ __global__ void __launch_bounds__(256) bt_and_c_kernel(const double* __restrict_
       sH[e] = (j < n) ? Hbar[j * L + e % L] : 0.0;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < BT_ROWS * L; e += blockDim.x) {
-      const int jr = e / L, i = e % L;
-      double acc = 0.0;
+    for (int i = il; i < L; i += 64) {
+      double acc[RPT];
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) acc[u] = 0.0;
       if (i < r) {
-        const double* t = T + static_cast<int64_t>(i) * L;
-        const double* h = sH + jr * L;
-        for (int c = 0; c < l; ++c) acc = fma(__ldg(t + c), h[c], acc);
+        for (int c = 0; c < l; ++c) {
+          const double t = stage_t ? sT[c * L + i] : __ldg(T + static_cast<int64_t>(i) * L + c);
+#pragma unroll
+          for (int u = 0; u < RPT; ++u) acc[u] = fma(t, sH[(grp + G * u) * L + c], acc[u]);
+        }
       }
-      sB[e] = acc;
-      const int64_t j = j0 + jr;
-      if (j < n) Bt[j * L + i] = acc;
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        const int jr = grp + G * u;
+        sB[jr * L + i] = acc[u];
+        const int64_t j = j0 + jr;
+        if (j < n) Bt[j * L + i] = acc[u];
+      }
     }
     __syncthreads();
-    // this block's own partial, accumulated over its feature blocks in a fixed order
-    for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
-      const int a = e / L, b = e % L;
-      if (a < r && b <= a) {
-        double acc = out[e];
+    // this block's own partial over the packed lower triangle, a fixed order per entry
+    for (int t = threadIdx.x; t < tri; t += blockDim.x) {
+      int a = static_cast<int>((sqrtf(8.f * static_cast<float>(t) + 1.f) - 1.f) * 0.5f);
+      while (a * (a + 1) / 2 > t) --a;
+      while ((a + 1) * (a + 2) / 2 <= t) ++a;
+      const int b = t - a * (a + 1) / 2;
+      double acc0 = 0.0, acc1 = 0.0;
 #pragma unroll 8
-        for (int jr = 0; jr < BT_ROWS; ++jr) acc = fma(sB[jr * L + a], sB[jr * L + b], acc);
-        out[e] = acc;
+      for (int jr = 0; jr < BT_ROWS; jr += 2) {
+        acc0 = fma(sB[jr * L + a], sB[jr * L + b], acc0);
+        acc1 = fma(sB[(jr + 1) * L + a], sB[(jr + 1) * L + b], acc1);
       }
+      out[a * L + b] += acc0 + acc1;
     }
   }
 }
 
-// C = sum over blocks (fixed order), symmetric fill from the lower triangle.
-__global__ void c_reduce_kernel(const double* __restrict__ Cpart, int parts, int L, double* __restrict__ C) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= L * L) return;
-  const int a = e / L, b = e % L;
-  const int src = a >= b ? e : (b * L + a);
+// C = sum over blocks (fixed order), symmetric fill from the lower triangle. A block takes
+// 32 entries; its warps sum interleaved subsets of the partials, combined in warp order.
+constexpr int CR_T = 256;
+__global__ void __launch_bounds__(CR_T) c_reduce_kernel(const double* __restrict__ Cpart, int parts, int L,
+                                                        double* __restrict__ C) {
+  __shared__ double acc_w[CR_T / 32][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
   double acc = 0.0;
-  for (int p = 0; p < parts; ++p) acc += Cpart[static_cast<int64_t>(p) * L * L + src];
-  C[e] = acc;
+  if (e < L * L) {
+    const int a = e / L, b = e % L;
+    const int src = a >= b ? e : (b * L + a);
+    for (int p = warp; p < parts; p += CR_T / 32) acc += Cpart[static_cast<int64_t>(p) * L * L + src];
+  }
+  acc_w[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && e < L * L) {
+    double t = 0.0;
+    for (int w = 0; w < CR_T / 32; ++w) t += acc_w[w][lane];
+    C[e] = t;
+  }
 }
 
-// V[j][i] (column-major output, ld n) = sum_c Bt[j][c] W[c][i] / sigma_i, i < k.
-__global__ void form_v_kernel(const double* __restrict__ Bt, const double* __restrict__ W,
-                              const double* __restrict__ sig, const int* __restrict__ info, int64_t n, int k, int L,
-                              double* __restrict__ V) {
+// V[j][i] (column-major output, ld n) = sum_c Bt[j][c] W[c][i] / sigma_i, i < k. A block
+// takes FV_ROWS rows j at a time (staged in shared memory, padded against bank conflicts)
+// and, with STAGE_W, the leading r x k block of W too (else W is read through L1, each
+// warp reading one address at a time); thread (row j, output group) keeps up to FV_ACC
+// independent FP64 accumulators.
+constexpr int FV_ROWS = 64;
+constexpr int FV_ACC = 13;
+template <bool STAGE_W>
+__global__ void __launch_bounds__(256) form_v_kernel(const double* __restrict__ Bt, const double* __restrict__ W,
+                                                     const double* __restrict__ sig, const int* __restrict__ info,
+                                                     int64_t n, int k, int L, double* __restrict__ V) {
+  extern __shared__ double fsm[];
   const int r = info[0];
-  const int64_t total = n * k;
-  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
-       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int i = static_cast<int>(idx / n);
-    const int64_t j = idx % n;
-    double acc = 0.0;
-    if (i < r && sig[i] > 0.0) {
-      const double* b = Bt + j * L;
-      for (int c = 0; c < r; ++c) acc = fma(b[c], W[static_cast<int64_t>(c) * L + i], acc);
-      acc /= sig[i];
+  const int kk = k < r ? k : r;                     // outputs i >= r are zero
+  const int ld = r + 1;
+  double* sBt = fsm;                                // FV_ROWS x (r + 1)
+  double* sInv = fsm + FV_ROWS * ld;                // kk
+  double* sW = sInv + kk;                           // r x kk when staged
+  for (int i = threadIdx.x; i < kk; i += blockDim.x) sInv[i] = sig[i] > 0.0 ? 1.0 / sig[i] : 0.0;
+  if (STAGE_W) {
+    for (int e = threadIdx.x; e < r * kk; e += blockDim.x) {
+      const int c = e / kk, i = e - c * kk;
+      sW[e] = W[c * L + i];
     }
-    V[idx] = acc;
+  }
+  constexpr int G = 256 / FV_ROWS;
+  const int jr = threadIdx.x % FV_ROWS, grp = threadIdx.x / FV_ROWS;
+  for (int64_t j0 = static_cast<int64_t>(blockIdx.x) * FV_ROWS; j0 < n; j0 += static_cast<int64_t>(gridDim.x) * FV_ROWS) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < FV_ROWS * r; e += blockDim.x) {
+      const int jj = e / r, c = e - jj * r;
+      const int64_t j = j0 + jj;
+      sBt[jj * ld + c] = (j < n) ? Bt[j * L + c] : 0.0;
+    }
+    __syncthreads();
+    const int64_t j = j0 + jr;
+    for (int i0 = grp; i0 < kk; i0 += G * FV_ACC) {   // outputs i0, i0 + G, ... (FV_ACC of them)
+      const int nu = (kk - i0 + G - 1) / G;          // live accumulators (the same in a warp)
+      double acc[FV_ACC];
+#pragma unroll
+      for (int u = 0; u < FV_ACC; ++u) acc[u] = 0.0;
+      for (int c = 0; c < r; ++c) {
+        const double b = sBt[jr * ld + c];
+#pragma unroll
+        for (int u = 0; u < FV_ACC; ++u) {
+          const int i = i0 + G * u;
+          if (u < nu) acc[u] = fma(b, STAGE_W ? sW[c * kk + i] : __ldg(W + c * L + i), acc[u]);
+        }
+      }
+      if (j < n) {
+#pragma unroll
+        for (int u = 0; u < FV_ACC; ++u) {
+          const int i = i0 + G * u;
+          if (u < nu) V[static_cast<int64_t>(i) * n + j] = acc[u] * sInv[i];
+        }
+      }
+    }
+  }
+  if (kk < k) {   // columns beyond the rank
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < (k - kk) * n;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x)
+      V[static_cast<int64_t>(kk) * n + idx] = 0.0;
   }
 }
 
@@ -168,26 +252,47 @@ __global__ void __launch_bounds__(SIGN_T) sign_fix_kernel(double* __restrict__ V
 
 // -------------------------------------------------------------- one-block dense helpers
 // Matrices are d x d blocks with leading dimension ld, in shared or global memory.
+// On this GPU FP64 instructions issue at a small fraction of the FP32 rate and share
+// one pipe per SM, so these helpers keep FP64 arithmetic to the work that needs it.
 
+// Block-wide sum of v (every thread gets the same value, summed in the same order);
+// red holds >= blockDim.x / 32 doubles.
 __device__ double blk_sum(double v, double* red) {
-  red[threadIdx.x] = v;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
-  }
-  const double out = red[0];
+  double s = 0.0;
+  for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += red[w];
   __syncthreads();
-  return out;
+  return s;
 }
 
-// Precision-generic math: the float overloads must not fall back to FP64 (slow here).
-__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float tabs(float x) { return fabsf(x); }
-__device__ __forceinline__ double tabs(double x) { return fabs(x); }
-__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
-__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
+// The same for two FP32 sums at once; red holds >= blockDim.x / 16 floats.
+__device__ void blk_sum2(float& a, float& b, float* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[2 * (threadIdx.x >> 5)] = a;
+    red[2 * (threadIdx.x >> 5) + 1] = b;
+  }
+  __syncthreads();
+  a = 0.f;
+  b = 0.f;
+  for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
+    a += red[2 * w];
+    b += red[2 * w + 1];
+  }
+  __syncthreads();
+}
+
+// 2^-e with 2^e <= x < 2^(e+1): an exact scale that brings x to [1, 2) (1 for x <= 0 or
+// non-finite x).
+__device__ double pow2_scale(double x) {
+  if (!(x > 0.0) || !isfinite(x)) return 1.0;
+  return ldexp(1.0, -ilogb(x));
+}
 
 // Jacobi rotation (c, s) that annihilates a_pq of [[a_pp, a_pq], [a_pq, a_qq]]. The angle is
 // found in FP32 (an angle off by 1e-7 relative still shrinks a_pq by seven digits per
@@ -206,223 +311,328 @@ __device__ __forceinline__ void jacobi_rotation(T app, T aqq, T apq, T& c, T& s)
   s = t * y;
 }
 
-// In-place Cholesky: the lower triangle of A becomes L1 (A = L1 L1^T). False if a pivot <= tol.
-template <typename T>
-__device__ bool blk_cholesky(T* A, int d, int ld, double tol) {
-  __shared__ int ok;
-  if (threadIdx.x == 0) ok = 1;
-  __syncthreads();
-  for (int k = 0; k < d; ++k) {
-    if (threadIdx.x == 0) {
-      const T v = A[k * ld + k];
-      if (!(static_cast<double>(v) > tol)) ok = 0;
-      else A[k * ld + k] = tsqrt(v);
-    }
-    __syncthreads();
-    if (!ok) return false;
-    const T dk = A[k * ld + k];
-    for (int i = k + 1 + threadIdx.x; i < d; i += blockDim.x) A[i * ld + k] /= dk;
-    __syncthreads();
-    const int rem = d - k - 1;
-    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
-      if (j <= i) A[i * ld + j] -= A[i * ld + k] * A[j * ld + k];
-    }
-    __syncthreads();
-  }
-  return true;
+// FP32 rotation for the FP32 solve: the same formulas with the two divisions taken by the
+// fast reciprocal (|2 a_pq| is far from the range where it loses accuracy; an overflowing
+// theta gives t = 0, no rotation) and one Newton step on c.
+__device__ __forceinline__ void jacobi_rotation32(float app, float aqq, float apq, float& c, float& s) {
+  const float theta = __fdividef(aqq - app, 2.f * apq);
+  const float t = __fdividef(theta >= 0.f ? 1.f : -1.f, fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+  const float x = fmaf(t, t, 1.f);
+  float y = rsqrtf(x);
+  y = y * fmaf(-0.5f * x * y, y, 1.5f);
+  c = y;
+  s = t * y;
 }
 
-// Linv = inverse of the lower triangle of Lm (strict upper part of Linv zeroed).
-template <typename T>
-__device__ void blk_trinv_lower(const T* Lm, T* Linv, int d, int ld) {
-  for (int e = threadIdx.x; e < d * d; e += blockDim.x) Linv[(e / d) * ld + e % d] = T(0);
-  __syncthreads();
-  for (int c = threadIdx.x; c < d; c += blockDim.x) {
-    for (int i = c; i < d; ++i) {
-      T acc = (i == c) ? T(1) : T(0);
-      for (int j = c; j < i; ++j) acc -= Lm[i * ld + j] * Linv[j * ld + c];
-      Linv[i * ld + c] = acc / Lm[i * ld + i];
-    }
+// Pair pi of round `round` in the round-robin (parallel) ordering of de = m + 1 indices:
+// every round pairs each index exactly once, and m rounds visit every pair once.
+__device__ __forceinline__ void rr_pair(int round, int pi, int m, int& p, int& q) {
+  if (pi == 0) {
+    p = m;
+    q = round;
+  } else {
+    p = round + pi;
+    if (p >= m) p -= m;
+    q = round - pi;
+    if (q < 0) q += m;
   }
-  __syncthreads();
+  if (p > q) { const int t = p; p = q; q = t; }
 }
 
-// One-warp Cholesky (right-looking, lanes over rows) and inverse of the factor, for the
-// small FP32 factorisations: a warp needs no block barriers between the d steps.
-template <typename T>
-__device__ bool warp_cholesky(T* A, int d, int ld, T tol) {
-  const int lane = threadIdx.x & 31;
-  for (int k = 0; k < d; ++k) {
-    const T v = A[k * ld + k];
-    if (!(v > tol)) return false;   // the same value in every lane: a uniform exit
-    const T dk = tsqrt(v);
-    const T inv = T(1) / dk;
-    __syncwarp();
-    if (lane == 0) A[k * ld + k] = dk;
-    for (int i = k + 1 + lane; i < d; i += 32) A[i * ld + k] *= inv;
-    __syncwarp();
-    for (int i = k + 1 + lane; i < d; i += 32) {
-      const T lik = A[i * ld + k];
-      for (int j = k + 1; j <= i; ++j) A[i * ld + j] -= lik * A[j * ld + k];
-    }
-    __syncwarp();
-  }
-  return true;
-}
+constexpr int kPairRegs = kMaxL / 64;   // pairs per lane in jacobi32: d / 2 <= 32 * kPairRegs
 
-template <typename T>
-__device__ void warp_trinv_lower(const T* Lm, T* Linv, int d, int ld) {
-  const int lane = threadIdx.x & 31;
-  for (int c = lane; c < d; c += 32) {
-    for (int i = 0; i < c; ++i) Linv[i * ld + c] = T(0);
-    for (int i = c; i < d; ++i) {
-      T acc = (i == c) ? T(1) : T(0);
-      for (int j = c; j < i; ++j) acc -= Lm[i * ld + j] * Linv[j * ld + c];
-      Linv[i * ld + c] = acc / Lm[i * ld + i];
+// Rotation `idx` of a round from the lane that holds it (lane idx % 32, register idx / 32).
+// Every lane of the warp must call this (shuffles); idx may differ between lanes.
+__device__ __forceinline__ void fetch_pair(const int (&pr)[kPairRegs], const float (&cr)[kPairRegs],
+                                           const float (&sr)[kPairRegs], int kp, int idx, int& pq, float& c,
+                                           float& s) {
+  const int src = idx & 31, reg = idx >> 5;
+  pq = 0;
+  c = 1.f;
+  s = 0.f;
+#pragma unroll
+  for (int t = 0; t < kPairRegs; ++t) {
+    if (t < kp) {
+      const int v1 = __shfl_sync(0xffffffffu, pr[t], src);
+      const float v2 = __shfl_sync(0xffffffffu, cr[t], src);
+      const float v3 = __shfl_sync(0xffffffffu, sr[t], src);
+      if (t == reg) { pq = v1; c = v2; s = v3; }
     }
   }
-  __syncwarp();
 }
 
-// Cyclic Jacobi eigendecomposition of the symmetric d x d matrix A (destroyed), in the
-// arithmetic of T (float or double), parallel ordering: each round rotates d/2 disjoint
-// pairs, A <- R A R^T and W <- W R^T, every thread updating whole 2 x 2 blocks so that a
-// round needs two barriers. On return W holds the eigenvectors as columns (W is set to
-// the identity first) and, when `sort` is set, lam the eigenvalues descending with W's
-// columns in the same order. Sweeps stop once the off-diagonal part is below `conv`
-// (relative, squared Frobenius norms), after a sweep without any rotation, or after
-// max_sweeps. A pair is left alone when |a_pq| <= eps_rel sqrt(|a_pp a_qq|), or - with
-// tau1 > 0 - when rotating it would move an eigenvalue by less than tau1 times the
-// smaller diagonal entry and turn the vectors by less than tau2 radians.
-template <typename T>
-__device__ void blk_jacobi(T* A, T* W, double* lam, int d, int ld, double* red, int* sweeps_out, double conv,
-                           double eps_rel, double tau1, double tau2, int max_sweeps, bool sort) {
-  __shared__ T cs[kMaxL / 2 + 1], sn[kMaxL / 2 + 1];
-  __shared__ int P[kMaxL / 2 + 1], Q[kMaxL / 2 + 1];
-  __shared__ int rotated;
-  const double tiny = sizeof(T) == 4 ? 1e-37 : 1e-300;
-  const int de = d + (d & 1);           // even count; index d (when d is odd) is a dummy
-  const int npairs = de / 2;
+// Cyclic Jacobi eigendecomposition of the symmetric d x d matrix in A, FP32, parallel
+// ordering (an odd d gets a dummy index d that pairs with nothing). Every warp works out all
+// rotations of a round itself from the current matrix - lane t holds pairs t, t + 32, ... in
+// registers - so that a round needs a single block barrier: the matrix moves between the
+// buffers A and A2, each 2 x 2 block (a, b), a <= b, becoming R_a M R_b^T and written with
+// its mirror image (the triangle of block pairs is folded into a rectangle of
+// ceil(N/2) x (N' + 1) items, N pairs, N' = N rounded up to even, so that lanes stay busy),
+// and the rows of W (set to the identity first; the eigenvectors on return, as columns) are
+// rotated in place. A pair is left alone when a_pq^2 <= eps_rel^2 |a_pp a_qq|; a rotated
+// pair's a_pq is set to zero. Sweeps stop once the off-diagonal part is at most `conv` of
+// the whole (squared Frobenius norms), after a sweep without rotations, or after
+// max_sweeps. The entries should be scaled to about 1. Returns the buffer (A or A2) that
+// holds the final, nearly diagonal matrix; *sweeps_out gets the sweeps made.
+__device__ float* jacobi32(float* A, float* A2, float* W, int d, int ld, float* red, float conv, float eps_rel,
+                           int max_sweeps, int* sweeps_out) {
+  const int de = d + (d & 1), npairs = de >> 1, m = de - 1;
+  const int nf = npairs + (npairs & 1);            // folded: nf / 2 rows of nf + 1 items
+  const int frows = nf >> 1, fcols = nf + 1;
+  const int kp = (npairs + 31) >> 5;               // live entries of the per-lane pair registers
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int e = threadIdx.x; e < d * d; e += blockDim.x) W[(e / d) * ld + e % d] = ((e / d) == (e % d)) ? T(1) : T(0);
+  const float eps2 = eps_rel * eps_rel;
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) W[(e / d) * ld + e % d] = ((e / d) == (e % d)) ? 1.f : 0.f;
+  __syncthreads();
+  float* cur = A;
+  float* nxt = A2;
+  int sweep = 0;
+  for (; sweep < max_sweeps && d > 1; ++sweep) {
+    float off = 0.f, tot = 0.f;
+    for (int i = warp; i < d; i += nwarps) {
+      for (int j = lane; j < d; j += 32) {
+        const float v = cur[i * ld + j];
+        tot = fmaf(v, v, tot);
+        if (i != j) off = fmaf(v, v, off);
+      }
+    }
+    blk_sum2(off, tot, red);
+    if (off <= conv * tot || tot == 0.f) break;
+    bool rotated = false;
+    for (int round = 0; round < m; ++round) {
+      int pr[kPairRegs];
+      float cr[kPairRegs], sr[kPairRegs];
+#pragma unroll
+      for (int t = 0; t < kPairRegs; ++t) {
+        const int pi = lane + 32 * t;
+        int p = 0, q = 0;
+        float c = 1.f, s = 0.f;
+        if (t < kp && pi < npairs) {
+          rr_pair(round, pi, m, p, q);
+          if (q < d) {
+            const float apq = cur[p * ld + q], app = cur[p * ld + p], aqq = cur[q * ld + q];
+            const float a2 = apq * apq;
+            if (a2 > 1e-37f && a2 > eps2 * fabsf(app * aqq)) {
+              jacobi_rotation32(app, aqq, apq, c, s);
+              rotated = true;
+            }
+          }
+        }
+        pr[t] = p | (q << 16);
+        cr[t] = c;
+        sr[t] = s;
+      }
+      // warp-rows: the folded A blocks (fcols items each, in chunks of 32), then W's rows
+      const int achunks = (fcols + 31) >> 5;
+      const int arows = frows * achunks;
+      for (int row = warp; row < arows + (d + 3) / 4; row += nwarps) {
+        if (row < arows) {
+          const int fr = achunks == 1 ? row : row / achunks, fc = (row - fr * achunks) * 32 + lane;
+          int pa, pb;
+          if (fc < nf - fr) {
+            pa = fr;
+            pb = fr + fc;
+          } else {
+            pa = nf - 1 - fr;
+            pb = pa + fc - (nf - fr);
+          }
+          const bool live = fc < fcols && pb < npairs;   // pa <= pb
+          int pqa, pqb;
+          float ca, sa, cb, sb;
+          fetch_pair(pr, cr, sr, kp, live ? pa : 0, pqa, ca, sa);
+          fetch_pair(pr, cr, sr, kp, live ? pb : 0, pqb, cb, sb);
+          if (live) {
+            const int ia = pqa & 0xffff, ja = pqa >> 16, ib = pqb & 0xffff, jb = pqb >> 16;
+            const bool ra = ja < d, rb = jb < d;
+            const float m00 = cur[ia * ld + ib];
+            const float m01 = rb ? cur[ia * ld + jb] : 0.f;
+            const float m10 = ra ? cur[ja * ld + ib] : 0.f;
+            const float m11 = (ra && rb) ? cur[ja * ld + jb] : 0.f;
+            const float r00 = ca * m00 - sa * m10, r01 = ca * m01 - sa * m11;   // R_a M
+            const float r10 = sa * m00 + ca * m10, r11 = sa * m01 + ca * m11;
+            const float o00 = cb * r00 - sb * r01, o01 = sb * r00 + cb * r01;   // (R_a M) R_b^T
+            const float o10 = cb * r10 - sb * r11, o11 = sb * r10 + cb * r11;
+            if (pa == pb) {
+              nxt[ia * ld + ia] = o00;
+              if (ra) {
+                const float z = sa != 0.f ? 0.f : m01;
+                nxt[ja * ld + ja] = o11;
+                nxt[ia * ld + ja] = z;
+                nxt[ja * ld + ia] = z;
+              }
+            } else {
+              nxt[ia * ld + ib] = o00;
+              nxt[ib * ld + ia] = o00;
+              if (rb) {
+                nxt[ia * ld + jb] = o01;
+                nxt[jb * ld + ia] = o01;
+              }
+              if (ra) {
+                nxt[ja * ld + ib] = o10;
+                nxt[ib * ld + ja] = o10;
+              }
+              if (ra && rb) {
+                nxt[ja * ld + jb] = o11;
+                nxt[jb * ld + ja] = o11;
+              }
+            }
+          }
+        } else {
+          // four rows of W at once (loads first) for the latency of shared memory
+          const int i0 = 4 * (row - arows);
+#pragma unroll
+          for (int t = 0; t < kPairRegs; ++t) {
+            const int pb = lane + 32 * t;
+            if (t < kp && pb < npairs && sr[t] != 0.f) {
+              const int ib = pr[t] & 0xffff, jb = pr[t] >> 16;
+              const float cb = cr[t], sb = sr[t];
+              float wp[4], wq[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u < d ? i0 + u : i0;
+                wp[u] = W[i * ld + ib];
+                wq[u] = W[i * ld + jb];
+              }
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                if (i0 + u < d) {
+                  W[(i0 + u) * ld + ib] = cb * wp[u] - sb * wq[u];
+                  W[(i0 + u) * ld + jb] = sb * wp[u] + cb * wq[u];
+                }
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+      float* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    // every warp made the same decisions from the same matrix, so this exit is uniform
+    if (!__any_sync(0xffffffffu, rotated)) { ++sweep; break; }
+  }
+  *sweeps_out = sweep;
+  return cur;
+}
+
+// Cyclic Jacobi eigendecomposition in FP64 (parallel ordering), in place, for the polish of
+// a nearly diagonal matrix and for the FP64 fallback route. Warp 0 works out a round's
+// rotations and lists only the pairs that need one; the rows of A for those pairs are then
+// rotated, and after a barrier the columns of A and of W, so that the FP64 work is
+// proportional to the rotations made. A pair is left alone when |a_pq| <= eps_rel
+// sqrt(|a_pp a_qq|), or - with tau1 > 0 - when rotating it would move an eigenvalue by less
+// than tau1 times the smaller diagonal entry and turn the vectors by less than tau2
+// radians. Sweeps stop once the off-diagonal part is at most `conv` of the whole (squared
+// Frobenius norms), after a sweep without rotations, or after max_sweeps. On return W holds
+// the eigenvectors as columns and, when `sort` is set, lam the eigenvalues descending with
+// W's columns in the same order (A is then scratch). The entries should be scaled to about
+// 1. Returns the number of sweeps.
+__device__ int jacobi64(double* A, double* W, double* lam, int d, int ld, double* red, double conv, double eps_rel,
+                        double tau1, double tau2, int max_sweeps, bool sort) {
+  __shared__ int act_pq[kMaxL / 2];
+  __shared__ double act_c[kMaxL / 2], act_s[kMaxL / 2];
+  __shared__ int nact[2];
+  __shared__ int needed;
+  const int de = d + (d & 1), npairs = de >> 1, m = de - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double eps2 = eps_rel * eps_rel;
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) W[(e / d) * ld + e % d] = ((e / d) == (e % d)) ? 1.0 : 0.0;
   __syncthreads();
   int sweep = 0;
-#ifdef SPCA_FIN_TRACE
-  long long c0 = clock64();
-  unsigned long long g0;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g0));
-#endif
   for (; sweep < max_sweeps && d > 1; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
-      const int i = e / d, j = e % d;
-      const double v = static_cast<double>(A[i * ld + j]);
-      tot += v * v;
-      if (i != j) off += v * v;
+      const int i = e / d, j = e - i * d;
+      const double v = A[i * ld + j];
+      tot = fma(v, v, tot);
+      if (i != j) off = fma(v, v, off);
     }
     const double off_sum = blk_sum(off, red);
     const double tot_sum = blk_sum(tot, red);
     if (off_sum <= conv * tot_sum || tot_sum == 0.0) break;
-    if (threadIdx.x == 0) rotated = 0;
-    __syncthreads();
     if (tau1 > 0.0) {
-      // polish: look at every pair at once (FP32 estimates) and stop if none needs a rotation
+      // look at every pair at once (FP32 estimates) and stop if none needs a rotation
+      if (threadIdx.x == 0) needed = 0;
+      __syncthreads();
       for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
-        const int i = e / d, j = e - (e / d) * d;
+        const int i = e / d, j = e - i * d;
         if (j <= i) continue;
         const float a = fabsf(static_cast<float>(A[i * ld + j]));
         const float ai = static_cast<float>(A[i * ld + i]), aj = static_cast<float>(A[j * ld + j]);
         const float gap = fabsf(aj - ai), mn = fminf(fabsf(ai), fabsf(aj));
         const bool work = a > static_cast<float>(eps_rel) * sqrtf(fabsf(ai)) * sqrtf(fabsf(aj)) &&
                           !(a * a <= static_cast<float>(tau1) * mn * gap && a <= static_cast<float>(tau2) * gap);
-        if (work) rotated = 1;
+        if (work) needed = 1;
       }
       __syncthreads();
-      const bool any = rotated != 0;
-      __syncthreads();
-      if (!any) break;
-      if (threadIdx.x == 0) rotated = 0;
-      __syncthreads();
+      if (!needed) break;
     }
-    for (int round = 0; round < de - 1; ++round) {
-      for (int pi = threadIdx.x; pi < npairs; pi += blockDim.x) {
-        int p, q;
-        if (pi == 0) {
-          p = de - 1;
-          q = round;
-        } else {
-          p = (round + pi) % (de - 1);
-          q = (round - pi + (de - 1)) % (de - 1);
-        }
-        if (p > q) { const int t = p; p = q; q = t; }
-        T c = T(1), sv = T(0);
-        if (q < d) {
-          const T apq = A[p * ld + q];
-          const T app = A[p * ld + p], aqq = A[q * ld + q];
-          const T a = tabs(apq);
-          const T gap = tabs(aqq - app);
-          const T mn = tmin(tabs(app), tabs(aqq));
-          bool work = a > T(tiny) && a > T(eps_rel) * tsqrt(tabs(app)) * tsqrt(tabs(aqq));
-          if (work && tau1 > 0.0 && a * a <= T(tau1) * mn * gap && a <= T(tau2) * gap) work = false;
-          if (work) {
-            jacobi_rotation<T>(app, aqq, apq, c, sv);
-            rotated = 1;
+    bool any = false;
+    for (int round = 0; round < m; ++round) {
+      if (warp == 0) {
+        int base = 0;
+        for (int pi0 = 0; pi0 < npairs; pi0 += 32) {
+          const int pi = pi0 + lane;
+          int p = 0, q = 0;
+          bool work = false;
+          double c = 1.0, s = 0.0;
+          if (pi < npairs) {
+            rr_pair(round, pi, m, p, q);
+            if (q < d) {
+              const double apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
+              const double a2 = apq * apq;
+              work = a2 > 1e-300 && a2 > eps2 * fabs(app * aqq);
+              if (work && tau1 > 0.0) {
+                const double gap = fabs(aqq - app), mn = fmin(fabs(app), fabs(aqq));
+                if (a2 <= tau1 * mn * gap && a2 <= (tau2 * gap) * (tau2 * gap)) work = false;
+              }
+              if (work) jacobi_rotation<double>(app, aqq, apq, c, s);
+            }
           }
+          const unsigned bal = __ballot_sync(0xffffffffu, work);
+          if (work) {
+            const int slot = base + __popc(bal & ((1u << lane) - 1u));
+            act_pq[slot] = p | (q << 16);
+            act_c[slot] = c;
+            act_s[slot] = s;
+          }
+          base += __popc(bal);
         }
-        P[pi] = p; Q[pi] = q; cs[pi] = c; sn[pi] = sv;
+        if (lane == 0) nact[round & 1] = base;
       }
       __syncthreads();
-      // A: the 2 x 2 block of pairs (a, b) becomes R_a M R_b^T (a warp per pa, lanes over pb);
-      // W: row i of pair b, W R_b^T (the next warps, lanes over pb)
-      for (int row = warp; row < npairs + d; row += nwarps) {
-        for (int pb = lane; pb < npairs; pb += 32) {
-        if (row < npairs) {
-          const int pa = row;
-          const T sa = sn[pa], sb = sn[pb];
-          if (sa == T(0) && sb == T(0)) continue;
-          const int ia = P[pa], ja = Q[pa], ib = P[pb], jb = Q[pb];   // rows ia, ja; columns ib, jb
-          const bool ra = ja < d, rb = jb < d;
-          const T ca = cs[pa], cb = cs[pb];
-          const T m00 = A[ia * ld + ib];
-          const T m01 = rb ? A[ia * ld + jb] : T(0);
-          const T m10 = ra ? A[ja * ld + ib] : T(0);
-          const T m11 = (ra && rb) ? A[ja * ld + jb] : T(0);
-          const T r00 = ca * m00 - sa * m10, r01 = ca * m01 - sa * m11;   // R_a M
-          const T r10 = sa * m00 + ca * m10, r11 = sa * m01 + ca * m11;
-          A[ia * ld + ib] = cb * r00 - sb * r01;                          // (R_a M) R_b^T
-          if (rb) A[ia * ld + jb] = sb * r00 + cb * r01;
-          if (ra) A[ja * ld + ib] = cb * r10 - sb * r11;
-          if (ra && rb) A[ja * ld + jb] = sb * r10 + cb * r11;
-        } else {
-          const int i = row - npairs;
-          const T sb = sn[pb];
-          if (sb == T(0)) continue;
-          const int ib = P[pb], jb = Q[pb];
-          const T cb = cs[pb];
-          const T wp = W[i * ld + ib], wq = W[i * ld + jb];
-          W[i * ld + ib] = cb * wp - sb * wq;
-          W[i * ld + jb] = sb * wp + cb * wq;
-        }
-        }
+      const int n = nact[round & 1];   // two slots: warp 0 may write the next round's first
+      if (n == 0) continue;
+      any = true;
+      const int nd = n * d;
+      for (int e = threadIdx.x; e < nd; e += blockDim.x) {   // rows p, q of A
+        const int k = e / d, j = e - k * d;
+        const int pq = act_pq[k], p = pq & 0xffff, q = pq >> 16;
+        const double c = act_c[k], s = act_s[k];
+        const double x = A[p * ld + j], y = A[q * ld + j];
+        A[p * ld + j] = c * x - s * y;
+        A[q * ld + j] = s * x + c * y;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < 2 * nd; e += blockDim.x) {   // columns p, q of A, then of W
+        const bool onw = e >= nd;
+        const int e2 = onw ? e - nd : e;
+        const int i = e2 / n, k = e2 - i * n;
+        double* M = onw ? W : A;
+        const int pq = act_pq[k], p = pq & 0xffff, q = pq >> 16;
+        const double c = act_c[k], s = act_s[k];
+        const double x = M[i * ld + p], y = M[i * ld + q];
+        M[i * ld + p] = c * x - s * y;
+        M[i * ld + q] = s * x + c * y;
       }
       __syncthreads();
     }
-    if (!rotated) { ++sweep; break; }
+    if (!any) { ++sweep; break; }
   }
-  if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
-#ifdef SPCA_FIN_TRACE
-  {
-    unsigned long long g1;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g1));
-    if (threadIdx.x == 0)
-      printf("jacobi fp%d d=%d sweeps=%d cycles=%lld ns=%llu threads=%d\n", static_cast<int>(8 * sizeof(T)), d, sweep,
-             clock64() - c0, g1 - g0, blockDim.x);
-  }
-#endif
-  if (!sort) return;
+  if (!sort) return sweep;
   // sort descending: rank of each eigenvalue, then permute W's columns through A as scratch
-  for (int i = threadIdx.x; i < d; i += blockDim.x) red[i] = static_cast<double>(A[i * ld + i]);
+  for (int i = threadIdx.x; i < d; i += blockDim.x) red[i] = A[i * ld + i];
   __syncthreads();
   for (int i = threadIdx.x; i < d; i += blockDim.x) {
     int rank = 0;
@@ -437,6 +647,228 @@ __device__ void blk_jacobi(T* A, T* W, double* lam, int d, int ld, double* red, 
   __syncthreads();
   for (int e = threadIdx.x; e < d * d; e += blockDim.x) W[(e / d) * ld + e % d] = A[(e / d) * ld + e % d];
   __syncthreads();
+  return sweep;
+}
+
+// Cyclic Jacobi (parallel ordering) for the polish of a nearly diagonal symmetric matrix,
+// held as its diagonal dg in FP64 and its off-diagonal part E in FP32 (E's diagonal unused).
+// With off-diagonal entries of about eps_32 |A|, FP32 rounding in them is of order
+// eps_32^2 |A|, far below what decides the small eigenvalues, while the diagonal - where
+// those eigenvalues build up - is updated in FP64 by a'_pp = a_pp - t a_pq,
+// a'_qq = a_qq + t a_pq (t = tan of the angle). Warp 0 works out a round's rotations (and
+// the diagonal updates) and lists the pairs that need one; rows p, q of E are then rotated,
+// and after a barrier its columns and those of W (FP32, the identity first), so that the
+// work is proportional to the rotations made. Skipping and stopping rules as for jacobi64.
+// On return lam holds the eigenvalues descending and W's columns the eigenvectors in the
+// same order (E is then scratch). Entries should be scaled to about 1. Returns the sweeps.
+__device__ int jacobi_mixed(double* dg, float* E, float* W, double* lam, int d, int ld, double* red, double conv,
+                            double eps_rel, double tau1, double tau2, int max_sweeps) {
+  __shared__ int act_pq[kMaxL / 2];
+  __shared__ float act_c[kMaxL / 2], act_s[kMaxL / 2];
+  __shared__ int nact[2];
+  __shared__ int needed;
+  const int de = d + (d & 1), npairs = de >> 1, m = de - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const double eps2 = eps_rel * eps_rel;
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) W[(e / d) * ld + e % d] = ((e / d) == (e % d)) ? 1.f : 0.f;
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < max_sweeps && d > 1; ++sweep) {
+    float offf = 0.f;
+    for (int i = warp; i < d; i += nwarps)
+      for (int j = lane; j < d; j += 32)
+        if (i != j) offf = fmaf(E[i * ld + j], E[i * ld + j], offf);
+    double diag = 0.0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) diag = fma(dg[i], dg[i], diag);
+    const double off_sum = blk_sum(static_cast<double>(offf), red);
+    const double tot_sum = off_sum + blk_sum(diag, red);
+    if (off_sum <= conv * tot_sum || tot_sum == 0.0) break;
+    if (tau1 > 0.0) {
+      // look at every pair at once (FP32 estimates) and stop if none needs a rotation
+      if (threadIdx.x == 0) needed = 0;
+      __syncthreads();
+      for (int i = warp; i < d; i += nwarps) {
+        const float ai = static_cast<float>(dg[i]);
+        for (int j = i + 1 + lane; j < d; j += 32) {
+          const float a = fabsf(E[i * ld + j]), aj = static_cast<float>(dg[j]);
+          const float gap = fabsf(aj - ai), mn = fminf(fabsf(ai), fabsf(aj));
+          const bool work = a > static_cast<float>(eps_rel) * sqrtf(fabsf(ai)) * sqrtf(fabsf(aj)) &&
+                            !(a * a <= static_cast<float>(tau1) * mn * gap && a <= static_cast<float>(tau2) * gap);
+          if (work) needed = 1;
+        }
+      }
+      __syncthreads();
+      if (!needed) break;
+    }
+    bool any = false;
+    for (int round = 0; round < m; ++round) {
+      if (warp == 0) {
+        int base = 0;
+        for (int pi0 = 0; pi0 < npairs; pi0 += 32) {
+          const int pi = pi0 + lane;
+          int p = 0, q = 0;
+          bool work = false;
+          float c = 1.f, s = 0.f;
+          if (pi < npairs) {
+            rr_pair(round, pi, m, p, q);
+            if (q < d) {
+              const double apq = static_cast<double>(E[p * ld + q]), app = dg[p], aqq = dg[q];
+              const double a2 = apq * apq;
+              work = a2 > 1e-300 && a2 > eps2 * fabs(app * aqq);
+              if (work && tau1 > 0.0) {
+                const double gap = fabs(aqq - app), mn = fmin(fabs(app), fabs(aqq));
+                if (a2 <= tau1 * mn * gap && a2 <= (tau2 * gap) * (tau2 * gap)) work = false;
+              }
+              if (work) {
+                const float theta = static_cast<float>(aqq - app) / (2.f * static_cast<float>(apq));
+                const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+                const float x = fmaf(t, t, 1.f);
+                float y = rsqrtf(x);
+                y = y * fmaf(-0.5f * x * y, y, 1.5f);
+                y = y * fmaf(-0.5f * x * y, y, 1.5f);
+                c = y;
+                s = t * y;
+                const double ta = static_cast<double>(t) * apq;
+                dg[p] = app - ta;
+                dg[q] = aqq + ta;
+              }
+            }
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, work);
+          if (work) {
+            const int slot = base + __popc(bal & ((1u << lane) - 1u));
+            act_pq[slot] = p | (q << 16);
+            act_c[slot] = c;
+            act_s[slot] = s;
+          }
+          base += __popc(bal);
+        }
+        if (lane == 0) nact[round & 1] = base;
+      }
+      __syncthreads();
+      const int n = nact[round & 1];   // two slots: warp 0 may write the next round's first
+      if (n == 0) continue;
+      any = true;
+      for (int k = warp; k < n; k += nwarps) {   // rows p, q of E, columns j outside {p, q}
+        const int pq = act_pq[k], p = pq & 0xffff, q = pq >> 16;
+        const float c = act_c[k], s = act_s[k];
+        for (int j = lane; j < d; j += 32) {
+          if (j == p || j == q) continue;
+          const float x = E[p * ld + j], y = E[q * ld + j];
+          E[p * ld + j] = c * x - s * y;
+          E[q * ld + j] = s * x + c * y;
+        }
+      }
+      __syncthreads();
+      for (int row = warp; row < 2 * d; row += nwarps) {   // columns p, q of E (rows outside {p, q}), of W
+        const bool onw = row >= d;
+        const int i = onw ? row - d : row;
+        float* M = onw ? W : E;
+        for (int k = lane; k < n; k += 32) {
+          const int pq = act_pq[k], p = pq & 0xffff, q = pq >> 16;
+          if (!onw && (i == p || i == q)) continue;
+          const float c = act_c[k], s = act_s[k];
+          const float x = M[i * ld + p], y = M[i * ld + q];
+          M[i * ld + p] = c * x - s * y;
+          M[i * ld + q] = s * x + c * y;
+        }
+      }
+      for (int k = threadIdx.x; k < n; k += blockDim.x) {   // the annihilated entries
+        const int pq = act_pq[k], p = pq & 0xffff, q = pq >> 16;
+        E[p * ld + q] = 0.f;
+        E[q * ld + p] = 0.f;
+      }
+      __syncthreads();
+    }
+    if (!any) { ++sweep; break; }
+  }
+  // sort descending: rank of each eigenvalue, then permute W's columns through E as scratch
+  for (int i = threadIdx.x; i < d; i += blockDim.x) red[i] = dg[i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    int rank = 0;
+    const double v = red[i];
+    for (int j = 0; j < d; ++j) {
+      const double u = red[j];
+      if (u > v || (u == v && j < i)) ++rank;
+    }
+    lam[rank] = v;
+    for (int t = 0; t < d; ++t) E[t * ld + rank] = W[t * ld + i];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) W[(e / d) * ld + e % d] = E[(e / d) * ld + e % d];
+  __syncthreads();
+  return sweep;
+}
+
+// In-place Cholesky: the lower triangle of A becomes L1 (A = L1 L1^T). False if a pivot <= tol.
+__device__ bool blk_cholesky(double* A, int d, int ld, double tol) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) ok = 1;
+  __syncthreads();
+  for (int k = 0; k < d; ++k) {
+    if (threadIdx.x == 0) {
+      const double v = A[k * ld + k];
+      if (!(v > tol)) ok = 0;
+      else A[k * ld + k] = sqrt(v);
+    }
+    __syncthreads();
+    if (!ok) return false;
+    const double dk = A[k * ld + k];
+    for (int i = k + 1 + threadIdx.x; i < d; i += blockDim.x) A[i * ld + k] /= dk;
+    __syncthreads();
+    const int rem = d - k - 1;
+    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+      if (j <= i) A[i * ld + j] -= A[i * ld + k] * A[j * ld + k];
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// Linv = inverse of the lower triangle of Lm (strict upper part of Linv zeroed).
+__device__ void blk_trinv_lower(const double* Lm, double* Linv, int d, int ld) {
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) Linv[(e / d) * ld + e % d] = 0.0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    for (int i = c; i < d; ++i) {
+      double acc = (i == c) ? 1.0 : 0.0;
+      for (int j = c; j < i; ++j) acc -= Lm[i * ld + j] * Linv[j * ld + c];
+      Linv[i * ld + c] = acc / Lm[i * ld + i];
+    }
+  }
+  __syncthreads();
+}
+
+// FP32 Cholesky of X (lower triangle, right-looking) and, alongside, Y = the inverse of the
+// factor: the row operations of the forward substitution L Y = I are applied to Y (the
+// identity first) step by step. Two block barriers per step. False, uniformly, if a pivot
+// is <= tol; X's lower triangle then holds a partial factor.
+__device__ bool blk_chol_inv32(float* X, float* Y, int d, int ld, float tol) {
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) Y[(e / d) * ld + e % d] = ((e / d) == (e % d)) ? 1.f : 0.f;
+  __syncthreads();
+  for (int k = 0; k < d; ++k) {
+    const float v = X[k * ld + k];
+    if (!(v > tol)) return false;   // the same value in every thread
+    const float dk = sqrtf(v), inv = 1.f / dk;
+    for (int e = threadIdx.x; e < d; e += blockDim.x) {   // column k of L (rows > k), row k of Y
+      if (e > k) X[e * ld + k] *= inv;
+      else Y[k * ld + e] *= inv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) X[k * ld + k] = dk;
+    // rows i > k over warps, columns j <= i over lanes: j > k updates the factor, j <= k Y
+    for (int i = k + 1 + (threadIdx.x >> 5); i < d; i += blockDim.x >> 5) {
+      const float lik = X[i * ld + k];
+      for (int j = threadIdx.x & 31; j <= i; j += 32) {
+        if (j > k) X[i * ld + j] -= lik * X[j * ld + k];
+        else Y[i * ld + j] -= lik * Y[k * ld + j];
+      }
+    }
+    __syncthreads();
+  }
+  return true;
 }
 
 // R from gram_bar (step 2), all in FP64: the fallback when the mixed-precision route
@@ -510,13 +942,15 @@ __global__ void __launch_bounds__(FT) factor_kernel(const double* __restrict__ g
       return;
     }
   }
-  // eigen route: gbar = W diag(lam) W^T
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) X[(e / l) * ld + e % l] = gbar[(e / l) * L + e % l];
+  // eigen route: gbar = W diag(lam) W^T, solved on gbar scaled by a power of two (exact)
+  const double sc = pow2_scale(dmax);
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) X[(e / l) * ld + e % l] = sc * gbar[(e / l) * L + e % l];
   __syncthreads();
-  int sweeps = 0;
   // relative off-diagonal Frobenius norm <= 1e-13: below that, round-off of the rotations
   // themselves (about eps * lambda_max per entry) keeps it from shrinking further
-  blk_jacobi<double>(X, Y, lam, l, ld, red, &sweeps, 1e-26, 1e-18, 0.0, 0.0, 40, true);
+  const int sweeps = jacobi64(X, Y, lam, l, ld, red, 1e-26, 1e-18, 0.0, 0.0, 40, true);
+  for (int i = threadIdx.x; i < l; i += blockDim.x) lam[i] /= sc;
+  __syncthreads();
   __shared__ int r_keep;
   if (threadIdx.x == 0) {
     const double cut = l * DBL_EPSILON * fmax(lam[0], 0.0);
@@ -539,24 +973,49 @@ __global__ void __launch_bounds__(FT) factor_kernel(const double* __restrict__ g
 //      eps_32 |C| (enough for the leading pairs, not for the small eigenvalues);
 // (ii) small FP64 products make W0 orthogonal to FP64 precision (two Newton-Schulz steps,
 //      W <- W (3 I - W^T W) / 2) and form C1 = W^T C W, nearly diagonal;
-// (iii) eig_polish_kernel: FP64 Jacobi on C1, skipping the rotations that would change no
-//      eigenvalue by more than 1e-8 relative and no vector by more than 1e-6 rad - the
+// (iii) eig_polish_kernel: Jacobi on C1 with its diagonal in FP64 and its (tiny)
+//      off-diagonal part in FP32 (jacobi_mixed), skipping the rotations that would change
+//      no eigenvalue by more than 1e-8 relative and no vector by more than 1e-6 rad - the
 //      remaining work sits among the small eigenvalues that FP32 could not separate;
 // (iv) Z = W W1 (FP64): the eigenvectors of C, columns by descending eigenvalue.
-__global__ void __launch_bounds__(FT) eig_f32_kernel(const double* __restrict__ C, float* __restrict__ Xg,
-                                                     float* __restrict__ Yg, double* __restrict__ W0,
-                                                     const int* __restrict__ info, int L, int smem) {
+// Both solves are one thread block each; the scale of C is brought to about 1 by a power
+// of two first (exact), so that FP32 ranges never matter.
+constexpr int EIG_T = 512;    // threads of the FP32 Jacobi kernel
+constexpr int POL_T = 512;    // threads of the polish and of the FP32 Cholesky kernels
+
+__global__ void __launch_bounds__(EIG_T) eig_f32_kernel(const double* __restrict__ C, float* __restrict__ Xg,
+                                                        float* __restrict__ Yg, float* __restrict__ Zg,
+                                                        double* __restrict__ W0, int* __restrict__ info, int L,
+                                                        int smem) {
   extern __shared__ float e32[];
-  __shared__ double red[FT];
+  __shared__ float red[2 * (EIG_T / 32)];
+  __shared__ double scale;
   const int r = info[0];
-  const int ld = smem ? r : L;
+  const int ld = smem ? (r | 1) : L;   // odd: a column's entries fall in different banks
   float* X = smem ? e32 : Xg;
-  float* Y = smem ? e32 + r * r : Yg;
+  float* X2 = smem ? e32 + r * ld : Zg;
+  float* Y = smem ? e32 + 2 * r * ld : Yg;
+  if (threadIdx.x < 32) {   // C scaled by a power of two so that its largest diagonal entry is in [1, 2)
+    double dm = 0.0;
+    for (int i = threadIdx.x; i < r; i += 32) dm = fmax(dm, fabs(C[i * L + i]));
+    for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    if (threadIdx.x == 0) scale = pow2_scale(dm);
+  }
+  __syncthreads();
+  const double sc = scale;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x)
-    X[(e / r) * ld + e % r] = static_cast<float>(C[(e / r) * L + e % r]);
+    X[(e / r) * ld + e % r] = static_cast<float>(sc * C[(e / r) * L + e % r]);
   __syncthreads();
-  if (r > 0) blk_jacobi<float>(X, Y, nullptr, r, ld, red, nullptr, 1e-10, 3e-8, 0.0, 0.0, 16, false);
+  int sweeps = 0;
+#ifdef SPCA_FIN_TRACE
+  const long long t0 = clock64();
+#endif
+  if (r > 0) jacobi32(X, X2, Y, r, ld, red, 1e-10f, 3e-8f, 16, &sweeps);
   __syncthreads();
+#ifdef SPCA_FIN_TRACE
+  if (threadIdx.x == 0) printf("eig_f32 d=%d threads=%d sweeps=%d cycles=%lld\n", r, blockDim.x, sweeps, clock64() - t0);
+#endif
+  if (threadIdx.x == 0) info[4] = sweeps;
   for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
     const int i = e / L, j = e % L;
     W0[e] = (i < r && j < r) ? static_cast<double>(Y[i * ld + j]) : 0.0;
@@ -604,31 +1063,46 @@ __global__ void __launch_bounds__(GEMM_T) small_gemm_kernel(const double* __rest
   }
 }
 
-__global__ void __launch_bounds__(FT) eig_polish_kernel(const double* __restrict__ C1, double* __restrict__ Xg,
-                                                        double* __restrict__ W1, double* __restrict__ lam,
-                                                        double* __restrict__ sig, int* __restrict__ info, int L,
-                                                        int smem) {
-  extern __shared__ double e64[];
-  __shared__ double red[FT];
+__global__ void __launch_bounds__(POL_T) eig_polish_kernel(const double* __restrict__ C1, float* __restrict__ Eg,
+                                                           float* __restrict__ Wg, double* __restrict__ W1,
+                                                           double* __restrict__ lam, double* __restrict__ sig,
+                                                           int* __restrict__ info, int L, int smem) {
+  extern __shared__ float p32[];
+  __shared__ double red[kMaxL];
+  __shared__ double dg[kMaxL];
+  __shared__ double scale;
   const int r = info[0];
-  const int ld = smem ? r : L;
-  double* X = smem ? e64 : Xg;
-  double* Y = smem ? e64 + r * r : W1;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) X[(e / r) * ld + e % r] = C1[(e / r) * L + e % r];
+  const int ld = smem ? (r | 1) : L;   // odd: columns of a row fall in different banks
+  float* E = smem ? p32 : Eg;
+  float* W = smem ? p32 + r * ld : Wg;
+  if (threadIdx.x < 32) {   // C1 scaled by a power of two (exact), undone on lam
+    double dm = 0.0;
+    for (int i = threadIdx.x; i < r; i += 32) dm = fmax(dm, fabs(C1[i * L + i]));
+    for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    if (threadIdx.x == 0) scale = pow2_scale(dm);
+  }
+  __syncthreads();
+  const double sc = scale;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e - i * r;
+    const double v = sc * C1[i * L + j];
+    if (i == j) dg[i] = v;
+    E[i * ld + j] = i == j ? 0.f : static_cast<float>(v);
+  }
   __syncthreads();
   int sweeps = 0;
-  if (r > 0) blk_jacobi<double>(X, Y, lam, r, ld, red, &sweeps, 1e-26, 1e-18, 1e-8, 1e-6, 40, true);
+#ifdef SPCA_FIN_TRACE
+  const long long t0 = clock64();
+#endif
+  if (r > 0) sweeps = jacobi_mixed(dg, E, W, lam, r, ld, red, 1e-26, 1e-18, 1e-8, 1e-6, 40);
+#ifdef SPCA_FIN_TRACE
+  if (threadIdx.x == 0) printf("eig_polish d=%d threads=%d sweeps=%d cycles=%lld\n", r, blockDim.x, sweeps, clock64() - t0);
+#endif
+  for (int i = threadIdx.x; i < r; i += blockDim.x) lam[i] /= sc;
   __syncthreads();
-  if (smem) {
-    for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
-      const int i = e / L, j = e % L;
-      W1[e] = (i < r && j < r) ? Y[i * ld + j] : 0.0;
-    }
-  } else {
-    for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
-      const int i = e / L, j = e % L;
-      if (!(i < r && j < r)) W1[e] = 0.0;
-    }
+  for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
+    const int i = e / L, j = e % L;
+    W1[e] = (i < r && j < r) ? static_cast<double>(W[i * ld + j]) : 0.0;
   }
   for (int i = threadIdx.x; i < L; i += blockDim.x) sig[i] = (i < r) ? sqrt(fmax(lam[i], 0.0)) : 0.0;
   if (threadIdx.x == 0) info[3] = sweeps;
@@ -644,23 +1118,29 @@ __global__ void __launch_bounds__(FT) eig_polish_kernel(const double* __restrict
 // chol_inv_f32_kernel: Y = inverse of the FP32 Cholesky factor of the leading l x l block of
 // M (FP64 in and out, ld L, zero outside). A pivot <= tol_rel * max diag, rank_ok == 0 or a
 // non-finite entry sets info[6] (the FP64 fallback then runs); `first` clears it first.
-__global__ void __launch_bounds__(32) chol_inv_f32_kernel(const double* __restrict__ M, int l, int L,
-                                                          double tol_rel, int rank_ok, int first,
-                                                          float* __restrict__ Xg, float* __restrict__ Yg,
-                                                          double* __restrict__ Y, int* __restrict__ info,
-                                                          int smem) {
+__global__ void __launch_bounds__(POL_T) chol_inv_f32_kernel(const double* __restrict__ M, int l, int L,
+                                                             double tol_rel, int rank_ok, int first,
+                                                             float* __restrict__ Xg, float* __restrict__ Yg,
+                                                             double* __restrict__ Y, int* __restrict__ info, int smem) {
   extern __shared__ float c32[];
+  __shared__ float wmax[POL_T / 32];
   const int ld = smem ? l : L;
   float* X = smem ? c32 : Xg;
   float* Yf = smem ? c32 + l * l : Yg;
-  for (int i = threadIdx.x >> 3; i < l; i += blockDim.x >> 3)   // 8 lanes per row
-    for (int j = threadIdx.x & 7; j < l; j += 8) X[i * ld + j] = static_cast<float>(M[i * L + j]);
-  __syncwarp();
   float dm = 0.f;
-  for (int i = threadIdx.x; i < l; i += 32) dm = fmaxf(dm, fabsf(X[i * ld + i]));
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e / l, j = e - i * l;
+    const float v = static_cast<float>(M[i * L + j]);
+    X[i * ld + j] = v;
+    if (i == j) dm = fmaxf(dm, fabsf(v));
+  }
   for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
-  bool ok = rank_ok && dm > 0.f && isfinite(dm) && warp_cholesky<float>(X, l, ld, static_cast<float>(tol_rel) * dm);
-  if (ok) warp_trinv_lower<float>(X, Yf, l, ld);
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = dm;
+  __syncthreads();
+  dm = 0.f;
+  for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) dm = fmaxf(dm, wmax[w]);
+  bool ok = rank_ok && dm > 0.f && isfinite(dm) && blk_chol_inv32(X, Yf, l, ld, static_cast<float>(tol_rel) * dm);
+  __syncthreads();
   for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
     const int i = e / L, j = e % L;
     Y[e] = (ok && i < l && j < l) ? static_cast<double>(Yf[i * ld + j]) : 0.0;
@@ -718,7 +1198,11 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
     cudaFuncSetAttribute(eig_polish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(kMaxDenseSmem));
     cudaFuncSetAttribute(bt_and_c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(2 * sizeof(double) * BT_ROWS * kMaxL));
+                         static_cast<int>(kMaxDenseSmem));
+    cudaFuncSetAttribute(form_v_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(kMaxDenseSmem));
+    cudaFuncSetAttribute(form_v_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(kMaxDenseSmem));
     attr_done = true;
   }
   prof->begin(SPCA_K_FINALIZE, st);
@@ -730,8 +1214,10 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
   if (r_max < 0) r_max = 0;
   const int64_t LL = static_cast<int64_t>(s.L) * s.L;
   float* s32 = reinterpret_cast<float*>(f.Cpart);   // FP32 scratch when l x l does not fit in shared memory
-  const size_t dense32 = 2 * sizeof(float) * s.l * s.l;
+  const size_t dense32 = 2 * sizeof(float) * s.l * s.l;   // Cholesky: X, Y
   const int smem32 = dense32 <= kMaxDenseSmem ? 1 : 0;
+  const size_t dense32e = 3 * sizeof(float) * s.l * (s.l | 1);  // FP32 Jacobi: A, A2, W
+  const int smem32e = dense32e <= kMaxDenseSmem ? 1 : 0;
   const int l = s.l, L = s.L;
   const int rank_ok = r_max >= l ? 1 : 0;
   const size_t gemm_full = sizeof(double) * (kMaxL + static_cast<size_t>(l) * l);
@@ -739,12 +1225,12 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
   const size_t gemm_smem = gstage ? gemm_full : sizeof(double) * kMaxL;
   // mixed-precision route (buffers: Y1 W, X1 T, Y2 X, T2 C, X2 W, F X, T T)
   const dim3 gb(L), gt(GEMM_T);
-  chol_inv_f32_kernel<<<1, 32, smem32 ? dense32 : 0, st>>>(f.gbar, l, L, l * 1.2e-7, rank_ok, 1, s32, s32 + LL, f.W,
+  chol_inv_f32_kernel<<<1, POL_T, smem32 ? dense32 : 0, st>>>(f.gbar, l, L, l * 1.2e-7, rank_ok, 1, s32, s32 + LL, f.W,
                                                             f.info, smem32);
   // X1 = Y1 (gram Y1^T)
   small_gemm_kernel<<<gb, gt, gemm_smem, st>>>(f.gbar, 0, f.W, 1, nullptr, 1.0, 0.0, nullptr, l, L, gstage, f.X);
   small_gemm_kernel<<<gb, gt, gemm_smem, st>>>(f.W, 0, f.X, 0, nullptr, 1.0, 0.0, nullptr, l, L, gstage, f.T);
-  chol_inv_f32_kernel<<<1, 32, smem32 ? dense32 : 0, st>>>(f.T, l, L, l * 1.2e-7, 1, 0, s32, s32 + LL, f.X, f.info,
+  chol_inv_f32_kernel<<<1, POL_T, smem32 ? dense32 : 0, st>>>(f.T, l, L, l * 1.2e-7, 1, 0, s32, s32 + LL, f.X, f.info,
                                                             smem32);
   // T2 = Y2 Y1; X2 = T2 (gram T2^T); T = T2 - F T2
   small_gemm_kernel<<<gb, gt, gemm_smem, st>>>(f.X, 0, f.W, 0, nullptr, 1.0, 0.0, nullptr, l, L, gstage, f.C);
@@ -757,18 +1243,22 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
   const int factor_smem = dense3 <= kMaxDenseSmem ? 1 : 0;
   factor_kernel<<<1, FT, factor_smem ? dense3 : 0, st>>>(f.gbar, s.l, s.L, static_cast<int>(r_max), f.T, f.X, f.W,
                                                          f.lam, f.info, factor_smem);
-  const size_t dense64 = 2 * sizeof(double) * s.l * s.l;
+  const size_t dense64 = 2 * sizeof(float) * s.l * (s.l | 1);   // polish: E, W (FP32)
   const int smem64 = dense64 <= kMaxDenseSmem ? 1 : 0;
   const int64_t nblk = (s.n + BT_ROWS - 1) / BT_ROWS;
   const int parts = static_cast<int>(nblk < f.nparts ? nblk : f.nparts);
-  bt_and_c_kernel<<<parts, 256, 2 * sizeof(double) * BT_ROWS * s.L, st>>>(f.Hbar, f.T, f.info, s.n, s.l, s.L, f.Bt,
-                                                                          f.Cpart);
-  c_reduce_kernel<<<(s.L * s.L + 255) / 256, 256, 0, st>>>(f.Cpart, parts, s.L, f.C);
+  const size_t bt_base = 2 * sizeof(double) * BT_ROWS * s.L;
+  const size_t bt_full = bt_base + sizeof(double) * LL;
+  const int stage_t = bt_full <= kMaxDenseSmem ? 1 : 0;
+  bt_and_c_kernel<<<parts, 256, stage_t ? bt_full : bt_base, st>>>(f.Hbar, f.T, f.info, s.n, s.l, s.L, stage_t, f.Bt,
+                                                                   f.Cpart);
+  c_reduce_kernel<<<(s.L * s.L + 31) / 32, CR_T, 0, st>>>(f.Cpart, parts, s.L, f.C);
   // eigenvectors of C: FP32 Jacobi, FP64 orthogonalisation and polish (scratch: Cpart, whose
   // partials are consumed by now, and T, X, W)
-  double* s64 = f.Cpart + 2 * LL;
+  float* s64 = reinterpret_cast<float*>(f.Cpart + 2 * LL);   // E, W of the polish: 2 L^2 floats
   double* W1 = f.Cpart + 3 * LL;
-  eig_f32_kernel<<<1, FT, smem32 ? dense32 : 0, st>>>(f.C, s32, s32 + LL, f.W, f.info, s.L, smem32);
+  eig_f32_kernel<<<1, EIG_T, smem32e ? dense32e : 0, st>>>(f.C, s32, s32 + LL, s32 + 2 * LL, f.W, f.info, s.L,
+                                                          smem32e);
   // Newton-Schulz, twice: W <- 1.5 W - 0.5 W (W^T W)  (W: f.W -> f.T -> f.W)
   small_gemm_kernel<<<gb, gt, gemm_smem, st>>>(f.W, 1, f.W, 0, nullptr, 1.0, 0.0, f.info, 0, s.L, gstage, f.X);
   small_gemm_kernel<<<gb, gt, gemm_smem, st>>>(f.W, 0, f.X, 0, f.W, -0.5, 1.5, f.info, 0, s.L, gstage, f.T);
@@ -777,10 +1267,20 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
   // C1 = W^T C W
   small_gemm_kernel<<<gb, gt, gemm_smem, st>>>(f.C, 0, f.W, 0, nullptr, 1.0, 0.0, f.info, 0, s.L, gstage, f.X);
   small_gemm_kernel<<<gb, gt, gemm_smem, st>>>(f.W, 1, f.X, 0, nullptr, 1.0, 0.0, f.info, 0, s.L, gstage, f.T);
-  eig_polish_kernel<<<1, FT, smem64 ? dense64 : 0, st>>>(f.T, s64, W1, f.lam, f.sig, f.info, s.L, smem64);
+  eig_polish_kernel<<<1, POL_T, smem64 ? dense64 : 0, st>>>(f.T, s64, s64 + LL, W1, f.lam, f.sig, f.info, s.L,
+                                                            smem64);
   // Z = W W1 (into f.X): the eigenvectors of C, used to form V
   small_gemm_kernel<<<gb, gt, gemm_smem, st>>>(f.W, 0, W1, 0, nullptr, 1.0, 0.0, f.info, 0, s.L, gstage, f.X);
-  form_v_kernel<<<grid_for(s.n * k, 256), 256, 0, st>>>(f.Bt, f.X, f.sig, f.info, s.n, k, s.L, V_dev);
+  // a block of rows of Bt, 1/sigma and (when it fits) W's leading l x k block in shared
+  // memory, sized for r = l, the largest rank
+  const size_t fv_base = sizeof(double) * (FV_ROWS * (static_cast<size_t>(l) + 1) + k);
+  const size_t fv_full = fv_base + sizeof(double) * static_cast<size_t>(l) * k;
+  const int64_t fv_tiles = (s.n + FV_ROWS - 1) / FV_ROWS;
+  const int fv_grid = static_cast<int>(fv_tiles < 152 * 2 ? fv_tiles : 152 * 2);
+  if (fv_full <= kMaxDenseSmem)
+    form_v_kernel<true><<<fv_grid, 256, fv_full, st>>>(f.Bt, f.X, f.sig, f.info, s.n, k, s.L, V_dev);
+  else
+    form_v_kernel<false><<<fv_grid, 256, fv_base, st>>>(f.Bt, f.X, f.sig, f.info, s.n, k, s.L, V_dev);
   sign_fix_kernel<<<k, SIGN_T, 0, st>>>(V_dev, s.n);
   prof->launches[SPCA_K_FINALIZE] += 24;  // launches above beyond the one begin() counted
   prof->end(SPCA_K_FINALIZE, st);
