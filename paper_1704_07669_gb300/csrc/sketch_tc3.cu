@@ -5,8 +5,10 @@
 //  - phase 1 of tile i streams the slice of A from HBM (TMA, FP32, 64 features x 128 rows
 //    per stage), converter warps subtract c, scale and round into a 16-bit operand buffer
 //    (two 64-feature blocks), and MMA1 accumulates D1 = A_hat Omega in TMEM;
-//  - phase 2 of tile i streams the same slice again - now from L2 - once G(i) is known, and
-//    MMA2 accumulates H += A_hat^T G' per 128-feature unit;
+//  - the converted operand of each unit also goes out, by a bulk copy, to an image in global
+//    memory (two tiles per CTA, kept in L2); phase 2 of tile i, once G(i) is known, bulk-loads
+//    that image into the idle stage ring - half the bytes of the FP32 slice and no second
+//    conversion - and MMA2 accumulates H += A_hat^T G' per 128-feature unit;
 //  - a reduce group of four warps turns D1(i) into G'(i) (cluster reduction, rounding,
 //    Gram matrix, sums, G^T operand) while the other warps already stream tile i+1: phase 1
 //    of tile i+1 runs before phase 2 of tile i, so the latency of the reduction overlaps the
@@ -63,7 +65,7 @@ __host__ __device__ inline Tc3Layout tc3_layout(int L, int w, int CS, int gs) {
   t.pub = o; o += 2u * static_cast<uint32_t>(L * gs) * (t.RPC / 8) * 16u;   // two tile parities
   t.shift = o; o += ((static_cast<uint32_t>(w) * 4u) + 15u) & ~15u;
   t.sy = o; o += ((static_cast<uint32_t>(t.RPC) * L * 4u) + 15u) & ~15u;
-  t.bars = o; o += 8u * 32u;
+  t.bars = o; o += 16u * 32u;
   t.total = o + 1024u;
   return t;
 }
@@ -84,6 +86,8 @@ struct Tc3Args {
   int drain_every;
   const float* shift;
   const uint16_t* om16;
+  uint16_t* img;               // operand images: per CTA two tiles of w / 128 units (128 x 128, 16-bit)
+  int64_t img_halves;          // its size; a copy that would leave it is skipped and flags[0] bit 3 set
   const float* scale;
   float* Hpart;
   double* gram_part;
@@ -117,9 +121,14 @@ __device__ __forceinline__ int find_seg3(const Tc3Args& a, int64_t tile) {
 
 // barrier slots
 enum {
-  B_STAGE_FULL = 0,                    // [NSTAGE]
-  B_STAGE_EMPTY = B_STAGE_FULL + NSTAGE,
-  B_PAIR_FULL = B_STAGE_EMPTY + NSTAGE,   // [2]
+  // a ring slot holds a phase-1 stage or a phase-2 unit; each kind has its own full and
+  // empty barriers, so that a waiter, which sees only its own kind, is never more than one
+  // phase ahead of the barrier it polls by parity
+  B_STAGE_FULL = 0,                        // [NSTAGE] a phase-1 stage landed
+  B_STAGE_EMPTY = B_STAGE_FULL + NSTAGE,   // [NSTAGE] a phase-1 stage was converted
+  B_UNIT_FULL = B_STAGE_EMPTY + NSTAGE,    // [NSTAGE] a phase-2 unit landed
+  B_SLOT_EMPTY = B_UNIT_FULL + NSTAGE,     // [NSTAGE] a phase-2 unit was consumed by MMA2
+  B_PAIR_FULL = B_SLOT_EMPTY + NSTAGE,   // [2]
   B_PAIR_EMPTY = B_PAIR_FULL + 2,
   B_OM_FULL = B_PAIR_EMPTY + 2,
   B_OM_EMPTY,
@@ -131,8 +140,10 @@ enum {
   B_XCH_FREE,
   B_PUB_READY,                         // [2]
   B_FINAL = B_PUB_READY + 2,           // the MMA issuer's last commit
-  B_COUNT
+  B_IMG_READY,                         // [2] a tile's operand image is in global memory (tile parity)
+  B_COUNT = B_IMG_READY + 2
 };
+static_assert(B_COUNT <= 64, "barrier slots: 16 x 32 bytes in the layout");
 
 // tile i of this cluster is a drain tile: H leaves TMEM after its MMA2
 __device__ __forceinline__ bool drain_tile(int i, int nt, int every) { return ((i + 1) % every == 0) || (i == nt - 1); }
@@ -170,6 +181,15 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
   const int64_t g0 = f0 / 64;
   const int nt = cid < a.ntiles ? static_cast<int>((a.ntiles - 1 - cid) / ncl + 1) : 0;   // local tiles
   const float op_scale = a.scale ? *a.scale : 1.f;
+  constexpr uint32_t UNIT_BYTES = 2 * BLOCK16;   // one 128 x 128 operand unit
+  static_assert(STAGE_BYTES == UNIT_BYTES, "a ring slot holds a stage or a unit");
+  const int64_t img_cta = (static_cast<int64_t>(cid) * CS + rank) * 2 * U * (UNIT_BYTES / 2);
+  auto img_off = [&](int ti, int u) { return img_cta + (static_cast<int64_t>(ti & 1) * U + u) * (UNIT_BYTES / 2); };
+  auto img_ok = [&](int64_t off) {
+    const bool ok = off >= 0 && off + UNIT_BYTES / 2 <= a.img_halves;
+    if (!ok) atomicOr(a.flags, 8);
+    return ok;
+  };
   const float inv_s = 1.f / op_scale;
 
   for (int i = tid; i < w; i += T3_NT) sShift[i] = (f0 + i < n) ? a.shift[f0 + i] : 0.f;
@@ -180,10 +200,12 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(bar(B_STAGE_FULL + s), 1);
       mbar_init(bar(B_STAGE_EMPTY + s), CV_WARPS);
+      mbar_init(bar(B_UNIT_FULL + s), 1);
+      mbar_init(bar(B_SLOT_EMPTY + s), 1);
     }
     for (int p = 0; p < 2; ++p) {
       mbar_init(bar(B_PAIR_FULL + p), CV_WARPS);
-      mbar_init(bar(B_PAIR_EMPTY + p), 1);
+      mbar_init(bar(B_PAIR_EMPTY + p), 2);   // MMA1 done, and the image copy has read the slot
       mbar_init(bar(B_D1_FULL + p), 1);
       mbar_init(bar(B_D1_EMPTY + p), RG_THREADS);
       mbar_init(bar(B_PUB_READY + p), static_cast<uint32_t>(CS));
@@ -195,6 +217,8 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
     mbar_init(bar(B_XCH_READY), static_cast<uint32_t>(CS));
     mbar_init(bar(B_XCH_FREE), static_cast<uint32_t>(CS));
     mbar_init(bar(B_FINAL), 1);
+    mbar_init(bar(B_IMG_READY), 1);
+    mbar_init(bar(B_IMG_READY + 1), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -213,50 +237,85 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
   if (warp == PROD_WARP) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      uint32_t sc = 0, fills[NSTAGE] = {0, 0}, om_fills = 0;
+      // the ring: phase 1 of tile i+1 (2U FP32 stages), then phase 2 of tile i (U image units)
+      // per ring slot (two, kept in registers): fills of each kind and the kind of the last one
+      static_assert(NSTAGE == 2, "two ring slots");
+      uint32_t pos = 0, om_fills = 0;
+      uint32_t n1a = 0, n1b = 0, n2a = 0, n2b = 0;
+      int lasta = 0, lastb = 0;
+      const uint64_t keep = l2_policy_evict_last(), drop = l2_policy_evict_first();
+      auto claim = [&](int s) {   // the previous fill of ring slot s has been consumed
+        const int last = s ? lastb : lasta;
+        const uint32_t n1 = s ? n1b : n1a, n2 = s ? n2b : n2a;
+        if (last == 1 && !dead && !mbar_wait(bar(B_STAGE_EMPTY + s), (n1 - 1) & 1u)) dead = true;
+        if (last == 2 && !dead && !mbar_wait(bar(B_SLOT_EMPTY + s), (n2 - 1) & 1u)) dead = true;
+      };
+      auto filled = [&](int s, int kind) {
+        if (s) { lastb = kind; if (kind == 1) ++n1b; else ++n2b; }
+        else { lasta = kind; if (kind == 1) ++n1a; else ++n2a; }
+      };
       for (int i = -1; i < nt; ++i) {
-        for (int ph = 0; ph < 2; ++ph) {
-          const int ti = ph == 0 ? i + 1 : i;
-          if (ti < 0 || ti >= nt) continue;
+        if (i + 1 < nt) {
+          const int ti = i + 1;
           const int64_t tile = cid + static_cast<int64_t>(ti) * ncl;
           const int sgi = find_seg3(a, tile);
           const void* tmap = &a.maps[sgi];
           const int32_t y0 = static_cast<int32_t>((tile - a.seg[sgi].tile0) * T3_ROWS);
-          T3_TRACE(ti, ph);
+          T3_TRACE(ti, 0);
           for (int u = 0; u < U; ++u) {
             for (int b = 0; b < 2; ++b) {
-              const int s = static_cast<int>(sc % NSTAGE);
-              if (fills[s] > 0 && !dead && !mbar_wait(bar(B_STAGE_EMPTY + s), (fills[s] - 1) & 1u)) dead = true;
+              const int s = static_cast<int>(pos % NSTAGE);
+              claim(s);
               mbar_expect_tx(bar(B_STAGE_FULL + s), STAGE_BYTES);
-              tma_load_2d(su32(sStage) + s * STAGE_BYTES, tmap, static_cast<int32_t>(f0 + 64 * (2 * u + b)), y0,
-                          bar(B_STAGE_FULL + s));
-              ++fills[s];
-              ++sc;
+              tma_load_2d_hint(su32(sStage) + s * STAGE_BYTES, tmap, static_cast<int32_t>(f0 + 64 * (2 * u + b)),
+                               y0, bar(B_STAGE_FULL + s), drop);
+              filled(s, 1);
+              ++pos;
             }
-            if (ph == 0) {   // Omega chunks of this unit for MMA1 (one slot: after the rows are on their way)
-              if (om_fills > 0 && !dead && !mbar_wait(bar(B_OM_EMPTY), (om_fills - 1) & 1u)) dead = true;
-              mbar_expect_tx(bar(B_OM_FULL), 2 * chunk_bytes);
-              for (int c = 0; c < 2; ++c)
-                bulk_g2s(su32(sOm) + c * chunk_bytes, a.om16 + (g0 + 2 * u + c) * static_cast<int64_t>(L) * 64,
-                         chunk_bytes, bar(B_OM_FULL));
-              ++om_fills;
-            }
+            // Omega chunks of this unit for MMA1 (one slot: after the rows are on their way)
+            if (om_fills > 0 && !dead && !mbar_wait(bar(B_OM_EMPTY), (om_fills - 1) & 1u)) dead = true;
+            mbar_expect_tx(bar(B_OM_FULL), 2 * chunk_bytes);
+            for (int c = 0; c < 2; ++c)
+              bulk_g2s_hint(su32(sOm) + c * chunk_bytes, a.om16 + (g0 + 2 * u + c) * static_cast<int64_t>(L) * 64,
+                            chunk_bytes, bar(B_OM_FULL), keep);
+            ++om_fills;
+          }
+        }
+        if (i >= 0) {
+          const int ti = i;
+          T3_TRACE(ti, 1);
+          // the converters have written this tile's image (all its bulk copies complete)
+          // (one barrier per tile parity: the other parity's next tile cannot complete before this wait)
+          if (!dead && !mbar_wait(bar(B_IMG_READY + (ti & 1)), static_cast<uint32_t>(ti >> 1) & 1u)) dead = true;
+          for (int u = 0; u < U; ++u) {
+            const int s = static_cast<int>(pos % NSTAGE);
+            claim(s);
+            mbar_expect_tx(bar(B_UNIT_FULL + s), UNIT_BYTES);
+            const int64_t off = img_off(ti, u);
+            if (img_ok(off))
+              bulk_g2s_hint(su32(sStage) + s * STAGE_BYTES, a.img + off, UNIT_BYTES, bar(B_UNIT_FULL + s), drop);
+            else
+              mbar_complete_tx(bar(B_UNIT_FULL + s), UNIT_BYTES);   // complete the phase without a copy
+            filled(s, 2);
+            ++pos;
           }
         }
       }
       // let the last copies land before the CTA may exit
-      for (int s = 0; s < NSTAGE; ++s)
-        if (fills[s] > 0) mbar_wait(bar(B_STAGE_FULL + s), (fills[s] - 1) & 1u);
+      if (n1a > 0) mbar_wait(bar(B_STAGE_FULL + 0), (n1a - 1) & 1u);
+      if (n1b > 0) mbar_wait(bar(B_STAGE_FULL + 1), (n1b - 1) & 1u);
+      if (n2a > 0) mbar_wait(bar(B_UNIT_FULL + 0), (n2a - 1) & 1u);
+      if (n2b > 0) mbar_wait(bar(B_UNIT_FULL + 1), (n2b - 1) & 1u);
       if (om_fills > 0) mbar_wait(bar(B_OM_FULL), (om_fills - 1) & 1u);
     }
   } else if (warp >= CV_WARP0 && warp < CV_WARP0 + CV_WARPS) {
     // ------------------------------------------------------------ converters
     const int cw = warp - CV_WARP0;
-    uint32_t sc = 0, units = 0;
+    const uint64_t keep = l2_policy_evict_last();
+    uint32_t pos = 0, units = 0, f1a = 0, f1b = 0;   // ring position; phase-1 fills seen per slot
     for (int i = -1; i < nt; ++i) {
-      for (int ph = 0; ph < 2; ++ph) {
-        const int ti = ph == 0 ? i + 1 : i;
-        if (ti < 0 || ti >= nt) continue;
+      if (i + 1 < nt) {
+        const int ti = i + 1;
         const int64_t tile = cid + static_cast<int64_t>(ti) * ncl;
         const int sgi = find_seg3(a, tile);
         const int64_t row0 = (tile - a.seg[sgi].tile0) * T3_ROWS;
@@ -266,8 +325,9 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
           if (units >= 2 && !dead && !mbar_wait(bar(B_PAIR_EMPTY + p), ((units >> 1) - 1) & 1u)) dead = true;
           uint8_t* slot = sPair + p * 2 * BLOCK16;
           for (int b = 0; b < 2; ++b) {
-            const int s = static_cast<int>(sc % NSTAGE);
-            if (!dead && !mbar_wait(bar(B_STAGE_FULL + s), (sc / NSTAGE) & 1u)) dead = true;
+            const int s = static_cast<int>(pos % NSTAGE);
+            const uint32_t f1 = s ? f1b++ : f1a++;
+            if (!dead && !mbar_wait(bar(B_STAGE_FULL + s), f1 & 1u)) dead = true;
             const float* src = sStage + s * (STAGE_BYTES / 4);
             const int fb = 2 * u + b;
             // lane: features 4 (lane % 16) .. +3 of row 2 k + lane / 16; (x - c) s = fma(x, s, -c s)
@@ -288,73 +348,103 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(B_STAGE_EMPTY + s));
-            ++sc;
+            ++pos;
           }
           fence_async_cta();
           __syncwarp();
           if (lane == 0) mbar_arrive(bar(B_PAIR_FULL + p));
+          if (cw == 0 && lane == 0) {
+            // once every converter is done with the unit, copy it out for phase 2; the copy of
+            // the tile's previous unit has read its slot by now or soon: release that slot
+            if (!dead && !mbar_wait(bar(B_PAIR_FULL + p), (units >> 1) & 1u)) dead = true;
+            const int64_t off = img_off(ti, u);
+            if (img_ok(off)) bulk_s2g_hint(a.img + off, su32(slot), UNIT_BYTES, keep);
+            bulk_commit();
+            if (u > 0) {
+              bulk_wait_read<1>();
+              mbar_arrive(bar(B_PAIR_EMPTY + (p ^ 1u)));
+            }
+          }
           ++units;
         }
-        if (cw == 0 && lane == 0) T3_TRACE(ti, 2 + ph);
+        if (cw == 0 && lane == 0) {
+          // the tile's image is complete in global memory: phase 2 may load it
+          bulk_wait_all();
+          mbar_arrive(bar(B_PAIR_EMPTY + ((units - 1) & 1u)));
+          mbar_arrive(bar(B_IMG_READY + (ti & 1)));
+        }
+        __syncwarp();
+        if (cw == 0 && lane == 0) T3_TRACE(ti, 2);
       }
+      if (i >= 0) pos += U;   // phase 2 of tile i passes through the ring without the converters
     }
   } else if (warp == MMA3_WARP) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t id1 = idesc_fmt<FMT>(T3_ROWS, L, 0, 0);
       const uint32_t id2 = idesc_fmt<FMT>(T3_ROWS, L, 1, 0);
-      uint32_t units = 0, om_uses = 0;
+      uint32_t pos = 0, units = 0, om_uses = 0, f2a = 0, f2b = 0;   // phase-2 fills seen per slot
       tc_fence_after();
       for (int i = -1; i < nt; ++i) {
-        for (int ph = 0; ph < 2; ++ph) {
-          const int ti = ph == 0 ? i + 1 : i;
-          if (ti < 0 || ti >= nt) continue;
+        if (i + 1 < nt) {   // MMA1 of tile i+1 on the converted units
+          const int ti = i + 1;
           const uint32_t d1 = tmem + static_cast<uint32_t>((ti & 1) * L);
-          if (ph == 0 && ti >= 2 && !dead && !mbar_wait(bar(B_D1_EMPTY + (ti & 1)), ((ti >> 1) - 1) & 1u)) dead = true;
-          if (ph == 1 && !dead && !mbar_wait(bar(B_G_READY), static_cast<uint32_t>(ti) & 1u)) dead = true;
-          const bool zero_h = ti == 0 || drain_tile(ti - 1, nt, a.drain_every);
+          if (ti >= 2 && !dead && !mbar_wait(bar(B_D1_EMPTY + (ti & 1)), ((ti >> 1) - 1) & 1u)) dead = true;
           tc_fence_after();
           for (int u = 0; u < U; ++u) {
             const uint32_t p = units & 1u;
             if (!dead && !mbar_wait(bar(B_PAIR_FULL + p), (units >> 1) & 1u)) dead = true;
             const uint32_t slot = su32(sPair) + p * 2 * BLOCK16;
-            if (ph == 0) {
-              if (!dead && !mbar_wait(bar(B_OM_FULL), om_uses & 1u)) dead = true;
-              tc_fence_after();
-              if (!dead) {
-                const uint64_t dA = sdesc(slot, 16, 1024);
-                const uint64_t dB = sdesc(su32(sOm), 16, 1024);
+            if (!dead && !mbar_wait(bar(B_OM_FULL), om_uses & 1u)) dead = true;
+            tc_fence_after();
+            if (!dead) {
+              const uint64_t dA = sdesc(slot, 16, 1024);
+              const uint64_t dB = sdesc(su32(sOm), 16, 1024);
 #pragma unroll
-                for (int b = 0; b < 2; ++b)
+              for (int b = 0; b < 2; ++b)
 #pragma unroll
-                  for (int kk = 0; kk < 4; ++kk)
-                    mma_bf16(d1, dA + ((static_cast<uint32_t>(b) * BLOCK16 + kk * 32u) >> 4),
-                             dB + ((static_cast<uint32_t>(b) * chunk_bytes + kk * 32u) >> 4), id1,
-                             (u | b | kk) != 0 ? 1u : 0u);
-              }
-              mma_commit(bar(B_OM_EMPTY));
-              ++om_uses;
-            } else {
-              tc_fence_after();
-              if (!dead) {
-                const uint64_t dA2 = sdesc(slot, BLOCK16, 1024);    // MN-major: features x rows
-                const uint64_t dB2 = sdesc(su32(sGt), 16, 1024);   // K-major: L x rows
-#pragma unroll
-                for (int ks = 0; ks < T3_ROWS / 16; ++ks)
-#pragma unroll
-                  for (int h = 0; h < GS; ++h)
-                    mma_bf16(tH + static_cast<uint32_t>(u * L), dA2 + ((static_cast<uint32_t>(ks) * 2048u) >> 4),
-                             dB2 + ((static_cast<uint32_t>(h) * static_cast<uint32_t>(L) * 128u +
-                                     static_cast<uint32_t>(ks >> 2) * GT_CHUNK +
-                                     static_cast<uint32_t>(ks & 3) * 32u) >> 4),
-                             id2, (zero_h && ks == 0 && h == 0) ? 0u : 1u);
-              }
+                for (int kk = 0; kk < 4; ++kk)
+                  mma_bf16(d1, dA + ((static_cast<uint32_t>(b) * BLOCK16 + kk * 32u) >> 4),
+                           dB + ((static_cast<uint32_t>(b) * chunk_bytes + kk * 32u) >> 4), id1,
+                           (u | b | kk) != 0 ? 1u : 0u);
             }
+            mma_commit(bar(B_OM_EMPTY));
+            ++om_uses;
             mma_commit(bar(B_PAIR_EMPTY + p));
             ++units;
+            pos += 2;
           }
-          mma_commit(ph == 0 ? bar(B_D1_FULL + (ti & 1)) : bar(B_MMA2_DONE));
-          T3_TRACE(ti, 4 + ph);
+          mma_commit(bar(B_D1_FULL + (ti & 1)));
+          T3_TRACE(ti, 4);
+        }
+        if (i >= 0) {   // MMA2 of tile i on its image units, as they land in the ring
+          const int ti = i;
+          if (!dead && !mbar_wait(bar(B_G_READY), static_cast<uint32_t>(ti) & 1u)) dead = true;
+          const bool zero_h = ti == 0 || drain_tile(ti - 1, nt, a.drain_every);
+          tc_fence_after();
+          for (int u = 0; u < U; ++u) {
+            const int s = static_cast<int>(pos % NSTAGE);
+            const uint32_t f2 = s ? f2b++ : f2a++;
+            if (!dead && !mbar_wait(bar(B_UNIT_FULL + s), f2 & 1u)) dead = true;
+            tc_fence_after();
+            if (!dead) {
+              const uint64_t dA2 = sdesc(su32(sStage) + s * STAGE_BYTES, BLOCK16, 1024);   // MN-major: features x rows
+              const uint64_t dB2 = sdesc(su32(sGt), 16, 1024);                           // K-major: L x rows
+#pragma unroll
+              for (int ks = 0; ks < T3_ROWS / 16; ++ks)
+#pragma unroll
+                for (int h = 0; h < GS; ++h)
+                  mma_bf16(tH + static_cast<uint32_t>(u * L), dA2 + ((static_cast<uint32_t>(ks) * 2048u) >> 4),
+                           dB2 + ((static_cast<uint32_t>(h) * static_cast<uint32_t>(L) * 128u +
+                                   static_cast<uint32_t>(ks >> 2) * GT_CHUNK +
+                                   static_cast<uint32_t>(ks & 3) * 32u) >> 4),
+                           id2, (zero_h && ks == 0 && h == 0) ? 0u : 1u);
+            }
+            mma_commit(bar(B_SLOT_EMPTY + s));
+            ++pos;
+          }
+          mma_commit(bar(B_MMA2_DONE));
+          T3_TRACE(ti, 5);
         }
       }
       // every MMA of this CTA has completed before TMEM is released
@@ -738,6 +828,8 @@ cudaError_t tc3_pass(const State& s, const TcWork& w, const TcPending& pend, cud
   args.drain_every = w.fmt == FMT_F16 ? 2 : 4;   // 32 MMAs per TMEM accumulation of H either way
   args.shift = s.shift;
   args.om16 = w.om16;
+  args.img = w.img;
+  args.img_halves = static_cast<int64_t>(cfg.nclusters) * cfg.CS * cfg.w * 256;
   args.scale = w.fmt == FMT_F16 ? w.scale : nullptr;
   args.Hpart = w.Hpart;
   args.gram_part = w.gram_part;

@@ -169,7 +169,8 @@ void free_all(spca_session* s) {
                   s->simt.gram_part, s->simt.sG_part, s->simt.Hpart, s->simt.cs_part, s->shift_part, s->fin.Hbar,
                   s->fin.gbar, s->fin.T, s->fin.X, s->fin.W, s->fin.lam, s->fin.Bt, s->fin.Cpart, s->fin.C,
                   s->fin.sig, s->fin.info, s->fin_sigma, s->fin_V, s->dstage[0], s->dstage[1],
-                  s->tcw.om16, s->tcw.Hpart, s->tcw.gram_part, s->tcw.sG_part, s->tcw.scale, s->tcw.scale_bits};
+                  s->tcw.om16, s->tcw.Hpart, s->tcw.gram_part, s->tcw.sG_part, s->tcw.scale, s->tcw.scale_bits,
+                  s->tcw.img};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < 2; ++i) {
@@ -272,6 +273,7 @@ size_t session_footprint(int64_t n, int k, int p, int math, int64_t max_block_ro
     if (t.v3 && int64_t(t.cfg3.nclusters) * t.cfg3.CS > nctas) nctas = int64_t(t.cfg3.nclusters) * t.cfg3.CS;
     add(npad * L, 2); add(1, 4); add(1, 4); add((hp > hp3 ? hp : hp3) * L, 4); add(nctas * L * L, 8);
     add(nctas * L, 8);
+    if (t.v3) add(hp3 * 256, 2);
   }
   add(int64_t(kShiftParts) * n, 8);
   const int64_t per = int64_t(L) * L * 8;
@@ -308,6 +310,7 @@ spca_status session_finalize_async(spca_session* s, double* sigma_dev, double* V
 }
 
 spca_status session_flags_status(spca_session* s, int flags) {
+  if (flags & 8) return fail(s, SPCA_E_CUDA, "a copy of the tensor-core pass was out of its buffer (skipped)");
   if (flags & 2) return fail(s, SPCA_E_TIMEOUT, "a bounded device wait gave up during the pass");
   if (flags & 1) return fail(s, SPCA_E_NUMERIC, "non-finite values (NaN/Inf) reached the sketch");
   return SPCA_OK;
@@ -425,6 +428,7 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
     CC(dalloc(&t.Hpart, size_t(hp > hp3 ? hp : hp3) * L));
     CC(dalloc(&t.gram_part, size_t(nctas) * L * L));
     CC(dalloc(&t.sG_part, size_t(nctas) * L));
+    if (t.v3) CC(dalloc(&t.img, size_t(hp3) * 256));
   }
   CC(dalloc(&s->shift_part, size_t(kShiftParts) * n));
 
@@ -581,6 +585,7 @@ spca_status spca_finalize(spca_session* s, double* sigma, double* V, int32_t out
   // the non-finite flag is read after the finalisation kernels so that the stream never idles mid-call
   CU(cudaMemcpyAsync(s->host_flags, s->flags, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CU(cudaStreamSynchronize(s->stream));
+  if (s->host_flags[0] & 8) return fail(s, SPCA_E_CUDA, "a copy of the tensor-core pass was out of its buffer (skipped)");
   if (s->host_flags[0] & 2) return fail(s, SPCA_E_TIMEOUT, "a bounded device wait gave up during the pass");
   if (s->host_flags[0] & 1) return fail(s, SPCA_E_NUMERIC, "non-finite values (NaN/Inf) reached the sketch");
   return SPCA_OK;

@@ -105,6 +105,7 @@ struct TcWork {
   float* Hpart;          // nclusters x (CS*w) x L; column l carries the column sums
   double* gram_part;     // nclusters*CS x L x L
   double* sG_part;       // nclusters*CS x L
+  uint16_t* img;         // pipelined kernel: converted operand images, nclusters*CS x 2 tiles x 128 w
 };
 
 constexpr int kTcPendingMax = 48;       // row blocks batched into one launch
