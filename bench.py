@@ -211,14 +211,23 @@ def roofline_for(math_name, prof, bytes_total, rows_total, pk):
             "algorithmic_bytes_per_launch": bytes_total / max(dom_launches, 1)}
 
 
+TC_KERNEL_SOURCES = ("sketch_tc3.cu", "tc_ptx.cuh")   # the pipelined kernel that runs the pass
+
+
+def tc_source_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for name in TC_KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1704_07669_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_record(math_name):
     """DRAM bytes per row of the fused kernel from a committed ncu capture, if it was taken on
-    the kernel source as it is now (the record stores the source's SHA-256)."""
-    import hashlib
+    the kernel sources as they are now (the record stores their SHA-256)."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "tc_sketch_traffic.json")))[math_name]
-        src = open(os.path.join(ROOT, "paper_1704_07669_gb300", "csrc", "sketch_tc.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+        if tc_source_sha256() != rec["source_sha256"]:
             return None
         return rec
     except Exception:

@@ -41,7 +41,7 @@ constexpr uint32_t STAGE_BYTES = T3_ROWS * 64 * 4;   // FP32: 128 rows x 64 feat
 constexpr uint32_t BLOCK16 = T3_ROWS * 64 * 2;       // 16-bit: 128 rows x 64 features
 constexpr int T3_MAX_UNITS = 6;                      // w <= 768
 constexpr uint32_t GT_CHUNK = 128u * 128u;   // G^T operand chunk: 128 rows (hi, lo, zero) x 64 tile rows
-constexpr int T3_GRAM_PER_THREAD = 4;        // G'^T G' entries per reduce-group thread
+constexpr int T3_GRAM_PER_THREAD = 4;        // G'^T G' entries per converter thread
 constexpr uint32_t TMEM3_COLS = 512;
 constexpr int T3_MAX_SEGS = 48;
 
@@ -141,7 +141,8 @@ enum {
   B_PUB_READY,                         // [2]
   B_FINAL = B_PUB_READY + 2,           // the MMA issuer's last commit
   B_IMG_READY,                         // [2] a tile's operand image is in global memory (tile parity)
-  B_COUNT = B_IMG_READY + 2
+  B_GT_FREE = B_IMG_READY + 2,         // the converters' Gram products are done with the G^T tile
+  B_COUNT
 };
 static_assert(B_COUNT <= 64, "barrier slots: 16 x 32 bytes in the layout");
 
@@ -219,6 +220,7 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
     mbar_init(bar(B_FINAL), 1);
     mbar_init(bar(B_IMG_READY), 1);
     mbar_init(bar(B_IMG_READY + 1), 1);
+    mbar_init(bar(B_GT_FREE), CV_WARPS);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -311,8 +313,34 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
   } else if (warp >= CV_WARP0 && warp < CV_WARP0 + CV_WARPS) {
     // ------------------------------------------------------------ converters
     const int cw = warp - CV_WARP0;
+    constexpr int CVT = CV_WARPS * 32;
+    const int ctid = tid - CV_WARP0 * 32;
     const uint64_t keep = l2_policy_evict_last();
     uint32_t pos = 0, units = 0, f1a = 0, f1b = 0;   // ring position; phase-1 fills seen per slot
+    // G'^T G' (columns < l, lower triangle): once G^T of a tile is pulled every CTA holds all 128
+    // of its rows, so the cluster splits the entries - this thread takes e = rank CVT + ctid +
+    // k CVT CS - and works on them while phase 2 of the tile runs. Products of the 16-bit terms
+    // are exact in FP32 and summed as double-float pairs.
+    const int LTl = l * (l + 1) / 2;
+    F2Acc gram_acc[T3_GRAM_PER_THREAD];
+    int gc1[T3_GRAM_PER_THREAD], gc2[T3_GRAM_PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < T3_GRAM_PER_THREAD; ++k) {
+      const int e = static_cast<int>(rank) * CVT + ctid + k * CVT * CS;
+      int c1 = 0, c2 = 0;
+      if (e < LTl) {
+        c1 = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) - 1.f) * 0.5f);
+        while (c1 * (c1 + 1) / 2 > e) --c1;
+        while ((c1 + 1) * (c1 + 2) / 2 <= e) ++c1;
+        c2 = e - c1 * (c1 + 1) / 2;
+      }
+      gc1[k] = e < LTl ? c1 : -1;
+      gc2[k] = c2;
+    }
+    auto gt_off = [&](int h, int lc, int g) {
+      return static_cast<uint32_t>(g >> 3) * GT_CHUNK + static_cast<uint32_t>((h * L + lc) >> 3) * 1024u +
+             sw128(static_cast<uint32_t>(lc & 7), static_cast<uint32_t>(g & 7) * 16u);
+    };
     for (int i = -1; i < nt; ++i) {
       if (i + 1 < nt) {
         const int ti = i + 1;
@@ -376,7 +404,48 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
         __syncwarp();
         if (cw == 0 && lane == 0) T3_TRACE(ti, 2);
       }
-      if (i >= 0) pos += U;   // phase 2 of tile i passes through the ring without the converters
+      if (i >= 0) {
+        pos += U;   // phase 2 of tile i passes through the ring without the converters
+        // meanwhile: this thread's entries of G'^T G' over the tile's 128 rows
+        if (!dead && !mbar_wait(bar(B_G_READY), static_cast<uint32_t>(i) & 1u)) dead = true;
+#pragma unroll
+        for (int k = 0; k < T3_GRAM_PER_THREAD; ++k) {
+          if (gc1[k] < 0) continue;
+          for (int g = 0; g < T3_ROWS / 8; ++g) {
+            float x1[GS][8], x2[GS][8];
+#pragma unroll
+            for (int h = 0; h < GS; ++h) {
+              unpack8<FMT>(*reinterpret_cast<const uint4*>(sGt + gt_off(h, gc1[k], g)), x1[h]);
+              unpack8<FMT>(*reinterpret_cast<const uint4*>(sGt + gt_off(h, gc2[k], g)), x2[h]);
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+              gram_acc[k].add(x1[0][r] * x2[0][r]);
+              if constexpr (GS == 2) {
+                gram_acc[k].add(x1[0][r] * x2[1][r]);
+                gram_acc[k].add(x1[1][r] * x2[0][r]);
+                gram_acc[k].add(x1[1][r] * x2[1][r]);
+              }
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_GT_FREE));
+      }
+    }
+    {
+      const int LL = L * L;
+      const int64_t cta = static_cast<int64_t>(cid) * CS + rank;
+      for (int e = ctid; e < LL; e += CVT) a.gram_part[cta * LL + e] = 0.0;
+      named_bar(2, CVT);
+      const double s2 = static_cast<double>(inv_s) * inv_s;
+#pragma unroll
+      for (int k = 0; k < T3_GRAM_PER_THREAD; ++k) {
+        if (gc1[k] < 0) continue;
+        const double v = gram_acc[k].value() * s2;
+        a.gram_part[cta * LL + gc1[k] * L + gc2[k]] = v;
+        a.gram_part[cta * LL + gc2[k] * L + gc1[k]] = v;
+      }
     }
   } else if (warp == MMA3_WARP) {
     // ------------------------------------------------------------ MMA issuer
@@ -455,48 +524,36 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
     // ------------------------------------------------------------ reduce group (warps 0-3)
     const int q = warp;   // TMEM lane quadrant
     F2Acc sg_acc;
-    // G'^T G' (columns < l, lower triangle): after the pull every CTA holds all 128 rows of the
-    // tile, so the cluster splits the entries - this thread takes e = rank 128 + tid + k 128 CS.
-    // Products of the 16-bit terms are exact in FP32 and summed as double-float pairs.
-    const int LTl = l * (l + 1) / 2;
-    F2Acc gram_acc[T3_GRAM_PER_THREAD];
-    int gc1[T3_GRAM_PER_THREAD], gc2[T3_GRAM_PER_THREAD];
-#pragma unroll
-    for (int k = 0; k < T3_GRAM_PER_THREAD; ++k) {
-      const int e = static_cast<int>(rank) * RG_THREADS + tid + k * RG_THREADS * CS;
-      int c1 = 0, c2 = 0;
-      if (e < LTl) {
-        c1 = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) - 1.f) * 0.5f);
-        while (c1 * (c1 + 1) / 2 > e) --c1;
-        while ((c1 + 1) * (c1 + 2) / 2 <= e) ++c1;
-        c2 = e - c1 * (c1 + 1) / 2;
-      }
-      gc1[k] = e < LTl ? c1 : -1;
-      gc2[k] = c2;
-    }
-    auto gt_off = [&](int h, int lc, int g) {
-      return static_cast<uint32_t>(g >> 3) * GT_CHUNK + static_cast<uint32_t>((h * L + lc) >> 3) * 1024u +
-             sw128(static_cast<uint32_t>(lc & 7), static_cast<uint32_t>(g & 7) * 16u);
-    };
     bool drained = false;
     const int r0 = static_cast<int>(rank) * RPC;
     auto drain_h = [&]() {
-      const int cpr = L / 8;
-      for (int ch = 0; ch < U * cpr; ++ch) {
-        const int mt = ch / cpr, c = (ch - mt * cpr) * 8;
-        float v[8];
-        tmem_ld8(tH + static_cast<uint32_t>(mt * L + c) + (static_cast<uint32_t>(q * 32) << 16), v);
+      for (int ch = 0; ch < U * L; ch += 32) {   // 32 columns of a unit: four loads, one wait, adds
+        const int mt = ch / L, c0 = ch - mt * L;
+        uint32_t r[32];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] *= (c + e == l ? inv_s : inv_s * inv_s);   // H carries s^2, sums s
+        for (int j = 0; j < 4; ++j)
+          if (c0 + 8 * j < L)
+            tmem_ld8_issue(tH + static_cast<uint32_t>(mt * L + c0 + 8 * j) + (static_cast<uint32_t>(q * 32) << 16),
+                           r + 8 * j);
+        tmem_wait_ld();
         const int64_t feat = f0 + mt * 128 + q * 32 + lane;
-        float4* dst = reinterpret_cast<float4*>(a.Hpart + (static_cast<int64_t>(cid) * (CS * static_cast<int64_t>(w)) +
-                                                            feat) * L + c);
-        if (drained) {   // added in L2; this thread is the only writer of these entries
-          red_add_v4(reinterpret_cast<float*>(dst), v[0], v[1], v[2], v[3]);
-          red_add_v4(reinterpret_cast<float*>(dst + 1), v[4], v[5], v[6], v[7]);
-        } else {
-          dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-          dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+        float* row = a.Hpart + (static_cast<int64_t>(cid) * (CS * static_cast<int64_t>(w)) + feat) * L + c0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (c0 + 8 * j < L) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)   // H carries s^2, sums s
+              v[e] = __uint_as_float(r[8 * j + e]) * (c0 + 8 * j + e == l ? inv_s : inv_s * inv_s);
+            float4* dst = reinterpret_cast<float4*>(row + 8 * j);
+            if (drained) {   // added in L2; this thread is the only writer of these entries
+              red_add_v4(reinterpret_cast<float*>(dst), v[0], v[1], v[2], v[3]);
+              red_add_v4(reinterpret_cast<float*>(dst + 1), v[4], v[5], v[6], v[7]);
+            } else {
+              dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+              dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+            }
+          }
         }
       }
       drained = true;
@@ -514,13 +571,23 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
       tc_fence_after();
       {
         const int row = q * 32 + lane;
-        const uint32_t d1 = tmem + static_cast<uint32_t>((i & 1) * L);
-        for (int c = 0; c < L; c += 8) {
-          float v[8];
-          tmem_ld8(d1 + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c), v);
-          float4* dst = reinterpret_cast<float4*>(sX + row * xld + c);
-          dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-          dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+        const uint32_t d1 = tmem + static_cast<uint32_t>((i & 1) * L) + (static_cast<uint32_t>(q * 32) << 16);
+        for (int c0 = 0; c0 < L; c0 += 32) {   // 32 columns: four loads issued before one wait
+          uint32_t r[32];
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (c0 + 8 * j < L) tmem_ld8_issue(d1 + static_cast<uint32_t>(c0 + 8 * j), r + 8 * j);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (c0 + 8 * j < L) {
+              float4* dst = reinterpret_cast<float4*>(sX + row * xld + c0 + 8 * j);
+              dst[0] = make_float4(__uint_as_float(r[8 * j]), __uint_as_float(r[8 * j + 1]),
+                                   __uint_as_float(r[8 * j + 2]), __uint_as_float(r[8 * j + 3]));
+              dst[1] = make_float4(__uint_as_float(r[8 * j + 4]), __uint_as_float(r[8 * j + 5]),
+                                   __uint_as_float(r[8 * j + 6]), __uint_as_float(r[8 * j + 7]));
+            }
+          }
         }
       }
       tc_fence_before();
@@ -617,6 +684,8 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
         if (!dead && !mbar_wait(bar(B_MMA2_DONE), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
         tc_fence_after();
         if (drain_tile(i - 1, nt, a.drain_every)) drain_h();
+        // the converters' Gram products of the previous tile no longer read the G^T tile
+        if (!dead && !mbar_wait(bar(B_GT_FREE), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
       }
       {
         const int total = GS * L * (T3_ROWS / 8);
@@ -646,29 +715,6 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
       fence_async_cta();
       mbar_arrive(bar(B_G_READY));
       if (tid == 0) T3_TRACE(i, 9);
-      named_bar(1, RG_THREADS);   // the whole G^T tile is in place
-      // this thread's entries of G'^T G' over the tile's 128 rows
-#pragma unroll
-      for (int k = 0; k < T3_GRAM_PER_THREAD; ++k) {
-        if (gc1[k] < 0) continue;
-        for (int g = 0; g < T3_ROWS / 8; ++g) {
-          float x1[GS][8], x2[GS][8];
-#pragma unroll
-          for (int h = 0; h < GS; ++h) {
-            unpack8<FMT>(*reinterpret_cast<const uint4*>(sGt + gt_off(h, gc1[k], g)), x1[h]);
-            unpack8<FMT>(*reinterpret_cast<const uint4*>(sGt + gt_off(h, gc2[k], g)), x2[h]);
-          }
-#pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            gram_acc[k].add(x1[0][r] * x2[0][r]);
-            if constexpr (GS == 2) {
-              gram_acc[k].add(x1[0][r] * x2[1][r]);
-              gram_acc[k].add(x1[1][r] * x2[0][r]);
-              gram_acc[k].add(x1[1][r] * x2[1][r]);
-            }
-          }
-        }
-      }
     }
     // the last tile's MMA2, then its drain
     if (nt > 0) {
@@ -679,20 +725,7 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
       for (int64_t e = tid; e < static_cast<int64_t>(w) * L; e += RG_THREADS)
         a.Hpart[(static_cast<int64_t>(cid) * CS * w + f0) * L + e] = 0.f;
     }
-    const int LL = L * L;
     const int64_t cta = static_cast<int64_t>(cid) * CS + rank;
-    for (int e = tid; e < LL; e += RG_THREADS) a.gram_part[cta * LL + e] = 0.0;
-    named_bar(1, RG_THREADS);
-    {
-      const double s2 = static_cast<double>(inv_s) * inv_s;
-#pragma unroll
-      for (int k = 0; k < T3_GRAM_PER_THREAD; ++k) {
-        if (gc1[k] < 0) continue;
-        const double v = gram_acc[k].value() * s2;
-        a.gram_part[cta * LL + gc1[k] * L + gc2[k]] = v;
-        a.gram_part[cta * LL + gc2[k] * L + gc1[k]] = v;
-      }
-    }
     if (tid < L) a.sG_part[cta * L + tid] = sg_acc.value() * inv_s;
   }
   if (dead) atomicOr(a.flags, 2);
@@ -741,9 +774,9 @@ bool tc3_config(int64_t n, int L, int fmt, TcConfig* cfg) {
     int64_t w = (n + CS - 1) / CS;
     w = ((w + 127) / 128) * 128;
     // TMEM: two D1 buffers and H (w / 128 tiles of L columns); the cluster's 128 CS reduce
-    // threads take at most T3_GRAM_PER_THREAD entries of G'^T G' each
+    // converter threads take at most T3_GRAM_PER_THREAD entries of G'^T G' each
     if (w / 128 > T3_MAX_UNITS || 2 * L + (w / 128) * L > static_cast<int64_t>(TMEM3_COLS)) continue;
-    if (static_cast<int64_t>(CS) * RG_THREADS * T3_GRAM_PER_THREAD < static_cast<int64_t>(L) * (L + 1) / 2) continue;
+    if (static_cast<int64_t>(CS) * CV_WARPS * 32 * T3_GRAM_PER_THREAD < static_cast<int64_t>(L) * (L + 1) / 2) continue;
     const Tc3Layout lay = tc3_layout(L, static_cast<int>(w), CS, gs);
     if (lay.total > 227u * 1024u) continue;
     cfg->CS = CS;
