@@ -170,15 +170,23 @@ __global__ void shift_partial_kernel(const T* __restrict__ rows, int64_t m, int6
   if (j >= n) return;
   const int64_t r0 = blockIdx.y * rows_per_part;
   const int64_t r1 = r0 + rows_per_part < m ? r0 + rows_per_part : m;
-  double acc = 0.0;
-  for (int64_t i = r0; i < r1; ++i) {
-    if constexpr (std::is_same<T, double>::value) {
-      acc += rows[i * ld + j];
-    } else {
-      acc += static_cast<double>(Elem<T>::get(rows, i * ld + j, scale));
+  if constexpr (std::is_same<T, double>::value) {
+    double acc = 0.0;
+    for (int64_t i = r0; i < r1; ++i) acc += rows[i * ld + j];
+    part[blockIdx.y * n + j] = acc;
+  } else {
+    // FP64 adds issue at a small fraction of the FP32 rate here: sum as an FP32 pair instead
+    // (Knuth's two-sum keeps each add's rounding error, about 48 significant bits in all)
+    float hi = 0.f, lo = 0.f;
+    for (int64_t i = r0; i < r1; ++i) {
+      const float x = Elem<T>::get(rows, i * ld + j, scale);
+      const float s = hi + x;
+      const float bb = s - hi;
+      lo += (hi - (s - bb)) + (x - bb);
+      hi = s;
     }
+    part[blockIdx.y * n + j] = static_cast<double>(hi) + static_cast<double>(lo);
   }
-  part[blockIdx.y * n + j] = acc;
 }
 
 __global__ void shift_final_kernel(const double* __restrict__ part, int parts, int64_t n, int64_t m,

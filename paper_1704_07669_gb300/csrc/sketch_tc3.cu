@@ -138,8 +138,9 @@ enum {
   B_MMA2_DONE,
   B_XCH_READY,
   B_XCH_FREE,
-  B_PUB_READY,                         // [2]
-  B_FINAL = B_PUB_READY + 2,           // the MMA issuer's last commit
+  B_PEER_FREE,                         // every peer's G^T buffer may be written (cluster scope)
+  B_GT_FULL,                           // every peer has stored its rows of G^T here (cluster scope)
+  B_FINAL,                             // the MMA issuer's last commit
   B_IMG_READY,                         // [2] a tile's operand image is in global memory (tile parity)
   B_GT_FREE = B_IMG_READY + 2,         // the converters' Gram products are done with the G^T tile
   B_COUNT
@@ -147,7 +148,10 @@ enum {
 static_assert(B_COUNT <= 64, "barrier slots: 16 x 32 bytes in the layout");
 
 // tile i of this cluster is a drain tile: H leaves TMEM after its MMA2
-__device__ __forceinline__ bool drain_tile(int i, int nt, int every) { return ((i + 1) % every == 0) || (i == nt - 1); }
+// (clusters drain at staggered tiles, so that not all of them load L2 with reductions at once)
+__device__ __forceinline__ bool drain_tile(int i, int nt, int every, uint32_t cid) {
+  return ((i + 1 + static_cast<int>(cid)) % every == 0) || (i == nt - 1);
+}
 
 template <int FMT>
 __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_constant__ Tc3Args a) {
@@ -209,7 +213,6 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
       mbar_init(bar(B_PAIR_EMPTY + p), 2);   // MMA1 done, and the image copy has read the slot
       mbar_init(bar(B_D1_FULL + p), 1);
       mbar_init(bar(B_D1_EMPTY + p), RG_THREADS);
-      mbar_init(bar(B_PUB_READY + p), static_cast<uint32_t>(CS));
     }
     mbar_init(bar(B_OM_FULL), 1);
     mbar_init(bar(B_OM_EMPTY), 1);
@@ -218,6 +221,8 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
     mbar_init(bar(B_XCH_READY), static_cast<uint32_t>(CS));
     mbar_init(bar(B_XCH_FREE), static_cast<uint32_t>(CS));
     mbar_init(bar(B_FINAL), 1);
+    mbar_init(bar(B_PEER_FREE), static_cast<uint32_t>(CS));
+    mbar_init(bar(B_GT_FULL), static_cast<uint32_t>(CS));
     mbar_init(bar(B_IMG_READY), 1);
     mbar_init(bar(B_IMG_READY + 1), 1);
     mbar_init(bar(B_GT_FREE), CV_WARPS);
@@ -489,7 +494,7 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
         if (i >= 0) {   // MMA2 of tile i on its image units, as they land in the ring
           const int ti = i;
           if (!dead && !mbar_wait(bar(B_G_READY), static_cast<uint32_t>(ti) & 1u)) dead = true;
-          const bool zero_h = ti == 0 || drain_tile(ti - 1, nt, a.drain_every);
+          const bool zero_h = ti == 0 || drain_tile(ti - 1, nt, a.drain_every, cid);
           tc_fence_after();
           for (int u = 0; u < U; ++u) {
             const int s = static_cast<int>(pos % NSTAGE);
@@ -640,6 +645,19 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
         fence_acq_rel_cluster();
         mbar_arrive_cluster(mapa(bar(B_XCH_FREE), static_cast<uint32_t>(lane)));
       }
+      // 3. the previous tile's MMA2 and Gram products are done with this CTA's G^T buffer: say
+      //    so to every peer, then drain H if due
+      if (i >= 1) {
+        if (!dead && !mbar_wait(bar(B_MMA2_DONE), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
+        if (!dead && !mbar_wait(bar(B_GT_FREE), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
+        if (warp == 0 && lane < CS) {
+          fence_acq_rel_cluster();
+          mbar_arrive_cluster(mapa(bar(B_PEER_FREE), static_cast<uint32_t>(lane)));
+        }
+        tc_fence_after();
+        if (drain_tile(i - 1, nt, a.drain_every, cid)) drain_h();
+      }
+      // 4. pack the own rows of G' (FP16: hi and lo) ...
       uint4* pub = sPub + (i & 1) * (GS * L * G8);
       for (int it = tid; it < L * G8; it += RG_THREADS) {
         const int lc = it / G8, g = it % G8;
@@ -658,13 +676,8 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
         }
       }
       if (tid == 0) T3_TRACE(i, 13);
-      named_bar(1, RG_THREADS);
-      if (warp == 0 && lane < CS) {
-        fence_acq_rel_cluster();
-        mbar_arrive_cluster(mapa(bar(B_PUB_READY + (i & 1)), static_cast<uint32_t>(lane)));
-      }
-      // sums of G and the G output of the own rows: off the path to G^T, done while the peers
-      // publish (sY stays valid until this group writes the next tile's rows)
+      // sums of G and the G output of the own rows (sY stays valid until this group writes the
+      // next tile's rows)
       if (tid < L) {
         for (int rr = 0; rr < RPC; ++rr) sg_acc.add(sY[rr * L + tid]);
       }
@@ -675,43 +688,30 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
           if (grow < mseg) a.seg[sgi].gout[grow * l + c] = sY[rr * L + c] * inv_s;
         }
       }
+      named_bar(1, RG_THREADS);
       if (tid == 0) T3_TRACE(i, 14);
-      // 3. the previous tile's MMA2 is done: drain H if due, then pull G'(i) into the operand
+      // ... and store them into every peer's G^T operand once every peer's buffer is free
+      if (i >= 1 && !dead && !mbar_wait_cluster(bar(B_PEER_FREE), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
       if (tid == 0) T3_TRACE(i, 11);
-      if (!dead && !mbar_wait_cluster(bar(B_PUB_READY + (i & 1)), static_cast<uint32_t>(i >> 1) & 1u)) dead = true;
-      if (tid == 0) T3_TRACE(i, 8);
-      if (i >= 1) {
-        if (!dead && !mbar_wait(bar(B_MMA2_DONE), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
-        tc_fence_after();
-        if (drain_tile(i - 1, nt, a.drain_every)) drain_h();
-        // the converters' Gram products of the previous tile no longer read the G^T tile
-        if (!dead && !mbar_wait(bar(B_GT_FREE), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
-      }
       {
-        const int total = GS * L * (T3_ROWS / 8);
-        for (int it0 = tid; it0 < total; it0 += 4 * RG_THREADS) {   // four remote loads in flight
-          uint4 pk[4];
-          uint32_t off[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int it = it0 + j * RG_THREADS;
-            off[j] = 0xFFFFFFFFu;
-            if (it < total) {
-              const int h = it / (L * (T3_ROWS / 8));
-              const int rem = it - h * (L * (T3_ROWS / 8));
-              const int lc = rem / (T3_ROWS / 8), g = rem % (T3_ROWS / 8);
-              const int pp = g / G8, gl = g % G8;
-              pk[j] = ld_dsmem_v4u(
-                  mapa(su32(sPub + (i & 1) * (GS * L * G8) + (h * L + lc) * G8 + gl), static_cast<uint32_t>(pp)));
-              off[j] = static_cast<uint32_t>(g >> 3) * GT_CHUNK + static_cast<uint32_t>((h * L + lc) >> 3) * 1024u +
-                       sw128(static_cast<uint32_t>(lc & 7), static_cast<uint32_t>(g & 7) * 16u);
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (off[j] != 0xFFFFFFFFu) *reinterpret_cast<uint4*>(sGt + off[j]) = pk[j];
+        const int nitems = GS * L * G8;
+        for (int t = tid; t < nitems * CS; t += RG_THREADS) {
+          const int it = t % nitems, pp = t / nitems;
+          const int h = it / (L * G8), rem = it - h * (L * G8), lc = rem / G8, gl = rem % G8;
+          const int g = static_cast<int>(rank) * G8 + gl;
+          const uint32_t off = static_cast<uint32_t>(g >> 3) * GT_CHUNK + static_cast<uint32_t>((h * L + lc) >> 3) * 1024u +
+                               sw128(static_cast<uint32_t>(lc & 7), static_cast<uint32_t>(g & 7) * 16u);
+          st_dsmem_v4u(mapa(su32(sGt + off), static_cast<uint32_t>(pp)), pub[it]);
         }
       }
+      fence_proxy_async_all();
+      named_bar(1, RG_THREADS);
+      if (warp == 0 && lane < CS) {
+        fence_acq_rel_cluster();
+        mbar_arrive_cluster(mapa(bar(B_GT_FULL), static_cast<uint32_t>(lane)));
+      }
+      if (tid == 0) T3_TRACE(i, 8);
+      if (!dead && !mbar_wait_cluster(bar(B_GT_FULL), static_cast<uint32_t>(i) & 1u)) dead = true;
       fence_async_cta();
       mbar_arrive(bar(B_G_READY));
       if (tid == 0) T3_TRACE(i, 9);
@@ -902,8 +902,8 @@ cudaError_t tc3_pass(const State& s, const TcWork& w, const TcPending& pend, cud
     cudaMemcpy(h, dtrace, sizeof(h), cudaMemcpyDeviceToHost);
     const unsigned long long t0 = h[0];
     static const char* names[15] = {"prodP1", "prodP2", "cvP1end", "cvP2end", "mma1", "mma2", "rgD1",
-                                    "rgXchRdy", "rgPubRdy", "rgG", "rgXchSent", "rgPubSent", "rgReduced",
-                                    "rgPublished", "rgGramDone"};
+                                    "rgXchRdy", "rgPushed", "rgG", "rgXchSent", "rgPeerFree", "rgReduced",
+                                    "rgPacked", "rgSums"};
     for (int t = 0; t < 8; ++t) {
       fprintf(stderr, "tc3 tile %d:", t);
       for (int p = 0; p < 15; ++p)

@@ -307,6 +307,13 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint32_t a, uint32_t parity) {
   }
   return false;
 }
+// store to a peer's shared memory (a shared::cluster address from mapa)
+__device__ __forceinline__ void st_dsmem_v4u(uint32_t a, uint4 v) {
+  asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+// generic-proxy writes of this thread before later async-proxy (tensor core, TMA) accesses
+__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
 __device__ __forceinline__ void fence_acq_rel_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
 __device__ __forceinline__ void named_bar(uint32_t id, uint32_t count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
