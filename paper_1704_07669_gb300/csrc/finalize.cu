@@ -65,22 +65,23 @@ __global__ void center_gram_kernel(const double* __restrict__ gram, const double
 // packed so that no lane idles over the upper half.
 __global__ void __launch_bounds__(256) bt_and_c_kernel(const double* __restrict__ Hbar, const double* __restrict__ T,
                                                        const int* __restrict__ info, int64_t n, int l, int L,
-                                                       int stage_t, double* __restrict__ Bt,
+                                                       int tcc, double* __restrict__ Bt,
                                                        double* __restrict__ Cpart) {
   extern __shared__ double sm[];
   double* sH = sm;                  // BT_ROWS x L
   double* sB = sm + BT_ROWS * L;    // BT_ROWS x L
-  double* sT = sB + BT_ROWS * L;    // L x L when staged: sT[c * L + i] = T[i][c]
+  double* sT = sB + BT_ROWS * L;    // tcc x L: sT[cc * L + i] = T[i][c0 + cc], tcc columns of T at a time
   constexpr int G = 256 / 64;       // row groups; thread = (row group, column i mod 64)
   constexpr int RPT = BT_ROWS / G;  // rows per thread
   const int r = info[0];
   const int tri = r * (r + 1) / 2;
+  const bool whole = tcc >= l;      // all of T^T staged once
   double* out = Cpart + static_cast<int64_t>(blockIdx.x) * L * L;
   for (int e = threadIdx.x; e < L * L; e += blockDim.x) out[e] = 0.0;
-  if (stage_t) {
-    for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
-      const int i = e / L, c = e - i * L;
-      sT[c * L + i] = T[e];
+  if (whole) {
+    for (int e = threadIdx.x; e < L * l; e += blockDim.x) {
+      const int i = e / l, cc = e - i * l;
+      sT[cc * L + i] = T[i * L + cc];
     }
   }
   const int grp = threadIdx.x >> 6, il = threadIdx.x & 63;
@@ -91,28 +92,38 @@ __global__ void __launch_bounds__(256) bt_and_c_kernel(const double* __restrict_
     for (int e = threadIdx.x; e < BT_ROWS * L; e += blockDim.x) {
       const int64_t j = j0 + e / L;
       sH[e] = (j < n) ? Hbar[j * L + e % L] : 0.0;
+      sB[e] = 0.0;
     }
-    __syncthreads();
-    for (int i = il; i < L; i += 64) {
-      double acc[RPT];
+    for (int c0 = 0; c0 < l; c0 += tcc) {
+      if (!whole) {
+        __syncthreads();
+        const int cn = l - c0 < tcc ? l - c0 : tcc;
+        for (int e = threadIdx.x; e < L * cn; e += blockDim.x) {
+          const int i = e / cn, cc = e - i * cn;
+          sT[cc * L + i] = T[i * L + c0 + cc];
+        }
+      }
+      __syncthreads();
+      const int c1 = l - c0 < tcc ? l : c0 + tcc;
+      for (int i = il; i < L; i += 64) {
+        if (i >= r) continue;
+        double acc[RPT];
 #pragma unroll
-      for (int u = 0; u < RPT; ++u) acc[u] = 0.0;
-      if (i < r) {
-        for (int c = 0; c < l; ++c) {
-          const double t = stage_t ? sT[c * L + i] : __ldg(T + static_cast<int64_t>(i) * L + c);
+        for (int u = 0; u < RPT; ++u) acc[u] = 0.0;
+        for (int c = c0; c < c1; ++c) {
+          const double t = sT[(c - c0) * L + i];
 #pragma unroll
           for (int u = 0; u < RPT; ++u) acc[u] = fma(t, sH[(grp + G * u) * L + c], acc[u]);
         }
-      }
 #pragma unroll
-      for (int u = 0; u < RPT; ++u) {
-        const int jr = grp + G * u;
-        sB[jr * L + i] = acc[u];
-        const int64_t j = j0 + jr;
-        if (j < n) Bt[j * L + i] = acc[u];
+        for (int u = 0; u < RPT; ++u) sB[(grp + G * u) * L + i] += acc[u];
       }
     }
     __syncthreads();
+    for (int e = threadIdx.x; e < BT_ROWS * L; e += blockDim.x) {
+      const int64_t j = j0 + e / L;
+      if (j < n) Bt[j * L + e % L] = sB[e];
+    }
     // this block's own partial over the packed lower triangle, a fixed order per entry
     for (int t = threadIdx.x; t < tri; t += blockDim.x) {
       int a = static_cast<int>((sqrtf(8.f * static_cast<float>(t) + 1.f) - 1.f) * 0.5f);
@@ -373,7 +384,10 @@ __device__ __forceinline__ void fetch_pair(const int (&pr)[kPairRegs], const flo
 // pair's a_pq is set to zero. Sweeps stop once the off-diagonal part is at most `conv` of
 // the whole (squared Frobenius norms), after a sweep without rotations, or after
 // max_sweeps. The entries should be scaled to about 1. Returns the buffer (A or A2) that
-// holds the final, nearly diagonal matrix; *sweeps_out gets the sweeps made.
+// holds the final, nearly diagonal matrix; *sweeps_out gets the sweeps made. With A2 NULL
+// (when only two d x d matrices fit in shared memory) the blocks are rotated in place, which
+// costs a second barrier per round: every warp must have read the round's pivots before any
+// block is overwritten.
 __device__ float* jacobi32(float* A, float* A2, float* W, int d, int ld, float* red, float conv, float eps_rel,
                            int max_sweeps, int* sweeps_out) {
   const int de = d + (d & 1), npairs = de >> 1, m = de - 1;
@@ -385,7 +399,7 @@ __device__ float* jacobi32(float* A, float* A2, float* W, int d, int ld, float* 
   for (int e = threadIdx.x; e < d * d; e += blockDim.x) W[(e / d) * ld + e % d] = ((e / d) == (e % d)) ? 1.f : 0.f;
   __syncthreads();
   float* cur = A;
-  float* nxt = A2;
+  float* nxt = A2 ? A2 : A;
   int sweep = 0;
   for (; sweep < max_sweeps && d > 1; ++sweep) {
     float off = 0.f, tot = 0.f;
@@ -422,6 +436,7 @@ __device__ float* jacobi32(float* A, float* A2, float* W, int d, int ld, float* 
         cr[t] = c;
         sr[t] = s;
       }
+      if (A2 == nullptr) __syncthreads();   // in place: the pivots are read before blocks change
       // warp-rows: the folded A blocks (fcols items each, in chunks of 32), then W's rows
       const int achunks = (fcols + 31) >> 5;
       const int arows = frows * achunks;
@@ -992,9 +1007,10 @@ __global__ void __launch_bounds__(EIG_T) eig_f32_kernel(const double* __restrict
   __shared__ double scale;
   const int r = info[0];
   const int ld = smem ? (r | 1) : L;   // odd: a column's entries fall in different banks
+  // smem: 1 = A, A2 and W in shared memory; 2 = A and W only (rotated in place); 0 = global
   float* X = smem ? e32 : Xg;
-  float* X2 = smem ? e32 + r * ld : Zg;
-  float* Y = smem ? e32 + 2 * r * ld : Yg;
+  float* X2 = smem == 1 ? e32 + r * ld : (smem == 2 ? nullptr : Zg);
+  float* Y = smem == 1 ? e32 + 2 * r * ld : (smem == 2 ? e32 + r * ld : Yg);
   if (threadIdx.x < 32) {   // C scaled by a power of two so that its largest diagonal entry is in [1, 2)
     double dm = 0.0;
     for (int i = threadIdx.x; i < r; i += 32) dm = fmax(dm, fabs(C[i * L + i]));
@@ -1216,8 +1232,12 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
   float* s32 = reinterpret_cast<float*>(f.Cpart);   // FP32 scratch when l x l does not fit in shared memory
   const size_t dense32 = 2 * sizeof(float) * s.l * s.l;   // Cholesky: X, Y
   const int smem32 = dense32 <= kMaxDenseSmem ? 1 : 0;
-  const size_t dense32e = 3 * sizeof(float) * s.l * (s.l | 1);  // FP32 Jacobi: A, A2, W
-  const int smem32e = dense32e <= kMaxDenseSmem ? 1 : 0;
+  size_t dense32e = 3 * sizeof(float) * s.l * (s.l | 1);  // FP32 Jacobi: A, A2, W
+  int smem32e = 1;
+  if (dense32e > kMaxDenseSmem) {   // A and W only, rotated in place
+    dense32e = 2 * sizeof(float) * s.l * (s.l | 1);
+    smem32e = dense32e <= kMaxDenseSmem ? 2 : 0;
+  }
   const int l = s.l, L = s.L;
   const int rank_ok = r_max >= l ? 1 : 0;
   const size_t gemm_full = sizeof(double) * (kMaxL + static_cast<size_t>(l) * l);
@@ -1247,11 +1267,11 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
   const int smem64 = dense64 <= kMaxDenseSmem ? 1 : 0;
   const int64_t nblk = (s.n + BT_ROWS - 1) / BT_ROWS;
   const int parts = static_cast<int>(nblk < f.nparts ? nblk : f.nparts);
+  // T^T staged in shared memory whole when it fits, else 32 of its columns at a time
   const size_t bt_base = 2 * sizeof(double) * BT_ROWS * s.L;
-  const size_t bt_full = bt_base + sizeof(double) * LL;
-  const int stage_t = bt_full <= kMaxDenseSmem ? 1 : 0;
-  bt_and_c_kernel<<<parts, 256, stage_t ? bt_full : bt_base, st>>>(f.Hbar, f.T, f.info, s.n, s.l, s.L, stage_t, f.Bt,
-                                                                   f.Cpart);
+  const int tcc = bt_base + sizeof(double) * s.L * s.l <= kMaxDenseSmem ? s.l : 32;
+  bt_and_c_kernel<<<parts, 256, bt_base + sizeof(double) * s.L * tcc, st>>>(f.Hbar, f.T, f.info, s.n, s.l, s.L, tcc,
+                                                                            f.Bt, f.Cpart);
   c_reduce_kernel<<<(s.L * s.L + 31) / 32, CR_T, 0, st>>>(f.Cpart, parts, s.L, f.C);
   // eigenvectors of C: FP32 Jacobi, FP64 orthogonalisation and polish (scratch: Cpart, whose
   // partials are consumed by now, and T, X, W)

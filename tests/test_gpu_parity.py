@@ -159,6 +159,7 @@ EDGE = [
     (700, 1001, 6, 5, 700, 0, True, 0.3, "n not a multiple of 4"),
     (513, 129, 1, 0, 100, 128, True, 0.3, "l = 1, ragged tiles"),
     (400, 300, 200, 56, 400, 0, True, 0.3, "l = 256 (largest)"),
+    (600, 500, 130, 10, 600, 0, True, 0.3, "l = 140: Jacobi rotated in place, T^T staged in chunks"),
     (2500, 333, 12, 8, 2500, 0, False, 0.0, "raw rows, odd n"),
 ]
 
