@@ -281,6 +281,112 @@ g_partial_kernel(const T* __restrict__ A, int64_t m, int64_t n, int64_t ld, cons
   }
 }
 
+// ---- FP32 rows, 16-byte aligned, n a multiple of 4: operands staged by cp.async rings
+// (several chunks in flight per CTA, no registers held across the loads), then the shift
+// subtracted in shared memory. Same tiles, same per-thread 8 x 4 products and the same
+// arithmetic per element as the kernels above.
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, bool valid) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr int GC_STAGES = 3;
+constexpr int GC_RAW_LD = BK + 4;   // raw A rows padded: the transposing reads below are conflict-free
+constexpr size_t kSmemGcp = sizeof(float) * (GC_STAGES * BM * GC_RAW_LD + GC_STAGES * BK * BN + BK * (BM + APAD));
+
+__global__ void __launch_bounds__(NT, 2)
+g_partial_cp_kernel(const float* __restrict__ A, int64_t m, int64_t n, int64_t ld, const float* __restrict__ shift,
+                    const float* __restrict__ omega, int L, int64_t kslice, float* __restrict__ Gpart,
+                    int64_t mstride) {
+  extern __shared__ __align__(16) float smem_gc[];
+  float (*raw)[BM][GC_RAW_LD] = reinterpret_cast<float (*)[BM][GC_RAW_LD]>(smem_gc);
+  float (*Bs)[BK][BN] = reinterpret_cast<float (*)[BK][BN]>(smem_gc + GC_STAGES * BM * GC_RAW_LD);
+  float (*As)[BM + APAD] = reinterpret_cast<float (*)[BM + APAD]>(smem_gc + GC_STAGES * BM * GC_RAW_LD +
+                                                                   GC_STAGES * BK * BN);
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t row0 = static_cast<int64_t>(blockIdx.x) * BM;
+  const int s = blockIdx.y;
+  const int c0 = blockIdx.z * BN;
+  const int64_t kb = static_cast<int64_t>(s) * kslice;
+  const int64_t ke = kb + kslice < n ? kb + kslice : n;
+  const int nchunks = ke > kb ? static_cast<int>((ke - kb + BK - 1) / BK) : 0;
+
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+
+  auto issue = [&](int ch) {   // chunk ch of this K slice into stage ch % GC_STAGES
+    const int stg = ch % GC_STAGES;
+    const int64_t k0 = kb + static_cast<int64_t>(ch) * BK;
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {   // A: 128 rows x 8 float4
+      const int idx = tid + it * NT;
+      const int r = idx >> 3, q = idx & 7;
+      const int64_t gr = row0 + r, gk = k0 + q * 4;
+      const bool ok = gr < m && gk < ke;
+      cp_async16(&raw[stg][r][q * 4], ok ? A + gr * ld + gk : A, ok);
+    }
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {   // Omega: 32 rows x 16 float4
+      const int idx = tid + it * NT;
+      const int kr = idx >> 4, q = idx & 15;
+      const int64_t gk = k0 + kr;
+      const int c = c0 + q * 4;
+      const bool ok = gk < ke && c < L;
+      cp_async16(&Bs[stg][kr][q * 4], ok ? omega + gk * L + c : omega, ok);
+    }
+  };
+  if (nchunks > 0) {
+#pragma unroll
+    for (int p = 0; p < GC_STAGES - 1; ++p) {
+      if (p < nchunks) issue(p);
+      cp_async_commit();
+    }
+    const int rr = tid & (BM - 1), kq = tid / BM;   // conversion: row rr, features [16 kq, 16 kq + 16)
+    const bool row_ok = row0 + rr < m;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      cp_async_wait<GC_STAGES - 2>();
+      __syncthreads();   // chunk ch has landed everywhere; every thread is past the products of ch - 1
+      const int stg = ch % GC_STAGES;
+      const int64_t k0 = kb + static_cast<int64_t>(ch) * BK;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {   // As[k][r] = raw[r][k] - c_k
+        const int k = 16 * kq + 4 * q;
+        const float4 v = *reinterpret_cast<const float4*>(&raw[stg][rr][k]);
+        const int64_t gk = k0 + k;
+        const bool ok = row_ok && gk < ke;
+        const float4 cc = gk < ke ? __ldg(reinterpret_cast<const float4*>(shift + gk)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        As[k + 0][rr] = ok ? v.x - cc.x : 0.f;
+        As[k + 1][rr] = ok ? v.y - cc.y : 0.f;
+        As[k + 2][rr] = ok ? v.z - cc.z : 0.f;
+        As[k + 3][rr] = ok ? v.w - cc.w : 0.f;
+      }
+      if (ch + GC_STAGES - 1 < nchunks) issue(ch + GC_STAGES - 1);
+      cp_async_commit();
+      __syncthreads();   // As holds chunk ch
+      mma_chunk<BM + APAD>(As, Bs[stg], ty * 8, tx * 4, acc);
+    }
+  }
+  const int c = c0 + tx * 4;
+  if (c < L) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int64_t r = row0 + ty * 8 + i;
+      if (r < m) {
+        *reinterpret_cast<float4*>(Gpart + (static_cast<int64_t>(s) * mstride + r) * L + c) =
+            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      }
+    }
+  }
+}
+
 // G = sum over splits (fixed order); per group of 32 rows: Gram and column-sum partials.
 __global__ void g_finish_kernel(const float* __restrict__ Gpart, int S, int64_t mstride, int64_t m, int L, int l,
                                 float* __restrict__ G, float* __restrict__ G_out, double* __restrict__ gram_part,
@@ -451,6 +557,101 @@ h_partial_kernel(const T* __restrict__ A, int64_t m, int64_t n, int64_t ld, cons
   }
 }
 
+constexpr int HC_STAGES = 4;
+constexpr size_t kSmemHcp = sizeof(float) * (HC_STAGES * BK * BM + HC_STAGES * BK * BN + 2 * BM);
+
+__global__ void __launch_bounds__(NT, 2)
+h_partial_cp_kernel(const float* __restrict__ A, int64_t m, int64_t n, int64_t ld, const float* __restrict__ shift,
+                    const float* __restrict__ G, int L, int64_t rslice, float* __restrict__ Hpart,
+                    float* __restrict__ cs_part) {
+  extern __shared__ __align__(16) float smem_hc[];
+  float (*As)[BK][BM] = reinterpret_cast<float (*)[BK][BM]>(smem_hc);
+  float (*Gs)[BK][BN] = reinterpret_cast<float (*)[BK][BN]>(smem_hc + HC_STAGES * BK * BM);
+  float (*red)[BM] = reinterpret_cast<float (*)[BM]>(smem_hc + HC_STAGES * BK * BM + HC_STAGES * BK * BN);
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t f0 = static_cast<int64_t>(blockIdx.x) * BM;
+  const int t = blockIdx.y;
+  const int c0 = blockIdx.z * BN;
+  const int64_t rb_ = static_cast<int64_t>(t) * rslice;
+  const int64_t re = rb_ + rslice < m ? rb_ + rslice : m;
+  const int nchunks = re > rb_ ? static_cast<int>((re - rb_ + BK - 1) / BK) : 0;
+  const bool do_cs = (blockIdx.z == 0);
+
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+
+  auto issue = [&](int ch) {   // chunk ch of this row slice into stage ch % HC_STAGES
+    const int stg = ch % HC_STAGES;
+    const int64_t r0c = rb_ + static_cast<int64_t>(ch) * BK;
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {   // A: 32 rows x 32 float4 (128 features)
+      const int idx = tid + it * NT;
+      const int r = idx >> 5, q = idx & 31;
+      const int64_t gr = r0c + r, gf = f0 + q * 4;
+      const bool ok = gr < re && gf < n;
+      cp_async16(&As[stg][r][q * 4], ok ? A + gr * ld + gf : A, ok);
+    }
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {   // G: 32 rows x 16 float4
+      const int idx = tid + it * NT;
+      const int r = idx >> 4, q = idx & 15;
+      const int64_t gr = r0c + r;
+      const int c = c0 + q * 4;
+      const bool ok = gr < re && c < L;
+      cp_async16(&Gs[stg][r][q * 4], ok ? G + gr * L + c : G, ok);
+    }
+  };
+  const int ff = tid & (BM - 1), kh = tid / BM;   // conversion: feature ff, rows [16 kh, 16 kh + 16)
+  const int64_t gf = f0 + ff;
+  const float cf = gf < n ? __ldg(shift + gf) : 0.f;
+  float csum = 0.f;
+  if (nchunks > 0) {
+#pragma unroll
+    for (int p = 0; p < HC_STAGES - 1; ++p) {
+      if (p < nchunks) issue(p);
+      cp_async_commit();
+    }
+    for (int ch = 0; ch < nchunks; ++ch) {
+      cp_async_wait<HC_STAGES - 2>();
+      __syncthreads();   // chunk ch has landed everywhere; every thread is past the products of ch - 1
+      const int stg = ch % HC_STAGES;
+      const int64_t r0c = rb_ + static_cast<int64_t>(ch) * BK;
+#pragma unroll
+      for (int q = 0; q < BK / 2; ++q) {   // the shift, in place, and the column sums
+        const int r = 16 * kh + q;
+        const bool ok = r0c + r < re && gf < n;
+        const float v = ok ? As[stg][r][ff] - cf : 0.f;
+        As[stg][r][ff] = v;
+        csum += v;
+      }
+      if (ch + HC_STAGES - 1 < nchunks) issue(ch + HC_STAGES - 1);
+      cp_async_commit();
+      __syncthreads();
+      mma_chunk<BM>(As[stg], Gs[stg], ty * 8, tx * 4, acc);
+    }
+  }
+  const int c = c0 + tx * 4;
+  if (c < L) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int64_t j = f0 + ty * 8 + i;
+      if (j < n) {
+        *reinterpret_cast<float4*>(Hpart + (static_cast<int64_t>(t) * n + j) * L + c) =
+            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      }
+    }
+  }
+  if (do_cs) {
+    red[kh][ff] = csum;
+    __syncthreads();
+    if (tid < BM && f0 + tid < n) cs_part[static_cast<int64_t>(t) * n + f0 + tid] = red[0][tid] + red[1][tid];
+  }
+}
+
 __global__ void h_finish_kernel(const float* __restrict__ Hpart, const float* __restrict__ cs_part, int T, int64_t n,
                                 int L, double* __restrict__ H, double* __restrict__ colsum) {
   const int64_t total = n * L;
@@ -574,15 +775,30 @@ cudaError_t simt_pass_t(const State& s, const SimtWork& w, const T* rows, float 
   if (S < 1) S = 1;
   const int64_t kslice = ((kchunks + S - 1) / S) * BK;
   S = static_cast<int>((s.n + kslice - 1) / kslice);
+  // FP32 rows that allow 16-byte copies take the kernels with cp.async rings
+  bool use_cp = false;
+  if constexpr (std::is_same<T, float>::value) use_cp = vec_ok && (s.n % 4 == 0);
   static bool g_attr = false;
   if (!g_attr) {
     cudaError_t e = allow_smem(g_partial_kernel<T>, kSmemG);
     if (e != cudaSuccess) return e;
+    if constexpr (std::is_same<T, float>::value) {
+      e = allow_smem(g_partial_cp_kernel, kSmemGcp);
+      if (e != cudaSuccess) return e;
+      e = allow_smem(h_partial_cp_kernel, kSmemHcp);
+      if (e != cudaSuccess) return e;
+    }
     g_attr = true;
   }
   prof->begin(SPCA_K_G_PARTIAL, st);
-  g_partial_kernel<T><<<dim3(row_tiles, S, col_tiles), NT, kSmemG, st>>>(rows, m, s.n, ld, s.shift, scale, vec_ok,
-                                                                         s.omega32, L, kslice, w.Gpart, mstride);
+  if constexpr (std::is_same<T, float>::value) {
+    if (use_cp)
+      g_partial_cp_kernel<<<dim3(row_tiles, S, col_tiles), NT, kSmemGcp, st>>>(rows, m, s.n, ld, s.shift, s.omega32, L,
+                                                                              kslice, w.Gpart, mstride);
+  }
+  if (!use_cp)
+    g_partial_kernel<T><<<dim3(row_tiles, S, col_tiles), NT, kSmemG, st>>>(rows, m, s.n, ld, s.shift, scale, vec_ok,
+                                                                           s.omega32, L, kslice, w.Gpart, mstride);
   prof->end(SPCA_K_G_PARTIAL, st);
   const int groups = static_cast<int>((m + GROUP_ROWS - 1) / GROUP_ROWS);
   prof->begin(SPCA_K_G_FINISH, st);
@@ -609,8 +825,14 @@ cudaError_t simt_pass_t(const State& s, const SimtWork& w, const T* rows, float 
     h_attr = true;
   }
   prof->begin(SPCA_K_H_PARTIAL, st);
-  h_partial_kernel<T><<<dim3(f_tiles, T_, col_tiles), NT, kSmemH, st>>>(rows, m, s.n, ld, s.shift, scale, vec_ok,
-                                                                        w.G, L, rslice, w.Hpart, w.cs_part);
+  if constexpr (std::is_same<T, float>::value) {
+    if (use_cp)
+      h_partial_cp_kernel<<<dim3(f_tiles, T_, col_tiles), NT, kSmemHcp, st>>>(rows, m, s.n, ld, s.shift, w.G, L, rslice,
+                                                                              w.Hpart, w.cs_part);
+  }
+  if (!use_cp)
+    h_partial_kernel<T><<<dim3(f_tiles, T_, col_tiles), NT, kSmemH, st>>>(rows, m, s.n, ld, s.shift, scale, vec_ok,
+                                                                          w.G, L, rslice, w.Hpart, w.cs_part);
   prof->end(SPCA_K_H_PARTIAL, st);
   prof->begin(SPCA_K_H_FINISH, st);
   h_finish_kernel<<<grid_for(s.n * L, 256), 256, 0, st>>>(w.Hpart, w.cs_part, T_, s.n, L, s.H, s.colsum);
