@@ -654,17 +654,24 @@ h_partial_cp_kernel(const float* __restrict__ A, int64_t m, int64_t n, int64_t l
 
 __global__ void h_finish_kernel(const float* __restrict__ Hpart, const float* __restrict__ cs_part, int T, int64_t n,
                                 int L, double* __restrict__ H, double* __restrict__ colsum) {
+  // the T FP32 partials are summed as an FP32 pair (two-sum, ~48 bits: FP64 adds issue at a
+  // small fraction of the FP32 rate here), then added once into the FP64 state
+  auto sum_pair = [](const float* p, int64_t stride, int T_) {
+    float hi = 0.f, lo = 0.f;
+    for (int t = 0; t < T_; ++t) {
+      const float x = p[static_cast<int64_t>(t) * stride];
+      const float s = hi + x;
+      const float bb = s - hi;
+      lo += (hi - (s - bb)) + (x - bb);
+      hi = s;
+    }
+    return static_cast<double>(hi) + static_cast<double>(lo);
+  };
   const int64_t total = n * L;
   for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
        idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    double acc = 0.0;
-    for (int t = 0; t < T; ++t) acc += static_cast<double>(Hpart[static_cast<int64_t>(t) * total + idx]);
-    H[idx] += acc;
-    if (idx < n) {
-      double a2 = 0.0;
-      for (int t = 0; t < T; ++t) a2 += static_cast<double>(cs_part[static_cast<int64_t>(t) * n + idx]);
-      colsum[idx] += a2;
-    }
+    H[idx] += sum_pair(Hpart + idx, total, T);
+    if (idx < n) colsum[idx] += sum_pair(cs_part + idx, n, T);
   }
 }
 

@@ -565,8 +565,16 @@ __global__ void tc_finish_kernel(const float* __restrict__ Hpart, int ncl, int64
   const int64_t total = n * L;
   for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
        idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    double acc = 0.0;
-    for (int c = 0; c < ncl; ++c) acc += static_cast<double>(Hpart[static_cast<int64_t>(c) * npad * L + idx]);
+    // the cluster partials summed as an FP32 pair (two-sum): FP64 adds issue slowly here
+    float hi = 0.f, lo = 0.f;
+    for (int c = 0; c < ncl; ++c) {
+      const float x = Hpart[static_cast<int64_t>(c) * npad * L + idx];
+      const float s = hi + x;
+      const float bb = s - hi;
+      lo += (hi - (s - bb)) + (x - bb);
+      hi = s;
+    }
+    const double acc = static_cast<double>(hi) + static_cast<double>(lo);
     const int col = static_cast<int>(idx % L);
     if (col < l) H[idx] += acc;
     else if (col == l) colsum[idx / L] += acc;
