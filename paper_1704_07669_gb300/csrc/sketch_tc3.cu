@@ -78,6 +78,7 @@ struct Tc3Seg {
 
 struct Tc3Args {
   CUtensorMap maps[T3_MAX_SEGS];   // per row block: FP32 rows, box 64 features x 128 rows
+  CUtensorMap hmap;                // the H partials (L columns x all rows), box 32 columns x 128 rows, 128-byte swizzle
   Tc3Seg seg[T3_MAX_SEGS];
   int nseg;
   int64_t ntiles;
@@ -531,38 +532,81 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
     F2Acc sg_acc;
     bool drained = false;
     const int r0 = static_cast<int>(rank) * RPC;
-    auto drain_h = [&]() {
-      for (int ch = 0; ch < U * L; ch += 32) {   // 32 columns of a unit: four loads, one wait, adds
-        const int mt = ch / L, c0 = ch - mt * L;
+    // H (TMEM) -> the cluster's FP32 partial in global memory, as boxes of 128 features x 32
+    // columns staged in the exchange buffer (free once every peer has read this CTA's rows of
+    // the tile, so callers wait B_XCH_FREE first) in the 128-byte swizzled layout of the
+    // tensor map: the TMA engine stores the first drain and adds the later ones in L2. Two
+    // staging halves alternate; thread 0 issues the copies and waits for their reads.
+    // (L a multiple of 32; otherwise drain_red below)
+    auto drain_tma = [&]() {
+      uint8_t* stg = reinterpret_cast<uint8_t*>(sX);
+      const int row = q * 32 + lane;
+      const int64_t hrow0 = static_cast<int64_t>(cid) * CS * w + f0;
+      const int nbox = U * (L / 32);
+      for (int bx = 0; bx < nbox; ++bx) {
+        const int mt = bx / (L / 32), c0 = (bx % (L / 32)) * 32;
+        uint8_t* half = stg + (bx & 1) * (128 * 128);
+        if (bx >= 2) {
+          if (tid == 0) bulk_wait_read<1>();   // the copy of box bx - 2 has read this half
+          named_bar(1, RG_THREADS);
+        }
         uint32_t r[32];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          if (c0 + 8 * j < L)
-            tmem_ld8_issue(tH + static_cast<uint32_t>(mt * L + c0 + 8 * j) + (static_cast<uint32_t>(q * 32) << 16),
-                           r + 8 * j);
+          tmem_ld8_issue(tH + static_cast<uint32_t>(mt * L + c0 + 8 * j) + (static_cast<uint32_t>(q * 32) << 16),
+                         r + 8 * j);
+        tmem_wait_ld();
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {   // 16-byte chunk ch of this row, swizzled by row % 8
+          float v[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)   // H carries s^2, sums s
+            v[e] = __uint_as_float(r[4 * ch + e]) * (c0 + 4 * ch + e == l ? inv_s : inv_s * inv_s);
+          *reinterpret_cast<float4*>(half + row * 128 + ((ch ^ (row & 7)) << 4)) = make_float4(v[0], v[1], v[2], v[3]);
+        }
+        fence_async_cta();
+        named_bar(1, RG_THREADS);
+        if (tid == 0) {
+          const int32_t y = static_cast<int32_t>(hrow0 + mt * 128);
+          if (drained) tma_reduce_add_2d(&a.hmap, c0, y, su32(half));
+          else tma_store_2d(&a.hmap, c0, y, su32(half));
+          bulk_commit();
+        }
+      }
+      if (tid == 0) bulk_wait_read<0>();
+      named_bar(1, RG_THREADS);   // the exchange buffer is free again
+      drained = true;
+      tc_fence_before();
+    };
+    // the same with plain stores, then reductions issued by the threads themselves
+    auto drain_red = [&]() {
+      for (int ch = 0; ch < U * L; ch += 16) {   // 16 columns of a unit: two loads, one wait
+        const int mt = ch / L, c0 = ch - mt * L;
+        uint32_t r[16];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+          tmem_ld8_issue(tH + static_cast<uint32_t>(mt * L + c0 + 8 * j) + (static_cast<uint32_t>(q * 32) << 16),
+                         r + 8 * j);
         tmem_wait_ld();
         const int64_t feat = f0 + mt * 128 + q * 32 + lane;
-        float* row = a.Hpart + (static_cast<int64_t>(cid) * (CS * static_cast<int64_t>(w)) + feat) * L + c0;
+        float* hrow = a.Hpart + (static_cast<int64_t>(cid) * (CS * static_cast<int64_t>(w)) + feat) * L + c0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          if (c0 + 8 * j < L) {
-            float v[8];
+          float v[4];
 #pragma unroll
-            for (int e = 0; e < 8; ++e)   // H carries s^2, sums s
-              v[e] = __uint_as_float(r[8 * j + e]) * (c0 + 8 * j + e == l ? inv_s : inv_s * inv_s);
-            float4* dst = reinterpret_cast<float4*>(row + 8 * j);
-            if (drained) {   // added in L2; this thread is the only writer of these entries
-              red_add_v4(reinterpret_cast<float*>(dst), v[0], v[1], v[2], v[3]);
-              red_add_v4(reinterpret_cast<float*>(dst + 1), v[4], v[5], v[6], v[7]);
-            } else {
-              dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-              dst[1] = make_float4(v[4], v[5], v[6], v[7]);
-            }
-          }
+          for (int e = 0; e < 4; ++e)   // H carries s^2, sums s
+            v[e] = __uint_as_float(r[4 * j + e]) * (c0 + 4 * j + e == l ? inv_s : inv_s * inv_s);
+          float* dst = hrow + 4 * j;
+          if (drained) red_add_v4(dst, v[0], v[1], v[2], v[3]);
+          else *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
         }
       }
       drained = true;
       tc_fence_before();
+    };
+    auto drain_h = [&]() {
+      if (L % 32 == 0) drain_tma();
+      else drain_red();
     };
     for (int i = 0; i < nt; ++i) {
       const int64_t tile = cid + static_cast<int64_t>(i) * ncl;
@@ -655,7 +699,10 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
           mbar_arrive_cluster(mapa(bar(B_PEER_FREE), static_cast<uint32_t>(lane)));
         }
         tc_fence_after();
-        if (drain_tile(i - 1, nt, a.drain_every, cid)) drain_h();
+        if (drain_tile(i - 1, nt, a.drain_every, cid)) {
+          if (!dead && !mbar_wait_cluster(bar(B_XCH_FREE), static_cast<uint32_t>(i) & 1u)) dead = true;
+          drain_h();
+        }
       }
       // 4. pack the own rows of G' (FP16: hi and lo) ...
       uint4* pub = sPub + (i & 1) * (GS * L * G8);
@@ -719,8 +766,10 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
     // the last tile's MMA2, then its drain
     if (nt > 0) {
       if (!dead && !mbar_wait(bar(B_MMA2_DONE), static_cast<uint32_t>(nt - 1) & 1u)) dead = true;
+      if (!dead && !mbar_wait_cluster(bar(B_XCH_FREE), static_cast<uint32_t>(nt - 1) & 1u)) dead = true;
       tc_fence_after();
       drain_h();
+      if (tid == 0) bulk_wait_all();   // the last stores and adds are complete before the CTA leaves
     } else {
       for (int64_t e = tid; e < static_cast<int64_t>(w) * L; e += RG_THREADS)
         a.Hpart[(static_cast<int64_t>(cid) * CS * w + f0) * L + e] = 0.f;
@@ -850,6 +899,17 @@ cudaError_t tc3_pass(const State& s, const TcWork& w, const TcPending& pend, cud
     args.seg[i].gout = pend.gout[i];
     args.seg[i].tile0 = tiles;
     tiles += (pend.m[i] + T3_ROWS - 1) / T3_ROWS;
+  }
+  if (s.L % 32 == 0) {
+    // H partials: L FP32 columns x (clusters x CS x w) rows, boxes of 32 columns x 128 rows
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(s.L), static_cast<cuuint64_t>(cfg.nclusters) * cfg.CS * cfg.w};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(s.L) * 4};
+    cuuint32_t box[2] = {32, 128};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode_fn()(&args.hmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, w.Hpart, dims, strides, box, estr,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                   CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaSuccess;   // the caller takes the other kernel
   }
   args.nseg = pend.nseg;
   args.ntiles = tiles;
