@@ -106,7 +106,19 @@ struct Tc3Args {
       a.trace[(ti) * 16 + (slot)] = t_;                                                   \
     }                                                                                     \
   } while (0)
+// stage events of tile 3: a.trace[128 + 4 * stage + event]
+#define T3_STRACE(ti, stage, ev)                                                          \
+  do {                                                                                    \
+    if (rank == 0 && cid == 0 && (ti) == 3 && (stage) < 32 && a.trace) {                 \
+      unsigned long long t_;                                                              \
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                              \
+      a.trace[128 + (stage) * 8 + (ev)] = t_;                                             \
+    }                                                                                     \
+  } while (0)
 #else
+#define T3_STRACE(ti, stage, ev) \
+  do {                           \
+  } while (0)
 #define T3_TRACE(ti, slot) \
   do {                     \
   } while (0)
@@ -273,8 +285,10 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
           for (int u = 0; u < U; ++u) {
             for (int b = 0; b < 2; ++b) {
               const int s = static_cast<int>(pos % NSTAGE);
+              T3_STRACE(ti, 2 * u + b, 3);
               claim(s);
               mbar_expect_tx(bar(B_STAGE_FULL + s), STAGE_BYTES);
+              T3_STRACE(ti, 2 * u + b, 0);
               tma_load_2d_hint(su32(sStage) + s * STAGE_BYTES, tmap, static_cast<int32_t>(f0 + 64 * (2 * u + b)),
                                y0, bar(B_STAGE_FULL + s), drop);
               filled(s, 1);
@@ -361,7 +375,9 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
           for (int b = 0; b < 2; ++b) {
             const int s = static_cast<int>(pos % NSTAGE);
             const uint32_t f1 = s ? f1b++ : f1a++;
+            if (cw == 0 && lane == 0) T3_STRACE(ti, 2 * u + b, 1);
             if (!dead && !mbar_wait(bar(B_STAGE_FULL + s), f1 & 1u)) dead = true;
+            if (cw == 0 && lane == 0) T3_STRACE(ti, 2 * u + b, 2);
             const float* src = sStage + s * (STAGE_BYTES / 4);
             const int fb = 2 * u + b;
             // lane: features 4 (lane % 16) .. +3 of row 2 k + lane / 16; (x - c) s = fma(x, s, -c s)
@@ -381,6 +397,7 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
               *reinterpret_cast<uint2*>(slot + off) = make_uint2(pack2<FMT>(v0, v1), pack2<FMT>(v2, v3));
             }
             __syncwarp();
+            if (cw == 0 && lane == 0) T3_STRACE(ti, 2 * u + b, 4);
             if (lane == 0) mbar_arrive(bar(B_STAGE_EMPTY + s));
             ++pos;
           }
@@ -931,8 +948,8 @@ cudaError_t tc3_pass(const State& s, const TcWork& w, const TcPending& pend, cud
   args.trace = nullptr;
 #ifdef SPCA_TC_TRACE
   static unsigned long long* dtrace = nullptr;
-  if (!dtrace) cudaMalloc(&dtrace, sizeof(unsigned long long) * 8 * 16);
-  cudaMemsetAsync(dtrace, 0, sizeof(unsigned long long) * 8 * 16, st);
+  if (!dtrace) cudaMalloc(&dtrace, sizeof(unsigned long long) * (128 + 256));
+  cudaMemsetAsync(dtrace, 0, sizeof(unsigned long long) * (128 + 256), st);
   args.trace = dtrace;
 #endif
 
@@ -957,7 +974,7 @@ cudaError_t tc3_pass(const State& s, const TcWork& w, const TcPending& pend, cud
   *used = true;
 #ifdef SPCA_TC_TRACE
   {
-    unsigned long long h[8 * 16];
+    unsigned long long h[128 + 256];
     cudaStreamSynchronize(st);
     cudaMemcpy(h, dtrace, sizeof(h), cudaMemcpyDeviceToHost);
     const unsigned long long t0 = h[0];
@@ -970,6 +987,13 @@ cudaError_t tc3_pass(const State& s, const TcWork& w, const TcPending& pend, cud
         if (h[t * 16 + p]) fprintf(stderr, " %s=%.1f", names[p], (double)(h[t * 16 + p] - t0) / 1000.0);
       fprintf(stderr, " us\n");
     }
+    for (int sg = 0; sg < 10; ++sg)
+      fprintf(stderr, "tc3 tile 3 stage %d: claim %.2f issued %.2f cvwait %.2f cvfull %.2f cvdone %.2f us\n", sg,
+              h[128 + sg * 8 + 3] ? (double)(h[128 + sg * 8 + 3] - t0) / 1000.0 : -1.0,
+              h[128 + sg * 8 + 0] ? (double)(h[128 + sg * 8 + 0] - t0) / 1000.0 : -1.0,
+              h[128 + sg * 8 + 1] ? (double)(h[128 + sg * 8 + 1] - t0) / 1000.0 : -1.0,
+              h[128 + sg * 8 + 2] ? (double)(h[128 + sg * 8 + 2] - t0) / 1000.0 : -1.0,
+              h[128 + sg * 8 + 4] ? (double)(h[128 + sg * 8 + 4] - t0) / 1000.0 : -1.0);
   }
 #endif
   e = launch_tc_finish(s, w, static_cast<int>(ncl), cfg.CS * static_cast<int64_t>(cfg.w),
