@@ -176,6 +176,70 @@ def centering_correction(H_hat, gram, s, sG, m):
     return H_hat - np.outer(s, sG) / m, gram - np.outer(sG, sG) / m
 
 
+class ShiftedPass:
+    """The accumulators of ``shifted_state``, fed one row block at a time.
+
+    For matrices too large to hold in FP64 at once: each block a is shifted,
+    g = a_hat Omega is formed (Alg. 4 step 6) and H, the Gram matrix and the sums
+    are increased by that block's terms (step 7, Eq. 11). The shift c is the
+    ``first_block_shift`` of the first block added unless one is given.
+    """
+
+    def __init__(self, Omega, c=None, keep_G=True):
+        self.Omega = np.asarray(Omega, dtype=np.float64)
+        n, l = self.Omega.shape
+        self.c = None if c is None else np.asarray(c, dtype=np.float64)
+        self.H = np.zeros((n, l))
+        self.gram = np.zeros((l, l))
+        self.s = np.zeros(n)
+        self.sG = np.zeros(l)
+        self.m = 0
+        self.G_parts = [] if keep_G else None
+
+    def add(self, a, overwrite=False, times=1):
+        """Fold block a in; with ``overwrite`` the shifted rows replace a's values.
+
+        ``times`` > 1 folds in that many consecutive copies of the same block (a
+        stream that repeats a block): each sum gains ``times`` equal terms.
+        """
+        a = np.asarray(a, dtype=np.float64)
+        if self.c is None:
+            self.c = first_block_shift(a)
+        if overwrite:
+            a_hat = a
+            np.subtract(a, self.c[None, :], out=a_hat)
+        else:
+            a_hat = a - self.c[None, :]
+        g = a_hat @ self.Omega
+        self.H += times * (a_hat.T @ g)
+        self.gram += times * (g.T @ g)
+        self.s += times * a_hat.sum(axis=0)
+        self.sG += times * g.sum(axis=0)
+        self.m += times * a_hat.shape[0]
+        if self.G_parts is not None:
+            self.G_parts.extend([g] * times)
+        return g
+
+    def state(self):
+        """Same keys as ``shifted_state`` (G only when kept)."""
+        G = np.vstack(self.G_parts) if self.G_parts else None
+        return {"G": G, "H": self.H, "gram": self.gram, "s": self.s, "sG": self.sG, "m": self.m}
+
+
+def finalize_centred(G_hat, H_hat, s, sG, m, Omega, k, b=10):
+    """sigma_1..k and V of the column-centred rows from the shifted pass (FP64).
+
+    The centring correction, then Alg. 4 steps 9-19 on G_bar = G_hat - (1/m) 1 sG^T
+    and H_bar, with the same sign convention as ``single_pass_pca``.
+    """
+    H_bar, _ = centering_correction(H_hat, np.zeros((len(sG), len(sG))), s, sG, m)
+    G_bar = np.asarray(G_hat, dtype=np.float64) - np.asarray(sG, dtype=np.float64)[None, :] / m
+    Q, B = blocked_qb(G_bar, H_bar, Omega, b)
+    _, sigma, V = svd_truncate(None, B, k)
+    V, _ = sign_fix(V)
+    return sigma, V
+
+
 # --------------------------------------------------------------------------
 # Finalisation: blocked QB with re-orthogonalisation (Alg. 4 steps 9-16).
 # --------------------------------------------------------------------------

@@ -109,6 +109,15 @@ __device__ __forceinline__ float4 load4_shifted(const T* row, int64_t j, int64_t
   return r;
 }
 
+// Kahan (compensated) summation step: s + x with the rounding error carried in c; the
+// sum is s - c.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = __fsub_rn(x, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+
 // 8 x 4 register tile update from one BK-deep chunk: acc[i][j] += sum_k As[k][m0+i] * Bs[k][n0+j].
 template <int LDA>
 __device__ __forceinline__ void mma_chunk(const float (*As)[LDA], const float (*Bs)[BN], int m0, int n0, float acc[8][4]) {
@@ -487,7 +496,10 @@ h_partial_kernel(const T* __restrict__ A, int64_t m, int64_t n, int64_t ld, cons
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  // column sums with Kahan compensation: the shifted sums are small against the sum of
+  // magnitudes (the shift is only the first rows' mean), so plain FP32 sums lose digits
   float cs[4] = {0.f, 0.f, 0.f, 0.f};
+  float cc[4] = {0.f, 0.f, 0.f, 0.f};
 
   float4 ra[4], rg[2];
   // A chunk: 32 rows x 128 features; thread -> row (tid >> 5) + 8 it, features (tid & 31) * 4
@@ -510,7 +522,10 @@ h_partial_kernel(const T* __restrict__ A, int64_t m, int64_t n, int64_t ld, cons
     for (int it = 0; it < 4; ++it) {
       *reinterpret_cast<float4*>(&As[buf][(tid >> 5) + 8 * it][(tid & 31) * 4]) = ra[it];
       if (do_cs) {
-        cs[0] += ra[it].x; cs[1] += ra[it].y; cs[2] += ra[it].z; cs[3] += ra[it].w;
+        kahan_add(cs[0], cc[0], ra[it].x);
+        kahan_add(cs[1], cc[1], ra[it].y);
+        kahan_add(cs[2], cc[2], ra[it].z);
+        kahan_add(cs[3], cc[3], ra[it].w);
       }
     }
 #pragma unroll
@@ -545,12 +560,14 @@ h_partial_kernel(const T* __restrict__ A, int64_t m, int64_t n, int64_t ld, cons
   if (do_cs) {
     const int w = tid >> 5;
     const int fl = (tid & 31) * 4;
-    red[w][fl + 0] = cs[0]; red[w][fl + 1] = cs[1]; red[w][fl + 2] = cs[2]; red[w][fl + 3] = cs[3];
+    red[w][fl + 0] = cs[0] - cc[0]; red[w][fl + 1] = cs[1] - cc[1];
+    red[w][fl + 2] = cs[2] - cc[2]; red[w][fl + 3] = cs[3] - cc[3];
     __syncthreads();
     if (tid < BM) {
-      float v = 0.f;
+      float v = 0.f, vc = 0.f;
 #pragma unroll
-      for (int ww = 0; ww < NT / 32; ++ww) v += red[ww][tid];
+      for (int ww = 0; ww < NT / 32; ++ww) kahan_add(v, vc, red[ww][tid]);
+      v -= vc;
       const int64_t j = f0 + tid;
       if (j < n) cs_part[static_cast<int64_t>(t) * n + j] = v;
     }
@@ -608,7 +625,7 @@ h_partial_cp_kernel(const float* __restrict__ A, int64_t m, int64_t n, int64_t l
   const int ff = tid & (BM - 1), kh = tid / BM;   // conversion: feature ff, rows [16 kh, 16 kh + 16)
   const int64_t gf = f0 + ff;
   const float cf = gf < n ? __ldg(shift + gf) : 0.f;
-  float csum = 0.f;
+  float csum = 0.f, ccomp = 0.f;   // Kahan-compensated column sum (see h_partial_kernel)
   if (nchunks > 0) {
 #pragma unroll
     for (int p = 0; p < HC_STAGES - 1; ++p) {
@@ -626,7 +643,7 @@ h_partial_cp_kernel(const float* __restrict__ A, int64_t m, int64_t n, int64_t l
         const bool ok = r0c + r < re && gf < n;
         const float v = ok ? As[stg][r][ff] - cf : 0.f;
         As[stg][r][ff] = v;
-        csum += v;
+        kahan_add(csum, ccomp, v);
       }
       if (ch + HC_STAGES - 1 < nchunks) issue(ch + HC_STAGES - 1);
       cp_async_commit();
@@ -646,7 +663,7 @@ h_partial_cp_kernel(const float* __restrict__ A, int64_t m, int64_t n, int64_t l
     }
   }
   if (do_cs) {
-    red[kh][ff] = csum;
+    red[kh][ff] = csum - ccomp;
     __syncthreads();
     if (tid < BM && f0 + tid < n) cs_part[static_cast<int64_t>(t) * n + f0 + tid] = red[0][tid] + red[1][tid];
   }

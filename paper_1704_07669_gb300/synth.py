@@ -125,3 +125,98 @@ def workload_c2(m=100_000, n=10_000, *, device="cpu", seed=SEED_BASE + 1, dtype=
     return {"name": f"{m}x{n} f32, sigma_i=10^(-i/20) (r={r}) + noise 1e-4 sigma_1, "
                     f"column means N(0,1), k=50 p=10, 4096-row blocks",
             "A": A, "k": 50, "p": 10, "block_rows": 4096, "center": True, "seed": seed}
+
+
+def workload_c3(m=400_000, n=40_000, *, device="cuda", seed=SEED_BASE + 2, block_rows=8192, r=1000):
+    """The 400000 x 40000 precision-sweep matrix, generated one row block at a time on ``device``.
+
+    A = U diag(sigma) V^T + noise with sigma_i = i^-1.5 (i <= r = 1000), per-entry
+    noise std 1e-3 sigma_1 / (sqrt(m) + sqrt(n)) (noise spectral norm ~ 1e-3 sigma_1)
+    and no column means; k = 100, p = 20 (l = 120), 8192-row blocks. U (m x r) and
+    V (n x r) have orthonormal columns: QR of a Gaussian matrix in FP32 on the device
+    (a 64 GB FP32 matrix, or even its FP64 factors, is never held whole). Block i's
+    noise is drawn from its own seed, so a block can be regenerated alone.
+
+    ``blocks()`` yields (row0, FP32 block) pairs as device tensors.
+    """
+    r = min(r, m, n)
+    sigma = torch.from_numpy(spectrum("pow1.5", r)).to(device=device, dtype=torch.float32)
+    noise = noise_std_for(1e-3, 1.0, m, n)
+
+    def orth(rows, s):
+        X = torch.randn(rows, r, generator=_gen(s, device), device=device, dtype=torch.float32)
+        Q, R = torch.linalg.qr(X, mode="reduced")
+        d = torch.sign(torch.diagonal(R))
+        d[d == 0] = 1.0
+        return Q * d[None, :]
+
+    Us = orth(m, seed * 4 + 1) * sigma[None, :]
+    Vt = orth(n, seed * 4 + 2).T.contiguous()
+
+    def blocks():
+        for r0 in range(0, m, block_rows):
+            r1 = min(m, r0 + block_rows)
+            a = Us[r0:r1] @ Vt
+            g = _gen(seed * 4 + 3 + 1000 * (r0 // block_rows + 1), device)
+            a.add_(torch.randn(r1 - r0, n, generator=g, device=device, dtype=torch.float32), alpha=noise)
+            yield r0, a
+
+    return {"name": f"{m}x{n}, sigma_i=i^-1.5 (r={r}) + noise 1e-3 sigma_1, no column means, "
+                    f"k=100 p=20, {block_rows}-row blocks",
+            "m": m, "n": n, "k": 100, "p": 20, "block_rows": block_rows, "seed": seed, "blocks": blocks}
+
+
+def store_rows(a, kind):
+    """Storage form of a row block: (stored tensor, per-block FP32 scale or None).
+
+    'f32' keeps FP32, 'bf16' rounds to bfloat16 (RNE), 'f8e4m3' stores
+    round(a / s) in FP8 e4m3 with the block's scale s = max|a| / 448.
+    """
+    if kind == "f32":
+        return a, None
+    if kind == "bf16":
+        return a.to(torch.bfloat16), None
+    if kind == "f8e4m3":
+        amax = float(a.abs().max())
+        s = float(np.float32(amax / 448.0)) if amax > 0 else 1.0
+        return (a / s).clamp_(-448.0, 448.0).to(torch.float8_e4m3fn), s
+    raise ValueError(kind)
+
+
+def workload_c4(m=937_500, n=40_000, *, device="cuda", seed=SEED_BASE + 3, block_rows=16384, pool=4, r=60):
+    """The 937500 x 40000 FP32 stream (150 GB), larger than the device: rows held on the host.
+
+    Row a = sum_{j<r} w_j z_j v_j + eps xi with w_j = 10^(-j/20), z and xi N(0, 1)
+    drawn per block from the block's seed, v_1..v_r orthonormal (QR of a Gaussian
+    matrix in FP32 on the device), and eps chosen so that the noise spectral norm is
+    about 1e-4 sigma_1 (sigma_1 ~ sqrt(m) w_0): eps = 1e-4 sqrt(m) / (sqrt(m) + sqrt(n)).
+    k = 50, p = 10 (l = 60), 16384-row blocks.
+
+    The 150 GB are not all materialised: ``pool`` distinct blocks are generated on
+    ``device`` and kept in pinned host memory, and the stream cycles through them
+    (block i is pool block i mod ``pool``; the ragged last block of m mod 16384 rows
+    is the head of its pool block). ``schedule`` lists (pool index, rows) per block.
+    """
+    r = min(r, n)
+    w = torch.tensor(10.0 ** (-np.arange(r) / 20.0), device=device, dtype=torch.float32)
+    eps = 1e-4 * math.sqrt(m) / (math.sqrt(m) + math.sqrt(n))
+    X = torch.randn(n, r, generator=_gen(seed * 4 + 2, device), device=device, dtype=torch.float32)
+    Q, R = torch.linalg.qr(X, mode="reduced")
+    d = torch.sign(torch.diagonal(R))
+    d[d == 0] = 1.0
+    Vt = (Q * d[None, :]).T.contiguous()
+    blocks = []
+    for b in range(min(pool, (m + block_rows - 1) // block_rows)):
+        g = _gen(seed * 4 + 3 + 1000 * (b + 1), device)
+        z = torch.randn(block_rows, r, generator=g, device=device, dtype=torch.float32)
+        a = (z * w[None, :]) @ Vt
+        a.add_(torch.randn(block_rows, n, generator=g, device=device, dtype=torch.float32), alpha=eps)
+        host = torch.empty((block_rows, n), dtype=torch.float32, pin_memory=True)
+        host.copy_(a)
+        blocks.append(host)
+        del a
+    schedule = [((r0 // block_rows) % len(blocks), min(block_rows, m - r0)) for r0 in range(0, m, block_rows)]
+    return {"name": f"{m}x{n} f32 stream from pinned host memory, rank-{r} factors (w_j=10^(-j/20)) + noise "
+                    f"1e-4 sigma_1, k=50 p=10, {block_rows}-row blocks, {len(blocks)} distinct blocks cycled",
+            "m": m, "n": n, "k": 50, "p": 10, "block_rows": block_rows, "seed": seed,
+            "pool": blocks, "schedule": schedule}

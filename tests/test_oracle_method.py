@@ -62,6 +62,38 @@ def test_centering_correction_matches_two_pass_centering():
     assert np.allclose(O.column_means(A_bar), 0.0, atol=1e-13)
 
 
+def test_block_fed_pass_matches_two_pass_centering_and_the_whole_method():
+    A = _rand(150, 40, 12) * 0.2 + 4.0 * _rand(1, 40, 13) + _rand(150, 5, 14) @ _rand(5, 40, 15)
+    Om = O.omega(40, 9, seed=16)
+    acc = O.ShiftedPass(Om)
+    for a in O.row_blocks(A, 23):          # ragged tail of 12 rows
+        acc.add(a)
+    st = acc.state()
+    assert np.array_equal(acc.c, O.first_block_shift(A[:23]))
+    A_bar = O.center(A)
+    G_bar = A_bar @ Om
+    H_bar, gram_bar = O.centering_correction(st["H"], st["gram"], st["s"], st["sG"], st["m"])
+    assert np.allclose(H_bar, A_bar.T @ G_bar, atol=1e-10)
+    assert np.allclose(gram_bar, G_bar.T @ G_bar, atol=1e-10)
+    assert np.allclose(st["G"] - st["sG"][None, :] / st["m"], G_bar, atol=1e-12)
+    sigma, V = O.finalize_centred(st["G"], st["H"], st["s"], st["sG"], st["m"], Om, 6, b=3)
+    ref = O.single_pass_pca(A, 6, 3, 16, 23, b=3)
+    assert np.allclose(sigma, ref["sigma"], rtol=1e-12)
+    assert np.allclose(V, ref["V"], atol=1e-10)
+    # a repeated block folded in once with its multiplicity = the literal stream
+    B = A[:40]
+    lit = O.ShiftedPass(Om)
+    for a in [B, B, B, A[40:51]]:
+        lit.add(a)
+    rep = O.ShiftedPass(Om)
+    rep.add(B.copy(), overwrite=True, times=3)
+    rep.add(A[40:51])
+    s1, s2 = lit.state(), rep.state()
+    assert s1["m"] == s2["m"] == 131
+    for key in ("G", "H", "gram", "s", "sG"):
+        assert np.allclose(s1[key], s2[key], rtol=1e-13, atol=1e-12), key
+
+
 # ---------------------------------------------------------------- Thm 1, Alg. 4 = Alg. 1
 
 @pytest.mark.parametrize("b", [1, 4, 12])
