@@ -120,6 +120,17 @@ def _ptr(x):
     return int(x), None
 
 
+def _wait_for_torch(*tensors):
+    """CUDA tensors handed to a library stream other than torch's may still be written by work
+    queued on torch's current stream (their producer, or a fill of an output buffer): the host
+    waits for that work before the library's stream reads or writes them."""
+    for t in tensors:
+        if t is not None and getattr(t, "is_cuda", False):
+            import torch
+            torch.cuda.current_stream(t.device).synchronize()
+            return
+
+
 def _dtype_code(x):
     name = str(getattr(x, "dtype", ""))
     if name.endswith("float32"):
@@ -264,8 +275,11 @@ class Session:
         self.l = self.k + self.p
         self.handle = spca_create(n, k, p, seed, math=math, center=int(center), max_block_rows=max_block_rows,
                                   stream=stream)
+        self.own_stream = stream is None   # the library's own stream: not ordered after torch's
 
     def update(self, rows, G_out=None, block_scale=None):
+        if self.own_stream:
+            _wait_for_torch(rows, G_out)
         spca_update(self.handle, rows, G_out=G_out, block_scale=block_scale)
 
     def finalize(self):
@@ -345,7 +359,9 @@ class Server:
         return sid.value
 
     def update(self, sid, rows):
-        """Queue a block of device-resident FP32 rows (a 2-D CUDA tensor); returns a ticket."""
+        """Queue a block of device-resident FP32 rows (a 2-D CUDA tensor); returns a ticket. The
+        worker reads them on its own streams, after the work queued on torch's current stream."""
+        _wait_for_torch(rows)
         t = ctypes.c_uint64(0)
         _check_srv(lib().spca_server_update(self.handle, int(sid), _ptr(rows)[0], int(rows.shape[0]),
                                             int(rows.stride(0)), ctypes.byref(t)))

@@ -35,6 +35,7 @@ constexpr int T3_ROWS = 128;
 constexpr int T3_NT = 384;
 constexpr int RG_THREADS = 128;     // warps 0-3
 constexpr int CV_WARP0 = 4, CV_WARPS = 6;
+constexpr int CV_ROWS = (T3_ROWS + 2 * CV_WARPS - 1) / (2 * CV_WARPS);   // stage rows per converter lane
 constexpr int PROD_WARP = 10, MMA3_WARP = 11;
 constexpr int NSTAGE = 2;
 constexpr uint32_t STAGE_BYTES = T3_ROWS * 64 * 4;   // FP32: 128 rows x 64 features
@@ -60,7 +61,11 @@ __host__ __device__ inline Tc3Layout tc3_layout(int L, int w, int CS, int gs) {
   t.stage = o; o += NSTAGE * STAGE_BYTES;
   t.pair = o; o += 2 * 2 * BLOCK16;                                     // two slots of two blocks
   t.om = o; o += 2u * static_cast<uint32_t>(L) * 128u;                  // Omega: two 64-feature chunks
-  t.xch = o; o += ((T3_ROWS * static_cast<uint32_t>(L + 4) * 4u) + 1023u) & ~1023u;
+  // the exchange rows of D1; the TMA drain of H (L a multiple of 32) stages its boxes in two
+  // 16 KB halves of the same space, so it is never smaller than that
+  uint32_t xch = ((T3_ROWS * static_cast<uint32_t>(L + 4) * 4u) + 1023u) & ~1023u;
+  if (L % 32 == 0 && xch < 2u * 128u * 128u) xch = 2u * 128u * 128u;
+  t.xch = o; o += xch;
   t.gt = o; o += 2u * GT_CHUNK;   // G^T: two chunks of 64 tile rows; rows [0,L) hi, [L,2L) lo, rest 0
   t.pub = o; o += 2u * static_cast<uint32_t>(L * gs) * (t.RPC / 8) * 16u;   // two tile parities
   t.shift = o; o += ((static_cast<uint32_t>(w) * 4u) + 15u) & ~15u;
@@ -147,16 +152,16 @@ enum {
   B_OM_EMPTY,
   B_D1_FULL,                           // [2]
   B_D1_EMPTY = B_D1_FULL + 2,          // [2]
-  B_G_READY = B_D1_EMPTY + 2,
-  B_MMA2_DONE,
-  B_XCH_READY,
+  B_G_READY = B_D1_EMPTY + 2,          // [2] a tile's G^T is in every CTA of the cluster (by tile parity)
+  B_MMA2_DONE = B_G_READY + 2,                         // [2] a tile's MMA2 has completed (by tile parity)
+  B_XCH_READY = B_MMA2_DONE + 2,
   B_XCH_FREE,
   B_PEER_FREE,                         // every peer's G^T buffer may be written (cluster scope)
   B_GT_FULL,                           // every peer has stored its rows of G^T here (cluster scope)
   B_FINAL,                             // the MMA issuer's last commit
   B_IMG_READY,                         // [2] a tile's operand image is in global memory (tile parity)
-  B_GT_FREE = B_IMG_READY + 2,         // the converters' Gram products are done with the G^T tile
-  B_COUNT
+  B_GT_FREE = B_IMG_READY + 2,         // [2] the converters' Gram products are done with a tile's G^T
+  B_COUNT = B_GT_FREE + 2
 };
 static_assert(B_COUNT <= 64, "barrier slots: 16 x 32 bytes in the layout");
 
@@ -169,6 +174,9 @@ __device__ __forceinline__ bool drain_tile(int i, int nt, int every, uint32_t ci
 template <int FMT>
 __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_constant__ Tc3Args a) {
   constexpr int GS = FMT == FMT_F16 ? 2 : 1;
+  // G^T buffers: without the lo terms (BF16) the rows [L, 2L) of the chunks hold a second
+  // tile's G^T, so a tile's G^T may be stored while the previous tile's MMA2 still reads its own
+  constexpr int GT_NB = GS == 1 ? 2 : 1;
   extern __shared__ __align__(1024) uint8_t smem3[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem3) + 1023) & ~uintptr_t(1023));
   const int L = a.L, w = a.w, CS = a.CS, l = a.l;
@@ -226,11 +234,12 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
       mbar_init(bar(B_PAIR_EMPTY + p), 2);   // MMA1 done, and the image copy has read the slot
       mbar_init(bar(B_D1_FULL + p), 1);
       mbar_init(bar(B_D1_EMPTY + p), RG_THREADS);
+      mbar_init(bar(B_MMA2_DONE + p), 1);
+      mbar_init(bar(B_G_READY + p), RG_THREADS);
+      mbar_init(bar(B_GT_FREE + p), CV_WARPS);
     }
     mbar_init(bar(B_OM_FULL), 1);
     mbar_init(bar(B_OM_EMPTY), 1);
-    mbar_init(bar(B_G_READY), RG_THREADS);
-    mbar_init(bar(B_MMA2_DONE), 1);
     mbar_init(bar(B_XCH_READY), static_cast<uint32_t>(CS));
     mbar_init(bar(B_XCH_FREE), static_cast<uint32_t>(CS));
     mbar_init(bar(B_FINAL), 1);
@@ -238,7 +247,6 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
     mbar_init(bar(B_GT_FULL), static_cast<uint32_t>(CS));
     mbar_init(bar(B_IMG_READY), 1);
     mbar_init(bar(B_IMG_READY + 1), 1);
-    mbar_init(bar(B_GT_FREE), CV_WARPS);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -385,13 +393,26 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
             const int fl = 4 * (lane & 15);
             const float4 sh = *reinterpret_cast<const float4*>(sShift + fb * 64 + fl);
             const float4 cs = make_float4(-sh.x * op_scale, -sh.y * op_scale, -sh.z * op_scale, -sh.w * op_scale);
-            for (int r = 2 * cw + (lane >> 4); r < T3_ROWS; r += 2 * CV_WARPS) {
-              const float4 x = *reinterpret_cast<const float4*>(src + r * 64 + fl);
+            // all of the warp's rows of the stage are loaded before any is converted (the loads
+            // overlap). The stage goes back to the producer only after the stores that consume
+            // every loaded value: an arrive issued while shared-memory loads are outstanding
+            // does not wait for them, and the next TMA fill could overwrite the stage first.
+            const int rl = 2 * cw + (lane >> 4);
+            float4 x[CV_ROWS];
+#pragma unroll
+            for (int j = 0; j < CV_ROWS; ++j) {
+              const int r = rl + 2 * CV_WARPS * j;
+              x[j] = r < T3_ROWS ? *reinterpret_cast<const float4*>(src + r * 64 + fl) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < CV_ROWS; ++j) {
+              const int r = rl + 2 * CV_WARPS * j;
+              if (r >= T3_ROWS) continue;
               const bool valid = row0 + r < mseg;
-              const float v0 = valid ? fmaf(x.x, op_scale, cs.x) : 0.f;
-              const float v1 = valid ? fmaf(x.y, op_scale, cs.y) : 0.f;
-              const float v2 = valid ? fmaf(x.z, op_scale, cs.z) : 0.f;
-              const float v3 = valid ? fmaf(x.w, op_scale, cs.w) : 0.f;
+              const float v0 = valid ? fmaf(x[j].x, op_scale, cs.x) : 0.f;
+              const float v1 = valid ? fmaf(x[j].y, op_scale, cs.y) : 0.f;
+              const float v2 = valid ? fmaf(x[j].z, op_scale, cs.z) : 0.f;
+              const float v3 = valid ? fmaf(x[j].w, op_scale, cs.w) : 0.f;
               const uint32_t off = static_cast<uint32_t>(b) * BLOCK16 + static_cast<uint32_t>(r >> 3) * 1024u +
                                    sw128(static_cast<uint32_t>(r & 7), static_cast<uint32_t>(fl) * 2u);
               *reinterpret_cast<uint2*>(slot + off) = make_uint2(pack2<FMT>(v0, v1), pack2<FMT>(v2, v3));
@@ -430,7 +451,8 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
       if (i >= 0) {
         pos += U;   // phase 2 of tile i passes through the ring without the converters
         // meanwhile: this thread's entries of G'^T G' over the tile's 128 rows
-        if (!dead && !mbar_wait(bar(B_G_READY), static_cast<uint32_t>(i) & 1u)) dead = true;
+        if (!dead && !mbar_wait(bar(B_G_READY + (i & 1)), static_cast<uint32_t>(i >> 1) & 1u)) dead = true;
+        const int hb = GT_NB == 2 ? (i & 1) : 0;   // the rows of tile i's G^T buffer
 #pragma unroll
         for (int k = 0; k < T3_GRAM_PER_THREAD; ++k) {
           if (gc1[k] < 0) continue;
@@ -438,8 +460,8 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
             float x1[GS][8], x2[GS][8];
 #pragma unroll
             for (int h = 0; h < GS; ++h) {
-              unpack8<FMT>(*reinterpret_cast<const uint4*>(sGt + gt_off(h, gc1[k], g)), x1[h]);
-              unpack8<FMT>(*reinterpret_cast<const uint4*>(sGt + gt_off(h, gc2[k], g)), x2[h]);
+              unpack8<FMT>(*reinterpret_cast<const uint4*>(sGt + gt_off(h + hb, gc1[k], g)), x1[h]);
+              unpack8<FMT>(*reinterpret_cast<const uint4*>(sGt + gt_off(h + hb, gc2[k], g)), x2[h]);
             }
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
@@ -453,7 +475,7 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
           }
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(bar(B_GT_FREE));
+        if (lane == 0) mbar_arrive(bar(B_GT_FREE + (i & 1)));
       }
     }
     {
@@ -511,7 +533,7 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
         }
         if (i >= 0) {   // MMA2 of tile i on its image units, as they land in the ring
           const int ti = i;
-          if (!dead && !mbar_wait(bar(B_G_READY), static_cast<uint32_t>(ti) & 1u)) dead = true;
+          if (!dead && !mbar_wait(bar(B_G_READY + (ti & 1)), static_cast<uint32_t>(ti >> 1) & 1u)) dead = true;
           const bool zero_h = ti == 0 || drain_tile(ti - 1, nt, a.drain_every, cid);
           tc_fence_after();
           for (int u = 0; u < U; ++u) {
@@ -521,7 +543,8 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
             tc_fence_after();
             if (!dead) {
               const uint64_t dA2 = sdesc(su32(sStage) + s * STAGE_BYTES, BLOCK16, 1024);   // MN-major: features x rows
-              const uint64_t dB2 = sdesc(su32(sGt), 16, 1024);                           // K-major: L x rows
+              const uint32_t gtb = GT_NB == 2 ? static_cast<uint32_t>(ti & 1) * static_cast<uint32_t>(L) * 128u : 0u;
+              const uint64_t dB2 = sdesc(su32(sGt) + gtb, 16, 1024);                      // K-major: L x rows
 #pragma unroll
               for (int ks = 0; ks < T3_ROWS / 16; ++ks)
 #pragma unroll
@@ -535,7 +558,7 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
             mma_commit(bar(B_SLOT_EMPTY + s));
             ++pos;
           }
-          mma_commit(bar(B_MMA2_DONE));
+          mma_commit(bar(B_MMA2_DONE + (ti & 1)));
           T3_TRACE(ti, 5);
         }
       }
@@ -590,8 +613,14 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
           bulk_commit();
         }
       }
-      if (tid == 0) bulk_wait_read<0>();
-      named_bar(1, RG_THREADS);   // the exchange buffer is free again
+      // the exchange buffer is free again once the copies have read it; after the stores of a
+      // launch's first drain, also wait until they are written: bulk copies are not ordered
+      // with one another, and a later drain's add-reductions to the same rows must not land first
+      if (tid == 0) {
+        if (drained) bulk_wait_read<0>();
+        else bulk_wait_all();
+      }
+      named_bar(1, RG_THREADS);
       drained = true;
       tc_fence_before();
     };
@@ -706,18 +735,26 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
         fence_acq_rel_cluster();
         mbar_arrive_cluster(mapa(bar(B_XCH_FREE), static_cast<uint32_t>(lane)));
       }
-      // 3. the previous tile's MMA2 and Gram products are done with this CTA's G^T buffer: say
-      //    so to every peer, then drain H if due
+      // 3. the MMA2 and Gram products of tile i - GT_NB are done with the G^T buffer tile i
+      //    takes in this CTA: say so to every peer; then drain H if due, after the previous
+      //    tile's MMA2
       if (i >= 1) {
-        if (!dead && !mbar_wait(bar(B_MMA2_DONE), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
-        if (!dead && !mbar_wait(bar(B_GT_FREE), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
+        if (i >= GT_NB) {
+          const int t = i - GT_NB;
+          const uint32_t ph = static_cast<uint32_t>(t >> 1) & 1u;
+          if (!dead && !mbar_wait(bar(B_MMA2_DONE + (t & 1)), ph)) dead = true;
+          if (!dead && !mbar_wait(bar(B_GT_FREE + (t & 1)), ph)) dead = true;
+        }
         if (warp == 0 && lane < CS) {
           fence_acq_rel_cluster();
           mbar_arrive_cluster(mapa(bar(B_PEER_FREE), static_cast<uint32_t>(lane)));
         }
-        tc_fence_after();
         if (drain_tile(i - 1, nt, a.drain_every, cid)) {
+          if (GT_NB == 2 && !dead &&
+              !mbar_wait(bar(B_MMA2_DONE + ((i - 1) & 1)), static_cast<uint32_t>((i - 1) >> 1) & 1u))
+            dead = true;
           if (!dead && !mbar_wait_cluster(bar(B_XCH_FREE), static_cast<uint32_t>(i) & 1u)) dead = true;
+          tc_fence_after();
           drain_h();
         }
       }
@@ -763,7 +800,8 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
           const int it = t % nitems, pp = t / nitems;
           const int h = it / (L * G8), rem = it - h * (L * G8), lc = rem / G8, gl = rem % G8;
           const int g = static_cast<int>(rank) * G8 + gl;
-          const uint32_t off = static_cast<uint32_t>(g >> 3) * GT_CHUNK + static_cast<uint32_t>((h * L + lc) >> 3) * 1024u +
+          const int hr = h + (GT_NB == 2 ? (i & 1) : 0);   // row block of tile i's G^T buffer
+          const uint32_t off = static_cast<uint32_t>(g >> 3) * GT_CHUNK + static_cast<uint32_t>((hr * L + lc) >> 3) * 1024u +
                                sw128(static_cast<uint32_t>(lc & 7), static_cast<uint32_t>(g & 7) * 16u);
           st_dsmem_v4u(mapa(su32(sGt + off), static_cast<uint32_t>(pp)), pub[it]);
         }
@@ -777,12 +815,12 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
       if (tid == 0) T3_TRACE(i, 8);
       if (!dead && !mbar_wait_cluster(bar(B_GT_FULL), static_cast<uint32_t>(i) & 1u)) dead = true;
       fence_async_cta();
-      mbar_arrive(bar(B_G_READY));
+      mbar_arrive(bar(B_G_READY + (i & 1)));
       if (tid == 0) T3_TRACE(i, 9);
     }
     // the last tile's MMA2, then its drain
     if (nt > 0) {
-      if (!dead && !mbar_wait(bar(B_MMA2_DONE), static_cast<uint32_t>(nt - 1) & 1u)) dead = true;
+      if (!dead && !mbar_wait(bar(B_MMA2_DONE + ((nt - 1) & 1)), static_cast<uint32_t>((nt - 1) >> 1) & 1u)) dead = true;
       if (!dead && !mbar_wait_cluster(bar(B_XCH_FREE), static_cast<uint32_t>(nt - 1) & 1u)) dead = true;
       tc_fence_after();
       drain_h();

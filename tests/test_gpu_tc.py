@@ -140,6 +140,41 @@ def test_tc_reset_is_a_fresh_pass(math):
 
 
 @pytest.mark.parametrize("math", TC_MATHS)
+def test_tc_repeated_sessions_at_padded_l_32(math):
+    """l + 1 = 17 pads to L = 32, where H drains through staged TMA copies: the staging must stay
+    inside its own buffer. Sessions created one after another (reusing freed device memory)
+    and a reset session must all give the Gram matrix and sigma of the FP32 path."""
+    n, k, p, seed = 300, 8, 8, 900
+    A = synth.low_rank_plus_noise(2917, n, synth.spectrum("dec20", 46), noise_std=1e-4, mean_std=0.5, seed=500,
+                                  device=DEV, dtype=torch.float32)
+    torch.cuda.synchronize()
+    cuts = [0, 587, 1223, 2037, 2585, 2917]
+
+    def run(math_, reps=1):
+        out = []
+        with spca.Session(n, k, p, seed, math=math_, max_block_rows=4096) as s:
+            for r in range(reps):
+                if r:
+                    s.reset(seed)
+                for a, b in zip(cuts[:-1], cuts[1:]):
+                    s.update(A[a:b])
+                sigma, _ = s.finalize()
+                out.append((sigma, s.state()["gram_bar"]))
+        return out
+
+    sig32, gram32 = run("fp32")[0]
+    results = [run(math)[0] for _ in range(3)] + run(math, reps=3)
+    sig0, gram0 = results[0]
+    tol_gram = 1e-3 if math == "fp16" else 4e-3   # BF16 rounds G' to 2^-9 relative
+    for sigma, gram in results:
+        # the same launches on the same rows: equal up to the order of FP32 partial sums
+        assert np.abs(gram - gram0).max() <= 1e-6 * np.abs(gram0).max()
+        assert np.abs(sigma - sig0).max() <= 1e-6 * sig0[0]
+        assert np.abs(gram - gram32).max() <= tol_gram * np.abs(gram32).max()
+        assert_sigma(sigma, sig32, math)
+
+
+@pytest.mark.parametrize("math", TC_MATHS)
 def test_tc_rejects_shapes_it_cannot_take(math):
     with pytest.raises(spca.SpcaError) as ei:
         spca.Session(40000, 100, 20, 1, math=math)
