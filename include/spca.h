@@ -145,6 +145,28 @@ spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t 
 spca_status spca_finalize(spca_session* s, double* sigma, double* V, int32_t out_on_device);
 
 /*
+ * spca_left_vectors - U, the leading k left singular vectors of the (centred)
+ * rows, from the sketch rows G that spca_update returned in G_out (Alg. 4
+ * steps 18-19: U = Q U~, with Q = G_bar R^-1 the orthonormal basis of the
+ * sketch in the Gram reading of Thm 1 and U~ the left singular vectors of B).
+ * Needs a spca_finalize after the last update, merge or reset; uses its R and
+ * U~, so that A_bar ~ U diag(sigma) V^T with the V that call returned.
+ *   G      device, m x l FP32, row-major with leading dimension l: the G_out
+ *          rows of the rows seen (any subset or order: row r of U belongs to
+ *          row r of G)
+ *   m      rows of G (0 is a no-op)
+ *   U      m x k doubles, COLUMN-major (column i at U + i*m); column i has the
+ *          sign that makes U diag(sigma) V^T the approximation; columns for
+ *          zero sigma are 0
+ *   out_on_device  1: U is a device pointer; 0: host memory
+ * With centering, G_bar = G - (1/m_seen) 1 sG^T uses the session's sums of G.
+ * Synchronises the session stream.
+ * Errors: SPCA_E_STATE (no finalize since the state last changed),
+ * SPCA_E_INVALID (NULL pointers, G not in device memory), SPCA_E_CUDA.
+ */
+spca_status spca_left_vectors(spca_session* s, const float* G, int64_t m, double* U, int32_t out_on_device);
+
+/*
  * spca_get_state - the centred accumulators, for inspection and parity tests.
  *   H_bar    n x l doubles, row-major: A_bar^T G_bar (NULL = skip)
  *   gram_bar l x l doubles: G_bar^T G_bar (NULL = skip)

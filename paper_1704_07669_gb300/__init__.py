@@ -70,6 +70,7 @@ def lib():
             "spca_create": (i32, [i64, i32, i32, u64, ctypes.POINTER(Options), ctypes.POINTER(vp)]),
             "spca_update": (i32, [vp, vp, i64, i64, i32, vp, i32, vp]),
             "spca_finalize": (i32, [vp, vp, vp, i32]),
+            "spca_left_vectors": (i32, [vp, vp, i64, vp, i32]),
             "spca_get_state": (i32, [vp, vp, vp, vp, vp, vp]),
             "spca_merge": (i32, [vp, vp]),
             "spca_sync": (i32, [vp]),
@@ -187,6 +188,16 @@ def spca_finalize(handle, sigma, V, out_on_device=None):
     _check(lib().spca_finalize(handle, sa, va, int(on)), handle)
 
 
+def spca_left_vectors(handle, G, U, m=None, out_on_device=None):
+    """Fill U (m x k doubles, column-major) from the kept sketch rows G (m x l FP32 CUDA tensor)."""
+    ga, _ = _ptr(G)
+    ua, udev = _ptr(U)
+    if m is None:
+        m = G.shape[0]
+    on = bool(udev) if out_on_device is None else bool(out_on_device)
+    _check(lib().spca_left_vectors(handle, ga, int(m), ua, int(on)), handle)
+
+
 def spca_get_state(handle, H_bar=None, gram_bar=None, colsum=None, shift=None):
     m = ctypes.c_int64(0)
     _check(lib().spca_get_state(handle, _ptr(H_bar)[0], _ptr(gram_bar)[0], _ptr(colsum)[0], _ptr(shift)[0],
@@ -288,6 +299,16 @@ class Session:
         Vc = np.zeros((self.k, self.n))      # column-major n x k == row-major k x n
         spca_finalize(self.handle, sigma, Vc, out_on_device=False)
         return sigma, Vc.T.copy()
+
+    def left_vectors(self, G):
+        """U (m x k float64 numpy) of the last finalize, from the kept sketch rows G (the G_out
+        rows, an m x l FP32 CUDA tensor)."""
+        if self.own_stream:
+            _wait_for_torch(G)
+        m = int(G.shape[0])
+        Uc = np.zeros((self.k, m))      # column-major m x k == row-major k x m
+        spca_left_vectors(self.handle, G, Uc, m=m, out_on_device=False)
+        return Uc.T.copy()
 
     def state(self):
         H = np.zeros((self.n, self.l))

@@ -229,8 +229,9 @@ __global__ void __launch_bounds__(256) form_v_kernel(const double* __restrict__ 
   }
 }
 
-// Per column i: the entry of largest |.| (lowest index on ties) is made positive.
-__global__ void __launch_bounds__(SIGN_T) sign_fix_kernel(double* __restrict__ V, int64_t n) {
+// Per column i: the entry of largest |.| (lowest index on ties) is made positive; the sign
+// applied goes to flip[i] (+1 or -1).
+__global__ void __launch_bounds__(SIGN_T) sign_fix_kernel(double* __restrict__ V, int64_t n, double* __restrict__ flip) {
   __shared__ double best_v[SIGN_T];
   __shared__ int64_t best_j[SIGN_T];
   double* col = V + static_cast<int64_t>(blockIdx.x) * n;
@@ -254,10 +255,56 @@ __global__ void __launch_bounds__(SIGN_T) sign_fix_kernel(double* __restrict__ V
     }
     __syncthreads();
   }
-  const bool flip = col[best_j[0]] < 0.0;
+  const bool neg = col[best_j[0]] < 0.0;
   __syncthreads();
-  if (flip) {
+  if (neg) {
     for (int64_t j = threadIdx.x; j < n; j += blockDim.x) col[j] = -col[j];
+  }
+  if (threadIdx.x == 0) flip[blockIdx.x] = neg ? -1.0 : 1.0;
+}
+
+// The map from sketch rows to left singular vectors (Alg. 4 steps 18-19 in the Gram reading
+// of Thm 1): Q = G_bar R^-1 = G_bar T^T and U = Q U~, U~ the eigenvectors Z of B B^T, so
+// U[:, i] = G_bar (T^T Z[:, i]) flip_i. M[c][i] = flip_i sum_{c' < r} T[c'][c] Z[c'][i] (l x k,
+// columns beyond the rank 0) and, for the centred rows G_bar = G_hat - (1/m) 1 sG^T,
+// mrow[i] = sum_c (sG[c] / m) M[c][i] (0 when centering is off: m = 0).
+__global__ void u_map_kernel(const double* __restrict__ T, const double* __restrict__ Z, const int* __restrict__ info,
+                             const double* __restrict__ flip, const double* __restrict__ sG, int64_t m, int l, int L,
+                             int k, double* __restrict__ M, double* __restrict__ mrow) {
+  const int r = info[0];
+  const int kk = k < r ? k : r;
+  for (int e = threadIdx.x; e < l * k; e += blockDim.x) {
+    const int c = e / k, i = e - c * k;
+    double acc = 0.0;
+    if (i < kk) {
+      for (int cp = 0; cp < r; ++cp) acc = fma(T[cp * L + c], Z[cp * L + i], acc);
+      acc *= flip[i];
+    }
+    M[e] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double acc = 0.0;
+    if (m > 0)
+      for (int c = 0; c < l; ++c) acc = fma(sG[c] / static_cast<double>(m), M[c * k + i], acc);
+    mrow[i] = acc;
+  }
+}
+
+// U rows [row0, row0 + mc) from the kept sketch rows: U[i * ldu + row] = G[row0 + row] M[:, i] - mrow[i]
+// (G row-major with leading dimension l, FP32; U column-major, FP64).
+__global__ void left_vectors_kernel(const float* __restrict__ G, int64_t row0, int64_t mc, int l, int k,
+                                    const double* __restrict__ M, const double* __restrict__ mrow,
+                                    double* __restrict__ U, int64_t ldu) {
+  const int64_t total = mc * k;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t row = idx % mc;
+    const int i = static_cast<int>(idx / mc);
+    const float* g = G + (row0 + row) * l;
+    double acc = 0.0;
+    for (int c = 0; c < l; ++c) acc = fma(static_cast<double>(g[c]), M[c * k + i], acc);
+    U[i * ldu + row] = acc - mrow[i];
   }
 }
 
@@ -1273,6 +1320,9 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
   bt_and_c_kernel<<<parts, 256, bt_base + sizeof(double) * s.L * tcc, st>>>(f.Hbar, f.T, f.info, s.n, s.l, s.L, tcc,
                                                                             f.Bt, f.Cpart);
   c_reduce_kernel<<<(s.L * s.L + 31) / 32, CR_T, 0, st>>>(f.Cpart, parts, s.L, f.C);
+  // T (= R^-T) is scratch below; the map to U keeps a copy
+  e = cudaMemcpyAsync(f.Tu, f.T, sizeof(double) * LL, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
   // eigenvectors of C: FP32 Jacobi, FP64 orthogonalisation and polish (scratch: Cpart, whose
   // partials are consumed by now, and T, X, W)
   float* s64 = reinterpret_cast<float*>(f.Cpart + 2 * LL);   // E, W of the polish: 2 L^2 floats
@@ -1301,11 +1351,22 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
     form_v_kernel<true><<<fv_grid, 256, fv_full, st>>>(f.Bt, f.X, f.sig, f.info, s.n, k, s.L, V_dev);
   else
     form_v_kernel<false><<<fv_grid, 256, fv_base, st>>>(f.Bt, f.X, f.sig, f.info, s.n, k, s.L, V_dev);
-  sign_fix_kernel<<<k, SIGN_T, 0, st>>>(V_dev, s.n);
-  prof->launches[SPCA_K_FINALIZE] += 24;  // launches above beyond the one begin() counted
+  sign_fix_kernel<<<k, SIGN_T, 0, st>>>(V_dev, s.n, f.flip);
+  u_map_kernel<<<1, 256, 0, st>>>(f.Tu, f.X, f.info, f.flip, s.sG, m, s.l, s.L, k, f.M, f.mrow);
+  prof->launches[SPCA_K_FINALIZE] += 25;  // launches above beyond the one begin() counted (not the copy)
   prof->end(SPCA_K_FINALIZE, st);
   e = cudaMemcpyAsync(sigma_dev, f.sig, sizeof(double) * k, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_left_vectors(const State& s, const FinalWork& f, int k, const float* G, int64_t row0, int64_t mc,
+                                double* U, int64_t ldu, cudaStream_t st) {
+  const int64_t total = mc * k;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  left_vectors_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(G, row0, mc, s.l, k, f.M, f.mrow, U, ldu);
   return cudaGetLastError();
 }
 

@@ -91,6 +91,7 @@ struct spca_session {
   int64_t m = 0;
   bool shift_set = false;
   bool scale_set = false;     // FP16 form: operand scale computed from the first rows
+  bool u_ready = false;       // a finalize has formed the map to U since the last change of the state
   char err[512] = "";
   char desc[256] = "";
 
@@ -168,7 +169,8 @@ void free_all(spca_session* s) {
   void* bufs[] = {s->omega32, s->H, s->shift, s->colsum, s->sG, s->gram, s->flags, s->simt.Gpart, s->simt.G,
                   s->simt.gram_part, s->simt.sG_part, s->simt.Hpart, s->simt.cs_part, s->shift_part, s->fin.Hbar,
                   s->fin.gbar, s->fin.T, s->fin.X, s->fin.W, s->fin.lam, s->fin.Bt, s->fin.Cpart, s->fin.C,
-                  s->fin.sig, s->fin.info, s->fin_sigma, s->fin_V, s->dstage[0], s->dstage[1],
+                  s->fin.sig, s->fin.info, s->fin.flip, s->fin.Tu, s->fin.M, s->fin.mrow, s->fin_sigma, s->fin_V,
+                  s->dstage[0], s->dstage[1],
                   s->tcw.om16, s->tcw.Hpart, s->tcw.gram_part, s->tcw.sG_part, s->tcw.scale, s->tcw.scale_bits,
                   s->tcw.img};
   for (void* b : bufs)
@@ -281,6 +283,7 @@ size_t session_footprint(int64_t n, int k, int p, int math, int64_t max_block_ro
   np = np < 4 ? 4 : (np > 304 ? 304 : np);
   add(n * L, 8); for (int i = 0; i < 4; ++i) add(int64_t(L) * L, 8);
   add(L, 8); add(n * L, 8); add(np * L * L, 8); add(int64_t(L) * L, 8); add(L, 8); add(8, 4); add(k, 8); add(n * k, 8);
+  add(L, 8); add(int64_t(L) * L, 8); add(int64_t(L) * L, 8); add(L, 8);
   return b;
 }
 
@@ -451,6 +454,10 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   CC(dalloc(&f.C, size_t(L) * L));
   CC(dalloc(&f.sig, L));
   CC(dalloc(&f.info, 8));
+  CC(dalloc(&f.flip, L));
+  CC(dalloc(&f.Tu, size_t(L) * L));
+  CC(dalloc(&f.M, size_t(L) * L));
+  CC(dalloc(&f.mrow, L));
   CC(dalloc(&s->fin_sigma, k));
   CC(dalloc(&s->fin_V, size_t(n) * k));
 
@@ -479,6 +486,7 @@ spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t 
   if (m_i < 0) return fail(s, SPCA_E_INVALID, "m_i < 0");
   if (m_i == 0) return SPCA_OK;
   if (!rows) return fail(s, SPCA_E_INVALID, "rows is NULL");
+  s->u_ready = false;
   if (ld < s->n) return fail(s, SPCA_E_INVALID, "ld (%lld) < n (%lld)", (long long)ld, (long long)s->n);
   const size_t es = dtype_size(dtype);
   if (es == 0) return fail(s, SPCA_E_INVALID, "unknown dtype %d", dtype);
@@ -588,6 +596,41 @@ spca_status spca_finalize(spca_session* s, double* sigma, double* V, int32_t out
   if (s->host_flags[0] & 8) return fail(s, SPCA_E_CUDA, "a copy of the tensor-core pass was out of its buffer (skipped)");
   if (s->host_flags[0] & 2) return fail(s, SPCA_E_TIMEOUT, "a bounded device wait gave up during the pass");
   if (s->host_flags[0] & 1) return fail(s, SPCA_E_NUMERIC, "non-finite values (NaN/Inf) reached the sketch");
+  s->u_ready = true;
+  return SPCA_OK;
+}
+
+spca_status spca_left_vectors(spca_session* s, const float* G, int64_t m, double* U, int32_t out_on_device) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  if (!s->u_ready) return fail(s, SPCA_E_STATE, "spca_left_vectors needs a spca_finalize after the last update");
+  if (m < 0) return fail(s, SPCA_E_INVALID, "m < 0");
+  if (m == 0) return SPCA_OK;
+  if (!G || !U) return fail(s, SPCA_E_INVALID, "G and U must be non-NULL");
+  if (out_on_device != 0 && out_on_device != 1) return fail(s, SPCA_E_INVALID, "out_on_device must be 0 or 1");
+  CU(cudaSetDevice(s->device));
+  {
+    cudaPointerAttributes attr;
+    std::memset(&attr, 0, sizeof(attr));
+    const bool ok = cudaPointerGetAttributes(&attr, G) == cudaSuccess;
+    cudaGetLastError();
+    if (!ok || (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged))
+      return fail(s, SPCA_E_INVALID, "G must be device memory (the G_out rows of spca_update)");
+  }
+  if (out_on_device) {
+    CU(launch_left_vectors(s->state(), s->fin, s->k, G, 0, m, U, m, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    return SPCA_OK;
+  }
+  // host output: through the finalisation's n x k scratch, in pieces of rows
+  const int64_t piece = s->n;
+  for (int64_t r0 = 0; r0 < m; r0 += piece) {
+    const int64_t mc = (m - r0) < piece ? (m - r0) : piece;
+    CU(launch_left_vectors(s->state(), s->fin, s->k, G, r0, mc, s->fin_V, mc, s->stream));
+    CU(cudaMemcpy2DAsync(U + r0, sizeof(double) * m, s->fin_V, sizeof(double) * mc, sizeof(double) * mc, s->k,
+                         cudaMemcpyDeviceToHost, s->stream));
+  }
+  CU(cudaStreamSynchronize(s->stream));
   return SPCA_OK;
 }
 
@@ -651,6 +694,7 @@ spca_status spca_merge(spca_session* dst, const spca_session* src) {
   }
   CU(cudaStreamSynchronize(dst->stream));
   dst->m += src->m;
+  dst->u_ready = false;
   return SPCA_OK;
 }
 
@@ -677,6 +721,7 @@ spca_status spca_reset(spca_session* s, uint64_t seed) {
   s->m = 0;
   s->shift_set = false;
   s->scale_set = false;
+  s->u_ready = false;
   return SPCA_OK;
 }
 

@@ -152,6 +152,10 @@ struct FinalWork {
   double* C;          // L x L
   double* sig;        // L
   double* Vtmp;       // n x k
+  double* flip;       // L: the sign applied to each column of V
+  double* Tu;         // L x L: T (= R^-T) of the last finalize
+  double* M;          // l x k: sketch rows to left singular vectors (after a finalize)
+  double* mrow;       // k: the centring term of that map
   int* info;          // [0]: rank kept, [1]: route (0 chol, 1 eigen), [2]: jacobi sweeps
   int nparts;
 };
@@ -163,6 +167,11 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k,
                          int64_t rows_seen, bool centered);
 
 cudaError_t centered_state(const State& s, const FinalWork& f, int64_t m, cudaStream_t st);
+
+// U rows [row0, row0 + mc) of the last finalize from kept sketch rows G (m x l, FP32), into
+// column-major U with leading dimension ldu (device memory)
+cudaError_t launch_left_vectors(const State& s, const FinalWork& f, int k, const float* G, int64_t row0, int64_t mc,
+                                double* U, int64_t ldu, cudaStream_t st);
 
 // ---------------------------------------------------------------- hooks for the serving loop
 size_t session_footprint(int64_t n, int k, int p, int math, int64_t max_block_rows);   // 0: does not fit

@@ -222,6 +222,36 @@ def test_reduced_precision_storage(dtype):
     check_sigma_V({"sigma": sigma, "V": V}, ref, 10)
 
 
+def test_left_vectors_from_kept_sketch_rows(small):
+    """U from the G_out rows (Alg. 4 steps 18-19) against the oracle's U = Q U~ of the blocked
+    QB, with the sign convention that pairs it with V; U^T U = I."""
+    A = small["A"]
+    k, p, seed, mb = small["k"], small["p"], small["seed"], small["block_rows"]
+    m, n = A.shape
+    A32 = A.to(torch.float32)
+    G = torch.zeros((m, k + p), device=DEV, dtype=torch.float32)
+    with spca.Session(n, k, p, seed, max_block_rows=256) as s:
+        with pytest.raises(spca.SpcaError) as ei:
+            s.left_vectors(G[:10])          # no finalize yet
+        assert ei.value.status == 4
+        Ad = A32.to(DEV)
+        for r0 in range(0, m, mb):
+            s.update(Ad[r0:r0 + mb], G_out=G[r0:r0 + mb])
+        sigma, V = s.finalize()
+        U = s.left_vectors(G)
+        U_part = s.left_vectors(G[500:777])   # any subset of the rows: row r of U is row r of G
+        s.update(Ad[:5])
+        with pytest.raises(spca.SpcaError) as ei:
+            s.left_vectors(G)               # the state changed since the finalize
+        assert ei.value.status == 4
+    A64 = A32.double().numpy()
+    ref = O.single_pass_pca(A64, k, p, seed, mb, finalize="blocked", omega_form="f32", keep_U=True)
+    assert U.shape == (m, k)
+    assert np.abs(U - ref["U"]).max() <= 1e-5
+    assert np.array_equal(U_part, U[500:777])
+    assert np.abs(U.T @ U - np.eye(k)).max() <= 1e-5
+
+
 def test_non_finite_input_is_reported():
     A = torch.randn(64, 40, device=DEV)
     A[5, 7] = float("nan")

@@ -175,6 +175,28 @@ def test_tc_repeated_sessions_at_padded_l_32(math):
 
 
 @pytest.mark.parametrize("math", TC_MATHS)
+def test_tc_left_vectors_from_kept_sketch_rows(math):
+    """U of the tensor-core forms from their own G_out rows against the oracle's U (Omega in
+    the operand format): the leading columns agree, with the same signs, and U^T U = I."""
+    A = synth.low_rank_plus_noise(3000, 700, synth.spectrum("dec20", 80), noise_std=1e-4, mean_std=0.5, seed=31,
+                                  device=DEV, dtype=torch.float32)
+    torch.cuda.synchronize()
+    k, p = 20, 10
+    G = torch.zeros((3000, k + p), device=DEV, dtype=torch.float32)
+    with spca.Session(700, k, p, 77, math=math) as s:
+        for r0 in range(0, 3000, 512):
+            s.update(A[r0:r0 + 512], G_out=G[r0:r0 + 512])
+        sigma, V = s.finalize()
+        U = s.left_vectors(G)
+    ref = O.single_pass_pca(A.cpu().double().numpy(), k, p, 77, 512, finalize="blocked",
+                            omega_form=OMEGA_FORM[math], keep_U=True)
+    assert np.abs(U.T @ U - np.eye(k)).max() <= 1e-3
+    lead = ref["sigma"] >= 0.1 * ref["sigma"][0]
+    cos = np.sum(U[:, lead] * ref["U"][:, lead], axis=0)
+    assert np.all(cos >= 1 - 1e-3), cos
+
+
+@pytest.mark.parametrize("math", TC_MATHS)
 def test_tc_rejects_shapes_it_cannot_take(math):
     with pytest.raises(spca.SpcaError) as ei:
         spca.Session(40000, 100, 20, 1, math=math)
