@@ -268,27 +268,28 @@ __global__ void __launch_bounds__(SIGN_T) sign_fix_kernel(double* __restrict__ V
 // U[:, i] = G_bar (T^T Z[:, i]) flip_i. M[c][i] = flip_i sum_{c' < r} T[c'][c] Z[c'][i] (l x k,
 // columns beyond the rank 0) and, for the centred rows G_bar = G_hat - (1/m) 1 sG^T,
 // mrow[i] = sum_c (sG[c] / m) M[c][i] (0 when centering is off: m = 0).
+__device__ double blk_sum(double v, double* red);
+
+// One block per column i (FP64 issues slowly: the l x k entries are spread over the SMs).
 __global__ void u_map_kernel(const double* __restrict__ T, const double* __restrict__ Z, const int* __restrict__ info,
                              const double* __restrict__ flip, const double* __restrict__ sG, int64_t m, int l, int L,
                              int k, double* __restrict__ M, double* __restrict__ mrow) {
+  __shared__ double red[32];
   const int r = info[0];
   const int kk = k < r ? k : r;
-  for (int e = threadIdx.x; e < l * k; e += blockDim.x) {
-    const int c = e / k, i = e - c * k;
+  const int i = blockIdx.x;
+  double part = 0.0;
+  for (int c = threadIdx.x; c < l; c += blockDim.x) {
     double acc = 0.0;
     if (i < kk) {
       for (int cp = 0; cp < r; ++cp) acc = fma(T[cp * L + c], Z[cp * L + i], acc);
       acc *= flip[i];
     }
-    M[e] = acc;
+    M[c * k + i] = acc;
+    if (m > 0) part = fma(sG[c] / static_cast<double>(m), acc, part);
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    double acc = 0.0;
-    if (m > 0)
-      for (int c = 0; c < l; ++c) acc = fma(sG[c] / static_cast<double>(m), M[c * k + i], acc);
-    mrow[i] = acc;
-  }
+  const double tot = blk_sum(part, red);
+  if (threadIdx.x == 0) mrow[i] = tot;
 }
 
 // U rows [row0, row0 + mc) from the kept sketch rows: U[i * ldu + row] = G[row0 + row] M[:, i] - mrow[i]
@@ -1352,11 +1353,15 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
   else
     form_v_kernel<false><<<fv_grid, 256, fv_base, st>>>(f.Bt, f.X, f.sig, f.info, s.n, k, s.L, V_dev);
   sign_fix_kernel<<<k, SIGN_T, 0, st>>>(V_dev, s.n, f.flip);
-  u_map_kernel<<<1, 256, 0, st>>>(f.Tu, f.X, f.info, f.flip, s.sG, m, s.l, s.L, k, f.M, f.mrow);
-  prof->launches[SPCA_K_FINALIZE] += 25;  // launches above beyond the one begin() counted (not the copy)
+  prof->launches[SPCA_K_FINALIZE] += 24;  // launches above beyond the one begin() counted (not the copy)
   prof->end(SPCA_K_FINALIZE, st);
   e = cudaMemcpyAsync(sigma_dev, f.sig, sizeof(double) * k, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_u_map(const State& s, const FinalWork& f, int k, int64_t m, cudaStream_t st) {
+  u_map_kernel<<<k, 64, 0, st>>>(f.Tu, f.X, f.info, f.flip, s.sG, m, s.l, s.L, k, f.M, f.mrow);
   return cudaGetLastError();
 }
 

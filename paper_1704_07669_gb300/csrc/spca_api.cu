@@ -617,6 +617,7 @@ spca_status spca_left_vectors(spca_session* s, const float* G, int64_t m, double
     if (!ok || (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged))
       return fail(s, SPCA_E_INVALID, "G must be device memory (the G_out rows of spca_update)");
   }
+  CU(launch_u_map(s->state(), s->fin, s->k, s->opt.center ? s->m : 0, s->stream));
   if (out_on_device) {
     CU(launch_left_vectors(s->state(), s->fin, s->k, G, 0, m, U, m, s->stream));
     CU(cudaStreamSynchronize(s->stream));

@@ -168,6 +168,10 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k,
 
 cudaError_t centered_state(const State& s, const FinalWork& f, int64_t m, cudaStream_t st);
 
+// the l x k map to U (and its centring term) from the last finalize's R^-T, eigenvectors and
+// column signs; m: the rows of the centring (0 when centering is off)
+cudaError_t launch_u_map(const State& s, const FinalWork& f, int k, int64_t m, cudaStream_t st);
+
 // U rows [row0, row0 + mc) of the last finalize from kept sketch rows G (m x l, FP32), into
 // column-major U with leading dimension ldu (device memory)
 cudaError_t launch_left_vectors(const State& s, const FinalWork& f, int k, const float* G, int64_t row0, int64_t mc,
