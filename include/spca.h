@@ -167,6 +167,22 @@ spca_status spca_finalize(spca_session* s, double* sigma, double* V, int32_t out
 spca_status spca_left_vectors(spca_session* s, const float* G, int64_t m, double* U, int32_t out_on_device);
 
 /*
+ * spca_power_step - the power scheme with P = 1 (Sec. 3.2 and Sec. 4): for
+ * Alg. 4, run the while loop once more with Omega replaced by H after "orth".
+ * Replaces Omega by the orthonormal basis of the centred H_bar of the rows seen
+ * so far (Cholesky QR twice, FP64 on the device; stored in the pass's operand
+ * format) and clears H, the Gram matrix, the sums and the row count; the shift c
+ * is kept. The caller then passes over the same rows again (spca_update) and
+ * calls spca_finalize, which returns the result for (A A^T) A: the same
+ * singular vectors with the tail's relative weight reduced.
+ * A session after a power step does not merge (SPCA_E_STATE); spca_reset goes
+ * back to the Gaussian Omega. Synchronises the session stream.
+ * Errors: SPCA_E_NUMERIC (no rows yet, or H_bar numerically of rank < l; the
+ * session is then unchanged), SPCA_E_CUDA, SPCA_E_STATE.
+ */
+spca_status spca_power_step(spca_session* s);
+
+/*
  * spca_get_state - the centred accumulators, for inspection and parity tests.
  *   H_bar    n x l doubles, row-major: A_bar^T G_bar (NULL = skip)
  *   gram_bar l x l doubles: G_bar^T G_bar (NULL = skip)

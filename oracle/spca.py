@@ -400,8 +400,18 @@ def jacobi_svd(A, sweeps=60, tol=1e-15):
 # The whole method.
 # --------------------------------------------------------------------------
 
+def power_omega(H, omega_form="f64"):
+    """The power scheme with P = 1 for Alg. 4 (Sec. 3.2, Sec. 4): the test matrix of the
+    extra pass is H after ``orth`` - the Q factor of H's QR - defined, like the random
+    Omega, as its value in the operand format."""
+    Q, _ = qr(H)
+    if omega_form == "f64":
+        return Q
+    return {"f32": round_f32, "bf16": round_bf16, "f16": round_f16}[omega_form](Q)
+
+
 def single_pass_pca(A, k, p, seed, block_rows, *, center_columns=True, b=10,
-                    finalize="blocked", omega_form="f64", keep_U=False):
+                    finalize="blocked", omega_form="f64", keep_U=False, power=0):
     """Single-pass PCA (Alg. 4) of the rows of A, in FP64.
 
     A           m x n data (float64 view of the stored values), rows = observations
@@ -411,6 +421,8 @@ def single_pass_pca(A, k, p, seed, block_rows, *, center_columns=True, b=10,
                 depend on it in exact arithmetic
     finalize    'blocked' = Alg. 4 steps 9-16 on the stored G (the paper);
                 'gram'    = R from the Gram matrix (G not stored)
+    power       P of the power scheme (0 or more): each extra pass reruns the while
+                loop with Omega replaced by orth(H) (Sec. 4)
     Returns dict(sigma (k), V (n x k), U (m x k) or None, Omega, G, H).
     """
     A = np.asarray(A, dtype=np.float64)
@@ -419,6 +431,9 @@ def single_pass_pca(A, k, p, seed, block_rows, *, center_columns=True, b=10,
     Om = omega(n, l, seed, omega_form)
     A_bar = center(A) if center_columns else A
     G, H = sketch_pass(row_blocks(A_bar, block_rows), Om)
+    for _ in range(power):   # the while loop once more, Omega replaced by orth(H)
+        Om = power_omega(H, omega_form)
+        G, H = sketch_pass(row_blocks(A_bar, block_rows), Om)
     if finalize == "blocked":
         Q, B = blocked_qb(G, H, Om, b)
     elif finalize == "gram":

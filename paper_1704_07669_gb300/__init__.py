@@ -71,6 +71,7 @@ def lib():
             "spca_update": (i32, [vp, vp, i64, i64, i32, vp, i32, vp]),
             "spca_finalize": (i32, [vp, vp, vp, i32]),
             "spca_left_vectors": (i32, [vp, vp, i64, vp, i32]),
+            "spca_power_step": (i32, [vp]),
             "spca_get_state": (i32, [vp, vp, vp, vp, vp, vp]),
             "spca_merge": (i32, [vp, vp]),
             "spca_sync": (i32, [vp]),
@@ -198,6 +199,10 @@ def spca_left_vectors(handle, G, U, m=None, out_on_device=None):
     _check(lib().spca_left_vectors(handle, ga, int(m), ua, int(on)), handle)
 
 
+def spca_power_step(handle):
+    _check(lib().spca_power_step(handle), handle)
+
+
 def spca_get_state(handle, H_bar=None, gram_bar=None, colsum=None, shift=None):
     m = ctypes.c_int64(0)
     _check(lib().spca_get_state(handle, _ptr(H_bar)[0], _ptr(gram_bar)[0], _ptr(colsum)[0], _ptr(shift)[0],
@@ -309,6 +314,10 @@ class Session:
         Uc = np.zeros((self.k, m))      # column-major m x k == row-major k x m
         spca_left_vectors(self.handle, G, Uc, m=m, out_on_device=False)
         return Uc.T.copy()
+
+    def power_step(self):
+        """Omega <- orth(H_bar) for one more pass over the same rows (power scheme, P = 1)."""
+        spca_power_step(self.handle)
 
     def state(self):
         H = np.zeros((self.n, self.l))

@@ -1249,8 +1249,8 @@ cudaError_t centered_state(const State& s, const FinalWork& f, int64_t m, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, double* sigma_dev, double* V_dev,
-                         cudaStream_t st, Prof* prof, int64_t rows_seen, bool centered) {
+// The dynamic shared memory limits of the one-block dense kernels, set once per process.
+void set_dense_attrs() {
   static bool attr_done = false;
   if (!attr_done) {
     cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kMaxDenseSmem));
@@ -1269,6 +1269,11 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
                          static_cast<int>(kMaxDenseSmem));
     attr_done = true;
   }
+}
+
+cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, double* sigma_dev, double* V_dev,
+                         cudaStream_t st, Prof* prof, int64_t rows_seen, bool centered) {
+  set_dense_attrs();
   prof->begin(SPCA_K_FINALIZE, st);
   cudaError_t e = centered_state(s, f, m, st);
   if (e != cudaSuccess) return e;
@@ -1357,6 +1362,63 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
   prof->end(SPCA_K_FINALIZE, st);
   e = cudaMemcpyAsync(sigma_dev, f.sig, sizeof(double) * k, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ the power scheme (P = 1)
+
+// T = the l x l identity (zero elsewhere in L x L); info[0] = l (all output columns of
+// bt_and_c), info[3] = 0 (no failed factorisation yet).
+__global__ void eye_kernel(double* __restrict__ T, int l, int L, int* __restrict__ info) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < L * L; e += gridDim.x * blockDim.x)
+    T[e] = (e / L == e % L && e / L < l) ? 1.0 : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    info[0] = l;
+    info[3] = 0;
+  }
+}
+
+// One block: C = L1 L1^T (FP64 Cholesky, in place) and T = L1^-1, so that Q = Y T^T has
+// orthonormal columns when C = Y^T Y. A pivot at or below l eps max_i C_ii sets info[3].
+__global__ void chol_tinv64_kernel(double* __restrict__ C, int l, int L, double* __restrict__ T, int* __restrict__ info) {
+  __shared__ double tol;
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int c = 0; c < l; ++c) mx = fmax(mx, C[c * L + c]);
+    tol = static_cast<double>(l) * 2.220446049250313e-16 * mx;
+  }
+  __syncthreads();
+  const bool ok = blk_cholesky(C, l, L, tol);
+  if (!ok) {
+    if (threadIdx.x == 0) info[3] = 1;
+    return;
+  }
+  for (int e = threadIdx.x; e < L * L; e += blockDim.x) T[e] = 0.0;
+  __syncthreads();
+  blk_trinv_lower(C, T, l, L);
+}
+
+cudaError_t power_omega_run(const State& s, const FinalWork& f, int64_t m, cudaStream_t st, const double** Q) {
+  set_dense_attrs();
+  cudaError_t e = centered_state(s, f, m, st);
+  if (e != cudaSuccess) return e;
+  const int l = s.l, L = s.L;
+  const int64_t nblk = (s.n + BT_ROWS - 1) / BT_ROWS;
+  const int parts = static_cast<int>(nblk < f.nparts ? nblk : f.nparts);
+  const size_t bt_base = 2 * sizeof(double) * BT_ROWS * L;
+  const int tcc = bt_base + sizeof(double) * L * l <= kMaxDenseSmem ? l : 32;
+  const size_t bt_smem = bt_base + sizeof(double) * L * tcc;
+  const int cr_grid = (L * L + 31) / 32;
+  // Q = orth(H_bar) by Cholesky QR twice: C = H^T H = L1 L1^T, Q1 = H L1^-T; then again on Q1
+  eye_kernel<<<(L * L + 255) / 256, 256, 0, st>>>(f.T, l, L, f.info);
+  bt_and_c_kernel<<<parts, 256, bt_smem, st>>>(f.Hbar, f.T, f.info, s.n, l, L, tcc, f.Bt, f.Cpart);
+  c_reduce_kernel<<<cr_grid, CR_T, 0, st>>>(f.Cpart, parts, L, f.C);
+  chol_tinv64_kernel<<<1, 256, 0, st>>>(f.C, l, L, f.T, f.info);
+  bt_and_c_kernel<<<parts, 256, bt_smem, st>>>(f.Hbar, f.T, f.info, s.n, l, L, tcc, f.Bt, f.Cpart);
+  c_reduce_kernel<<<cr_grid, CR_T, 0, st>>>(f.Cpart, parts, L, f.C);
+  chol_tinv64_kernel<<<1, 256, 0, st>>>(f.C, l, L, f.T, f.info);
+  bt_and_c_kernel<<<parts, 256, bt_smem, st>>>(f.Bt, f.T, f.info, s.n, l, L, tcc, f.Hbar, f.Cpart);
+  *Q = f.Hbar;
   return cudaGetLastError();
 }
 

@@ -158,6 +158,15 @@ __global__ void omega_f32_kernel(uint64_t seed, int64_t n, int l, int L, float* 
   }
 }
 
+// Omega given as a matrix (n x L FP64, ld L; the power scheme's orth(H)) in FP32, columns
+// >= l zero.
+__global__ void omega_from_q_f32_kernel(const double* __restrict__ Q, int64_t n, int l, int L, float* __restrict__ out) {
+  const int64_t total = n * L;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    out[idx] = (idx % L) < l ? static_cast<float>(Q[idx]) : 0.f;
+}
+
 __global__ void omega_words_kernel(uint64_t seed, int64_t n, int qn, uint32_t* __restrict__ out) {
   const int64_t total = n * qn;
   for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
@@ -888,6 +897,11 @@ cudaError_t launch_omega_f32(uint64_t seed, int64_t n, int l, int L, float* out,
   if (prof) prof->begin(SPCA_K_OMEGA, st);
   omega_f32_kernel<<<grid_for(n * (L / 4), 256), 256, 0, st>>>(seed, n, l, L, out, ld);
   if (prof) prof->end(SPCA_K_OMEGA, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_omega_from_q_f32(const double* Q, int64_t n, int l, int L, float* out, cudaStream_t st) {
+  omega_from_q_f32_kernel<<<grid_for(n * L, 256), 256, 0, st>>>(Q, n, l, L, out);
   return cudaGetLastError();
 }
 

@@ -610,9 +610,28 @@ __global__ void omega_op_kernel(uint64_t seed, int64_t n, int64_t npad, int l, i
   }
 }
 
+// Omega given as a matrix (n x L FP64, ld L; the power scheme's orth(H)), in the operand
+// format and the chunk layout above; columns >= l and features >= n are 0.
+template <int FMT>
+__global__ void omega_from_q_op_kernel(const double* __restrict__ Q, int64_t n, int64_t npad, int l, int L,
+                                       uint16_t* __restrict__ out) {
+  const int64_t total = npad * L;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t j = idx / L;
+    const int c = static_cast<int>(idx % L);
+    const float v = (j < n && c < l) ? static_cast<float>(Q[j * L + c]) : 0.f;
+    uint8_t* chunk = reinterpret_cast<uint8_t*>(out) + (j / 64) * static_cast<int64_t>(L) * 128;
+    const uint32_t off = static_cast<uint32_t>(c >> 3) * 1024u +
+                         sw128(static_cast<uint32_t>(c & 7), static_cast<uint32_t>(j % 64) * 2u);
+    *reinterpret_cast<uint16_t*>(chunk + off) = static_cast<uint16_t>(pack2<FMT>(v, 0.f) & 0xFFFFu);
+  }
+}
+
 // The operand scale of the FP16 form: the largest shifted row norm of the first rows
-// bounds every entry of s G (|g_rc| <= ||a_r - c|| ||omega_c||, ||omega_c|| ~ sqrt(n)),
-// so s = 2^floor(log2(2^14 / (1.25 sqrt(n) max_r ||a_r - c||))) keeps s G below 2^14 with
+// bounds every entry of s G (|g_rc| <= ||a_r - c|| ||omega_c||, ||omega_c|| ~ sqrt(n) for
+// the Gaussian Omega, 1 for an orthonormal one), so
+// s = 2^floor(log2(2^14 / (1.25 ||omega_c|| max_r ||a_r - c||))) keeps s G below 2^14 with
 // four-fold headroom under the FP16 maximum.
 __global__ void row_norm_max_kernel(const float* __restrict__ rows, int64_t m, int64_t n, int64_t ld,
                                     const float* __restrict__ shift, unsigned int* __restrict__ out_bits) {
@@ -634,11 +653,11 @@ __global__ void row_norm_max_kernel(const float* __restrict__ rows, int64_t m, i
   }
 }
 
-__global__ void op_scale_kernel(const unsigned int* __restrict__ bits, int64_t n, float* __restrict__ scale) {
+__global__ void op_scale_kernel(const unsigned int* __restrict__ bits, double omega_norm, float* __restrict__ scale) {
   const float mx = __uint_as_float(*bits);
   float s = 1.f;
   if (mx > 0.f && isfinite(mx)) {
-    const double e = floor(log2(16384.0 / (1.25 * sqrt(static_cast<double>(n)) * static_cast<double>(mx))));
+    const double e = floor(log2(16384.0 / (1.25 * omega_norm * static_cast<double>(mx))));
     s = static_cast<float>(exp2(fmin(fmax(e, -100.0), 100.0)));
   }
   *scale = s;
@@ -732,14 +751,23 @@ cudaError_t launch_omega_op(int fmt, uint64_t seed, int64_t n, int64_t npad, int
   return cudaGetLastError();
 }
 
+cudaError_t launch_omega_from_q_op(int fmt, const double* Q, int64_t n, int64_t npad, int l, int L, uint16_t* out,
+                                   cudaStream_t st) {
+  if (fmt == FMT_F16)
+    omega_from_q_op_kernel<FMT_F16><<<grid_for(npad * L, 256), 256, 0, st>>>(Q, n, npad, l, L, out);
+  else
+    omega_from_q_op_kernel<FMT_BF16><<<grid_for(npad * L, 256), 256, 0, st>>>(Q, n, npad, l, L, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_op_scale(const float* rows, int64_t m, int64_t n, int64_t ld, const float* shift,
-                            unsigned int* bits, float* scale, cudaStream_t st, Prof* prof) {
+                            unsigned int* bits, float* scale, double omega_norm, cudaStream_t st, Prof* prof) {
   if (prof) prof->begin(SPCA_K_SHIFT, st);
   cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
   const int blocks = static_cast<int>(m < 152 * 8 ? m : 152 * 8);
   row_norm_max_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(rows, m, n, ld, shift, bits);
-  op_scale_kernel<<<1, 1, 0, st>>>(bits, n, scale);
+  op_scale_kernel<<<1, 1, 0, st>>>(bits, omega_norm, scale);
   if (prof) {
     prof->launches[SPCA_K_SHIFT] += 1;
     prof->end(SPCA_K_SHIFT, st);

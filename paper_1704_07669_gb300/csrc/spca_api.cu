@@ -2,6 +2,7 @@
 // host staging, and the order of the launches that make up the pass.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -92,6 +93,7 @@ struct spca_session {
   bool shift_set = false;
   bool scale_set = false;     // FP16 form: operand scale computed from the first rows
   bool u_ready = false;       // a finalize has formed the map to U since the last change of the state
+  bool omega_orth = false;    // Omega is orth(H) of a previous pass (power scheme), not the Philox draw
   char err[512] = "";
   char desc[256] = "";
 
@@ -213,7 +215,7 @@ spca_status run_piece(spca_session* s, const void* rows, int64_t m, int64_t ld, 
   }
   if (s->tc && s->tcw.fmt == 1 && !s->scale_set) {
     CU(launch_op_scale(static_cast<const float*>(rows), m, s->n, ld, s->shift, s->tcw.scale_bits, s->tcw.scale,
-                       s->stream, &s->prof));
+                       s->omega_orth ? 1.0 : std::sqrt(static_cast<double>(s->n)), s->stream, &s->prof));
     s->scale_set = true;
   }
   if (s->tc) {
@@ -635,6 +637,38 @@ spca_status spca_left_vectors(spca_session* s, const float* G, int64_t m, double
   return SPCA_OK;
 }
 
+spca_status spca_power_step(spca_session* s) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  if (s->m < 1) return fail(s, SPCA_E_NUMERIC, "no rows accumulated yet");
+  CU(cudaSetDevice(s->device));
+  st = flush_tc(s);
+  if (st != SPCA_OK) return st;
+  const double* Q = nullptr;
+  CU(power_omega_run(s->state(), s->fin, s->opt.center ? s->m : 0, s->stream, &Q));
+  CU(cudaMemcpyAsync(s->host_flags, s->fin.info + 3, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CU(cudaStreamSynchronize(s->stream));
+  if (s->host_flags[0] != 0)
+    return fail(s, SPCA_E_NUMERIC, "H is numerically rank deficient: no orthonormal basis of rank l for the power step");
+  // Omega <- orth(H_bar) in the pass's operand format, then the accumulators of the next pass
+  if (s->tc) {
+    CU(launch_omega_from_q_op(s->tcw.fmt, Q, s->n, tc_npad(s->tcw), s->l, s->L, s->tcw.om16, s->stream));
+  } else {
+    CU(launch_omega_from_q_f32(Q, s->n, s->l, s->L, s->omega32, s->stream));
+  }
+  const int L = s->L;
+  CU(cudaMemsetAsync(s->H, 0, sizeof(double) * s->n * L, s->stream));
+  CU(cudaMemsetAsync(s->colsum, 0, sizeof(double) * s->n, s->stream));
+  CU(cudaMemsetAsync(s->sG, 0, sizeof(double) * L, s->stream));
+  CU(cudaMemsetAsync(s->gram, 0, sizeof(double) * L * L, s->stream));
+  CU(cudaStreamSynchronize(s->stream));
+  s->m = 0;                  // the shift c stays: the next pass centres on the same c
+  s->scale_set = false;      // FP16: the operand scale of the new Omega (unit columns)
+  s->u_ready = false;
+  s->omega_orth = true;
+  return SPCA_OK;
+}
+
 spca_status spca_get_state(spca_session* s, double* H_bar, double* gram_bar, double* colsum, float* shift,
                            int64_t* m) {
   spca_status st = check_usable(s);
@@ -667,6 +701,8 @@ spca_status spca_merge(spca_session* dst, const spca_session* src) {
       src->opt.center != dst->opt.center || src->device != dst->device)
     return fail(s, SPCA_E_INVALID, "sessions differ in n, k, p, seed, centering or device");
   if (src->opt.math != dst->opt.math) return fail(s, SPCA_E_INVALID, "sessions differ in math form");
+  if (src->omega_orth || dst->omega_orth)
+    return fail(s, SPCA_E_STATE, "sessions after a power step have their own Omega and do not merge");
   CU(cudaSetDevice(dst->device));
   st = flush_tc(dst);
   if (st != SPCA_OK) return st;
@@ -723,6 +759,7 @@ spca_status spca_reset(spca_session* s, uint64_t seed) {
   s->shift_set = false;
   s->scale_set = false;
   s->u_ready = false;
+  s->omega_orth = false;
   return SPCA_OK;
 }
 

@@ -37,6 +37,10 @@ struct Prof {
 cudaError_t launch_omega_f32(uint64_t seed, int64_t n, int l, int L, float* out, int64_t ld,
                              cudaStream_t st, Prof* prof = nullptr);
 cudaError_t launch_omega_words(uint64_t seed, int64_t n, int l, uint32_t* out, cudaStream_t st);
+// Omega from a matrix Q (n x L FP64, ld L), as FP32 / in the tensor-core operand layout
+cudaError_t launch_omega_from_q_f32(const double* Q, int64_t n, int l, int L, float* out, cudaStream_t st);
+cudaError_t launch_omega_from_q_op(int fmt, const double* Q, int64_t n, int64_t npad, int l, int L, uint16_t* out,
+                                   cudaStream_t st);
 
 // Shift c = FP32 of the FP64 column mean of the given rows; part: kShiftParts x n doubles.
 constexpr int kShiftParts = 64;
@@ -125,9 +129,10 @@ bool tc_config(int64_t n, int L, int fmt, TcConfig* cfg);
 const char* tc_config_reason();   // why the last tc_config call said no
 cudaError_t launch_omega_op(int fmt, uint64_t seed, int64_t n, int64_t npad, int l, int L, uint16_t* out,
                             cudaStream_t st, Prof* prof);
-// FP16 form: s = power of two from the largest shifted row norm of the given rows
+// FP16 form: s = power of two from the largest shifted row norm of the given rows and a bound
+// on the norm of Omega's columns
 cudaError_t launch_op_scale(const float* rows, int64_t m, int64_t n, int64_t ld, const float* shift,
-                            unsigned int* bits, float* scale, cudaStream_t st, Prof* prof);
+                            unsigned int* bits, float* scale, double omega_norm, cudaStream_t st, Prof* prof);
 cudaError_t tc_pass(const State& s, const TcWork& w, const TcPending& pend, cudaStream_t st, Prof* prof);
 // H partials -> FP64 state and Gram partials -> state, for a launch of ncl clusters
 cudaError_t launch_tc_finish(const State& s, const TcWork& w, int ncl, int64_t npad, int nctas, cudaStream_t st,
@@ -167,6 +172,10 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k,
                          int64_t rows_seen, bool centered);
 
 cudaError_t centered_state(const State& s, const FinalWork& f, int64_t m, cudaStream_t st);
+
+// the power scheme with P = 1: Q = orth(H_bar) (n x L FP64, in FinalWork scratch) by Cholesky
+// QR twice; f.info[3] != 0 afterwards if H_bar was numerically rank deficient
+cudaError_t power_omega_run(const State& s, const FinalWork& f, int64_t m, cudaStream_t st, const double** Q);
 
 // the l x k map to U (and its centring term) from the last finalize's R^-T, eigenvectors and
 // column signs; m: the rows of the centring (0 when centering is off)

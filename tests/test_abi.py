@@ -77,6 +77,7 @@ def test_null_session_calls_return_errors(lib):
     assert lib.spca_update(None, None, 1, 1, 0, None, 1, None) == 1
     assert lib.spca_finalize(None, None, None, 0) == 1
     assert lib.spca_left_vectors(None, None, 1, None, 0) == 1
+    assert lib.spca_power_step(None) == 1
     assert lib.spca_sync(None) == 1
     assert lib.spca_reset(None, 0) == 1
     assert lib.spca_merge(None, None) == 1

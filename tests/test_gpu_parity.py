@@ -252,6 +252,44 @@ def test_left_vectors_from_kept_sketch_rows(small):
     assert np.abs(U.T @ U - np.eye(k)).max() <= 1e-5
 
 
+def test_power_scheme_pass_matches_oracle(small):
+    """P = 1 (Sec. 4): a pass, spca_power_step (Omega <- orth(H_bar)), the same rows again,
+    finalize - against the oracle's while loop run twice. Merging such a session is refused,
+    and spca_reset returns to the Gaussian Omega."""
+    A = small["A"]
+    k, p, seed, mb = small["k"], small["p"], small["seed"], small["block_rows"]
+    m, n = A.shape
+    Ad = A.to(torch.float32).to(DEV)
+    with spca.Session(n, k, p, seed, max_block_rows=256) as s, spca.Session(n, k, p, seed) as other:
+        with pytest.raises(spca.SpcaError) as ei:
+            s.power_step()                   # no rows yet
+        assert ei.value.status == 5
+        for _ in range(2):
+            for r0 in range(0, m, mb):
+                s.update(Ad[r0:r0 + mb])
+            if s.rows_seen and _ == 0:
+                s.power_step()
+        assert s.rows_seen == m
+        sigma, V = s.finalize()
+        other.update(Ad[:100])
+        with pytest.raises(spca.SpcaError) as ei:
+            spca.spca_merge(other.handle, s.handle)
+        assert ei.value.status == 4
+        s.reset(seed)
+        for r0 in range(0, m, mb):
+            s.update(Ad[r0:r0 + mb])
+        sigma0, V0 = s.finalize()
+    A64 = A.to(torch.float32).double().numpy()
+    ref = O.single_pass_pca(A64, k, p, seed, mb, finalize="blocked", omega_form="f32", power=1)
+    check_sigma_V({"sigma": sigma, "V": V}, ref, k, tol_cos=1e-5)
+    ref0 = O.single_pass_pca(A64, k, p, seed, mb, finalize="blocked", omega_form="f32")
+    check_sigma_V({"sigma": sigma0, "V": V0}, ref0, k)
+    # the power pass is closer to the exact singular values (Sec. 4; with sigma_i = 1/i this
+    # flat spectrum gains a factor of about 3.5, the Type 1 pin in the oracle tests far more)
+    exact = np.linalg.svd(O.center(A64), compute_uv=False)[:k]
+    assert np.max(np.abs(sigma - exact) / exact) < np.max(np.abs(sigma0 - exact) / exact) / 2
+
+
 def test_non_finite_input_is_reported():
     A = torch.randn(64, 40, device=DEV)
     A[5, 7] = float("nan")

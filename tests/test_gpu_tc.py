@@ -197,6 +197,28 @@ def test_tc_left_vectors_from_kept_sketch_rows(math):
 
 
 @pytest.mark.parametrize("math", TC_MATHS)
+def test_tc_power_scheme_pass(math):
+    """The power step on the tensor-core forms: Omega <- orth(H_bar) in the operand format,
+    one more pass, against the oracle's twice-run while loop with Omega in that format."""
+    A = synth.low_rank_plus_noise(3000, 700, synth.spectrum("inv", 300), noise_std=1e-3, mean_std=0.5, seed=41,
+                                  device=DEV, dtype=torch.float32)
+    torch.cuda.synchronize()
+    k, p = 20, 10
+    with spca.Session(700, k, p, 78, math=math) as s:
+        for _ in range(2):
+            for r0 in range(0, 3000, 512):
+                s.update(A[r0:r0 + 512])
+            if _ == 0:
+                s.power_step()
+        sigma, V = s.finalize()
+    ref = O.single_pass_pca(A.cpu().double().numpy(), k, p, 78, 512, finalize="blocked",
+                            omega_form=OMEGA_FORM[math], power=1)
+    assert_sigma(sigma, ref["sigma"], math)
+    lead = ref["sigma"] >= 0.1 * ref["sigma"][0]
+    assert O.max_principal_sine(V[:, lead], ref["V"][:, lead]) <= 5e-2
+
+
+@pytest.mark.parametrize("math", TC_MATHS)
 def test_tc_rejects_shapes_it_cannot_take(math):
     with pytest.raises(spca.SpcaError) as ei:
         spca.Session(40000, 100, 20, 1, math=math)

@@ -9,6 +9,7 @@
 * Exactness: rank(A) = r <= l recovers sigma and V exactly; l >= n gives sigma(A).
 * Brute force: the one-sided Jacobi SVD against LAPACK on tiny inputs.
 * Eq. 7: the expected-error bound holds on average over seeds.
+* Power scheme (P = 1): the QB of (A A^T) A, and the Sec. 4 error reduction on Type 1.
 * Sec. 4.1: the Type 1 3000 x 3000 worked example (golden fixture).
 * Mutations: plausible slips planted in the oracle's own source make a pin fail.
 """
@@ -117,6 +118,35 @@ def test_alg4_equals_alg1_equals_gram_reading():
     for s, V in ((rg["sigma"], rg["V"]), (s1, V1)):
         assert np.max(np.abs(s - r4["sigma"]) / r4["sigma"]) < 1e-12
         assert np.abs(V - r4["V"]).max() < 1e-10
+
+
+# ---------------------------------------------------------------- power scheme (Sec. 3.2, Sec. 4)
+
+def test_power_scheme_is_the_qb_of_a_at_a_times_omega():
+    """P = 1: the while loop once more with Omega <- orth(H) gives the randomized QB of
+    (A A^T) A (Sec. 3.2): Q = orth(A orth(A^T A Omega)), B = Q^T A, written out with
+    numpy's QR and SVD."""
+    A = _rand(300, 200, 21) @ np.diag(0.97 ** np.arange(200))
+    k, p = 8, 4
+    r = O.single_pass_pca(A, k, p, 22, 37, b=4, power=1)
+    A_bar = O.center(A)
+    Om = O.omega(200, k + p, 22)
+    Om2, _ = np.linalg.qr(A_bar.T @ (A_bar @ Om))
+    Q, _ = np.linalg.qr(A_bar @ Om2)
+    _, s, Vt = np.linalg.svd(Q.T @ A_bar, full_matrices=False)
+    V, _ = O.sign_fix(Vt[:k].T)
+    assert np.max(np.abs(r["sigma"] - s[:k]) / s[:k]) < 1e-11
+    assert np.abs(r["V"] - V).max() < 1e-9
+
+
+def test_power_scheme_shrinks_the_sigma_error_on_a_slow_decay():
+    """Sec. 4: one more pass 'dramatically reduces max_err' for the Type 1 spectrum."""
+    m, n, k = 1500, 1000, 16
+    sig = synth.spectrum("type1", n)
+    A = (synth.haar(m, n, 5).numpy() * sig) @ synth.haar(n, n, 6).numpy().T
+    e0 = np.max(np.abs(O.single_pass_pca(A, k, 4, 7, 100, center_columns=False)["sigma"] - sig[:k]))
+    e1 = np.max(np.abs(O.single_pass_pca(A, k, 4, 7, 100, center_columns=False, power=1)["sigma"] - sig[:k]))
+    assert e1 <= e0 / 100 and e1 <= 1e-6, (e0, e1)
 
 
 # ---------------------------------------------------------------- exactness
