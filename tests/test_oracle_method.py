@@ -139,6 +139,23 @@ def test_power_scheme_is_the_qb_of_a_at_a_times_omega():
     assert np.abs(r["V"] - V).max() < 1e-9
 
 
+def test_two_power_passes_are_the_qb_of_a_at_a_squared_times_omega():
+    """P = 2: Omega <- orth(H) twice gives Q = orth((A A^T)^2 A Omega) (Sec. 3.2)."""
+    A = _rand(250, 160, 23) @ np.diag(0.96 ** np.arange(160))
+    k, p = 6, 4
+    r = O.single_pass_pca(A, k, p, 24, 41, b=5, power=2, center_columns=False)
+    Om = O.omega(160, k + p, 24)
+    Y = A @ Om
+    for _ in range(2):
+        W, _ = np.linalg.qr(A.T @ Y)
+        Y = A @ W
+    Q, _ = np.linalg.qr(Y)
+    _, s, Vt = np.linalg.svd(Q.T @ A, full_matrices=False)
+    V, _ = O.sign_fix(Vt[:k].T)
+    assert np.max(np.abs(r["sigma"] - s[:k]) / s[:k]) < 1e-11
+    assert np.abs(r["V"] - V).max() < 1e-9
+
+
 def test_power_scheme_shrinks_the_sigma_error_on_a_slow_decay():
     """Sec. 4: one more pass 'dramatically reduces max_err' for the Type 1 spectrum."""
     m, n, k = 1500, 1000, 16
