@@ -183,6 +183,27 @@ spca_status spca_left_vectors(spca_session* s, const float* G, int64_t m, double
 spca_status spca_power_step(spca_session* s);
 
 /*
+ * Checkpoint and resume. The session's state is a sum over the rows seen (Eq. 11),
+ * so a pass stopped after any block resumes from its accumulators: save them, and
+ * load them into a session created with the same n, k, p, seed and options (in
+ * this or another process), then continue with spca_update.
+ *   spca_state_bytes  host bytes of a checkpoint of this session
+ *   spca_save_state   write it into buf (host memory, >= spca_state_bytes);
+ *                     flushes pending tensor-core blocks, synchronises
+ *   spca_load_state   restore it (the session's own accumulators are replaced);
+ *                     synchronises
+ * A checkpoint holds H, the Gram matrix, the sums, the shift, the FP16 operand
+ * scale, the row count and, after spca_power_step, Omega. Layout (native byte
+ * order, host): a fixed header (magic "SPCAST1", n, m, k, p, l, L, math,
+ * center, seed, flags, the size of the Omega part), then the arrays in that
+ * order. Errors: SPCA_E_INVALID (NULL pointers, short buffer, a checkpoint of
+ * a session with other n, k, p, seed, math or centering), SPCA_E_CUDA.
+ */
+spca_status spca_state_bytes(spca_session* s, size_t* bytes);
+spca_status spca_save_state(spca_session* s, void* buf, size_t bytes);
+spca_status spca_load_state(spca_session* s, const void* buf, size_t bytes);
+
+/*
  * spca_get_state - the centred accumulators, for inspection and parity tests.
  *   H_bar    n x l doubles, row-major: A_bar^T G_bar (NULL = skip)
  *   gram_bar l x l doubles: G_bar^T G_bar (NULL = skip)

@@ -72,6 +72,9 @@ def lib():
             "spca_finalize": (i32, [vp, vp, vp, i32]),
             "spca_left_vectors": (i32, [vp, vp, i64, vp, i32]),
             "spca_power_step": (i32, [vp]),
+            "spca_state_bytes": (i32, [vp, ctypes.POINTER(ctypes.c_size_t)]),
+            "spca_save_state": (i32, [vp, vp, ctypes.c_size_t]),
+            "spca_load_state": (i32, [vp, vp, ctypes.c_size_t]),
             "spca_get_state": (i32, [vp, vp, vp, vp, vp, vp]),
             "spca_merge": (i32, [vp, vp]),
             "spca_sync": (i32, [vp]),
@@ -203,6 +206,20 @@ def spca_power_step(handle):
     _check(lib().spca_power_step(handle), handle)
 
 
+def spca_save_state(handle):
+    """A checkpoint of the session's accumulators (bytes)."""
+    nb = ctypes.c_size_t(0)
+    _check(lib().spca_state_bytes(handle, ctypes.byref(nb)), handle)
+    buf = ctypes.create_string_buffer(nb.value)
+    _check(lib().spca_save_state(handle, ctypes.cast(buf, ctypes.c_void_p), nb), handle)
+    return buf.raw
+
+
+def spca_load_state(handle, data):
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(lib().spca_load_state(handle, ctypes.cast(buf, ctypes.c_void_p), len(data)), handle)
+
+
 def spca_get_state(handle, H_bar=None, gram_bar=None, colsum=None, shift=None):
     m = ctypes.c_int64(0)
     _check(lib().spca_get_state(handle, _ptr(H_bar)[0], _ptr(gram_bar)[0], _ptr(colsum)[0], _ptr(shift)[0],
@@ -314,6 +331,13 @@ class Session:
         Uc = np.zeros((self.k, m))      # column-major m x k == row-major k x m
         spca_left_vectors(self.handle, G, Uc, m=m, out_on_device=False)
         return Uc.T.copy()
+
+    def save_state(self):
+        """A checkpoint (bytes) that load_state restores into a session of the same parameters."""
+        return spca_save_state(self.handle)
+
+    def load_state(self, data):
+        spca_load_state(self.handle, data)
 
     def power_step(self):
         """Omega <- orth(H_bar) for one more pass over the same rows (power scheme, P = 1)."""

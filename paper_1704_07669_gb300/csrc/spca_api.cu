@@ -637,6 +637,138 @@ spca_status spca_left_vectors(spca_session* s, const float* G, int64_t m, double
   return SPCA_OK;
 }
 
+// ---------------------------------------------------------------- checkpoint / resume
+// Layout: the header below, then H (n L doubles), the Gram matrix (L L doubles), the column
+// sums (n doubles), the sums of G (L doubles), the shift (n floats), the FP16 operand scale
+// (one float) and, after a power step, Omega (n L floats, or the tensor-core operand layout:
+// npad L halves).
+namespace {
+struct CkptHeader {
+  char magic[8];           // "SPCAST1"
+  int64_t n, m;
+  int32_t k, p, l, L, math, center;
+  uint64_t seed;
+  int32_t shift_set, scale_set, omega_orth, reserved;
+  int64_t omega_bytes;
+};
+constexpr char kCkptMagic[8] = {'S', 'P', 'C', 'A', 'S', 'T', '1', 0};
+
+int64_t ckpt_omega_bytes(const spca_session* s) {
+  if (!s->omega_orth) return 0;
+  return s->tc ? tc_npad(s->tcw) * s->L * int64_t(sizeof(uint16_t)) : s->n * s->L * int64_t(sizeof(float));
+}
+
+size_t ckpt_bytes(const spca_session* s) {
+  const size_t n = size_t(s->n), L = size_t(s->L);
+  return sizeof(CkptHeader) + sizeof(double) * (n * L + L * L + n + L) + sizeof(float) * (n + 1) +
+         size_t(ckpt_omega_bytes(s));
+}
+}  // namespace
+
+spca_status spca_state_bytes(spca_session* s, size_t* bytes) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  if (!bytes) return fail(s, SPCA_E_INVALID, "bytes is NULL");
+  *bytes = ckpt_bytes(s);
+  return SPCA_OK;
+}
+
+spca_status spca_save_state(spca_session* s, void* buf, size_t bytes) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  if (!buf) return fail(s, SPCA_E_INVALID, "buf is NULL");
+  if (bytes < ckpt_bytes(s)) return fail(s, SPCA_E_INVALID, "buffer of %zu bytes < %zu", bytes, ckpt_bytes(s));
+  CU(cudaSetDevice(s->device));
+  st = flush_tc(s);
+  if (st != SPCA_OK) return st;
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kCkptMagic, sizeof(h.magic));
+  h.n = s->n; h.m = s->m; h.k = s->k; h.p = s->p; h.l = s->l; h.L = s->L;
+  h.math = s->opt.math; h.center = s->opt.center; h.seed = s->seed;
+  h.shift_set = s->shift_set; h.scale_set = s->scale_set; h.omega_orth = s->omega_orth;
+  h.omega_bytes = ckpt_omega_bytes(s);
+  char* out = static_cast<char*>(buf);
+  std::memcpy(out, &h, sizeof(h));
+  size_t off = sizeof(h);
+  const size_t n = size_t(s->n), L = size_t(s->L);
+  auto get = [&](const void* dev, size_t nb) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(out + off, dev, nb, cudaMemcpyDeviceToHost, s->stream);
+    off += nb;
+    return e;
+  };
+  CU(get(s->H, sizeof(double) * n * L));
+  CU(get(s->gram, sizeof(double) * L * L));
+  CU(get(s->colsum, sizeof(double) * n));
+  CU(get(s->sG, sizeof(double) * L));
+  CU(get(s->shift, sizeof(float) * n));
+  if (s->tc) {
+    CU(get(s->tcw.scale, sizeof(float)));
+  } else {
+    const float one = 1.0f;
+    std::memcpy(out + off, &one, sizeof(float));
+    off += sizeof(float);
+  }
+  if (h.omega_bytes > 0) CU(get(s->tc ? static_cast<const void*>(s->tcw.om16) : s->omega32, size_t(h.omega_bytes)));
+  CU(cudaStreamSynchronize(s->stream));
+  return SPCA_OK;
+}
+
+spca_status spca_load_state(spca_session* s, const void* buf, size_t bytes) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  if (!buf) return fail(s, SPCA_E_INVALID, "buf is NULL");
+  CkptHeader h;
+  if (bytes < sizeof(h)) return fail(s, SPCA_E_INVALID, "buffer shorter than a checkpoint header");
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, kCkptMagic, sizeof(h.magic)) != 0) return fail(s, SPCA_E_INVALID, "not a checkpoint");
+  if (h.n != s->n || h.k != s->k || h.p != s->p || h.L != s->L || h.math != s->opt.math ||
+      h.center != s->opt.center || h.seed != s->seed)
+    return fail(s, SPCA_E_INVALID, "checkpoint of another session (n, k, p, seed, math or centering differ)");
+  if (h.m < 0 || (h.omega_orth != 0 && h.omega_orth != 1)) return fail(s, SPCA_E_INVALID, "corrupt checkpoint header");
+  const bool orth = h.omega_orth != 0;
+  const int64_t ob = orth ? (s->tc ? tc_npad(s->tcw) * s->L * int64_t(sizeof(uint16_t))
+                                   : s->n * s->L * int64_t(sizeof(float)))
+                          : 0;
+  if (h.omega_bytes != ob) return fail(s, SPCA_E_INVALID, "corrupt checkpoint header");
+  const size_t n = size_t(s->n), L = size_t(s->L);
+  const size_t need = sizeof(h) + sizeof(double) * (n * L + L * L + n + L) + sizeof(float) * (n + 1) + size_t(ob);
+  if (bytes < need) return fail(s, SPCA_E_INVALID, "checkpoint of %zu bytes is truncated (%zu needed)", bytes, need);
+  CU(cudaSetDevice(s->device));
+  st = flush_tc(s);
+  if (st != SPCA_OK) return st;
+  s->pend.nseg = 0;
+  s->pend.rows_total = 0;
+  const char* in = static_cast<const char*>(buf);
+  size_t off = sizeof(h);
+  auto put = [&](void* dev, size_t nb) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(dev, in + off, nb, cudaMemcpyHostToDevice, s->stream);
+    off += nb;
+    return e;
+  };
+  CU(put(s->H, sizeof(double) * n * L));
+  CU(put(s->gram, sizeof(double) * L * L));
+  CU(put(s->colsum, sizeof(double) * n));
+  CU(put(s->sG, sizeof(double) * L));
+  CU(put(s->shift, sizeof(float) * n));
+  if (s->tc) CU(put(s->tcw.scale, sizeof(float)));
+  else off += sizeof(float);
+  if (orth) {
+    CU(put(s->tc ? static_cast<void*>(s->tcw.om16) : static_cast<void*>(s->omega32), size_t(ob)));
+  } else if (s->omega_orth) {   // back to the seed's Gaussian Omega
+    if (s->tc) CU(launch_omega_op(s->tcw.fmt, s->seed, s->n, tc_npad(s->tcw), s->l, s->L, s->tcw.om16, s->stream, &s->prof));
+    else CU(launch_omega_f32(s->seed, s->n, s->l, s->L, s->omega32, s->L, s->stream, &s->prof));
+  }
+  CU(cudaMemsetAsync(s->flags, 0, sizeof(int) * 4, s->stream));
+  CU(cudaStreamSynchronize(s->stream));
+  s->m = h.m;
+  s->shift_set = h.shift_set != 0;
+  s->scale_set = h.scale_set != 0;
+  s->omega_orth = orth;
+  s->u_ready = false;
+  return SPCA_OK;
+}
+
 spca_status spca_power_step(spca_session* s) {
   spca_status st = check_usable(s);
   if (st != SPCA_OK) return st;

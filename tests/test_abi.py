@@ -78,6 +78,9 @@ def test_null_session_calls_return_errors(lib):
     assert lib.spca_finalize(None, None, None, 0) == 1
     assert lib.spca_left_vectors(None, None, 1, None, 0) == 1
     assert lib.spca_power_step(None) == 1
+    assert lib.spca_state_bytes(None, None) == 1
+    assert lib.spca_save_state(None, None, 0) == 1
+    assert lib.spca_load_state(None, None, 0) == 1
     assert lib.spca_sync(None) == 1
     assert lib.spca_reset(None, 0) == 1
     assert lib.spca_merge(None, None) == 1

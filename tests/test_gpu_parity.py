@@ -290,6 +290,53 @@ def test_power_scheme_pass_matches_oracle(small):
     assert np.max(np.abs(sigma - exact) / exact) < np.max(np.abs(sigma0 - exact) / exact) / 2
 
 
+def test_checkpoint_resume_is_the_same_pass(small):
+    """A pass saved after some blocks and resumed in a new session (spca_save_state /
+    spca_load_state) gives bit for bit the result of one session, also across a power step;
+    a checkpoint of another session, or a truncated one, is refused."""
+    A = small["A"]
+    k, p, seed, mb = small["k"], small["p"], small["seed"], small["block_rows"]
+    m, n = A.shape
+    Ad = A.to(torch.float32).to(DEV)
+    cuts = list(range(0, m, mb))
+    half = cuts[len(cuts) // 2]
+
+    def feed(s, a, b):
+        for r0 in range(a, b, mb):
+            s.update(Ad[r0:min(b, r0 + mb)])
+
+    with spca.Session(n, k, p, seed) as one:
+        feed(one, 0, m)
+        s_one, V_one = one.finalize()
+        one.power_step()
+        feed(one, 0, m)
+        s_pow, V_pow = one.finalize()
+    with spca.Session(n, k, p, seed) as a:
+        feed(a, 0, half)
+        ck1 = a.save_state()
+        feed(a, half, m)
+        a.power_step()
+        feed(a, 0, half)
+        ck2 = a.save_state()
+    with spca.Session(n, k, p, seed) as b:
+        b.load_state(ck1)
+        assert b.rows_seen == half
+        feed(b, half, m)
+        s_b, V_b = b.finalize()
+        b.load_state(ck2)
+        feed(b, half, m)
+        s_b2, V_b2 = b.finalize()
+        with pytest.raises(spca.SpcaError) as ei:
+            b.load_state(ck1[:len(ck1) - 8])
+        assert ei.value.status == 1
+    assert np.array_equal(s_b, s_one) and np.array_equal(V_b, V_one)
+    assert np.array_equal(s_b2, s_pow) and np.array_equal(V_b2, V_pow)
+    with spca.Session(n, k, p, seed + 1) as c:
+        with pytest.raises(spca.SpcaError) as ei:
+            c.load_state(ck1)
+        assert ei.value.status == 1
+
+
 def test_non_finite_input_is_reported():
     A = torch.randn(64, 40, device=DEV)
     A[5, 7] = float("nan")

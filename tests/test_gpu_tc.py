@@ -197,6 +197,35 @@ def test_tc_left_vectors_from_kept_sketch_rows(math):
 
 
 @pytest.mark.parametrize("math", TC_MATHS)
+def test_tc_checkpoint_resume(math):
+    """Save after half of the blocks, resume in a new session: the result of one session
+    whose pending blocks were launched at the same point (the FP16 operand scale travels
+    with the checkpoint)."""
+    A = synth.low_rank_plus_noise(3000, 700, synth.spectrum("dec20", 80), noise_std=1e-4, mean_std=0.5, seed=43,
+                                  device=DEV, dtype=torch.float32)
+    torch.cuda.synchronize()
+    k, p = 20, 10
+    with spca.Session(700, k, p, 79, math=math) as one:
+        for r0 in range(0, 1536, 512):
+            one.update(A[r0:r0 + 512])
+        one.sync()
+        for r0 in range(1536, 3000, 512):
+            one.update(A[r0:r0 + 512])
+        s_one, V_one = one.finalize()
+    with spca.Session(700, k, p, 79, math=math) as a:
+        for r0 in range(0, 1536, 512):
+            a.update(A[r0:r0 + 512])
+        ck = a.save_state()
+    with spca.Session(700, k, p, 79, math=math) as b:
+        b.load_state(ck)
+        for r0 in range(1536, 3000, 512):
+            b.update(A[r0:r0 + 512])
+        s_b, V_b = b.finalize()
+    assert np.allclose(s_b, s_one, rtol=1e-6, atol=0)
+    assert O.max_principal_sine(V_b[:, :10], V_one[:, :10]) <= 1e-5
+
+
+@pytest.mark.parametrize("math", TC_MATHS)
 def test_tc_power_scheme_pass(math):
     """The power step on the tensor-core forms: Omega <- orth(H_bar) in the operand format,
     one more pass, against the oracle's twice-run while loop with Omega in that format."""
