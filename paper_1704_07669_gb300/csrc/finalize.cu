@@ -1368,18 +1368,18 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
 // ------------------------------------------------------------------ the power scheme (P = 1)
 
 // T = the l x l identity (zero elsewhere in L x L); info[0] = l (all output columns of
-// bt_and_c), info[3] = 0 (no failed factorisation yet).
+// bt_and_c), info[6] = 0 (no failed factorisation yet).
 __global__ void eye_kernel(double* __restrict__ T, int l, int L, int* __restrict__ info) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < L * L; e += gridDim.x * blockDim.x)
     T[e] = (e / L == e % L && e / L < l) ? 1.0 : 0.0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     info[0] = l;
-    info[3] = 0;
+    info[6] = 0;
   }
 }
 
 // One block: C = L1 L1^T (FP64 Cholesky, in place) and T = L1^-1, so that Q = Y T^T has
-// orthonormal columns when C = Y^T Y. A pivot at or below l eps max_i C_ii sets info[3].
+// orthonormal columns when C = Y^T Y. A pivot at or below l eps max_i C_ii sets info[6].
 __global__ void chol_tinv64_kernel(double* __restrict__ C, int l, int L, double* __restrict__ T, int* __restrict__ info) {
   __shared__ double tol;
   if (threadIdx.x == 0) {
@@ -1390,7 +1390,7 @@ __global__ void chol_tinv64_kernel(double* __restrict__ C, int l, int L, double*
   __syncthreads();
   const bool ok = blk_cholesky(C, l, L, tol);
   if (!ok) {
-    if (threadIdx.x == 0) info[3] = 1;
+    if (threadIdx.x == 0) info[6] = 1;
     return;
   }
   for (int e = threadIdx.x; e < L * L; e += blockDim.x) T[e] = 0.0;

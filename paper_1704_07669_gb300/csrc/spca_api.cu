@@ -778,7 +778,7 @@ spca_status spca_power_step(spca_session* s) {
   if (st != SPCA_OK) return st;
   const double* Q = nullptr;
   CU(power_omega_run(s->state(), s->fin, s->opt.center ? s->m : 0, s->stream, &Q));
-  CU(cudaMemcpyAsync(s->host_flags, s->fin.info + 3, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CU(cudaMemcpyAsync(s->host_flags, s->fin.info + 6, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CU(cudaStreamSynchronize(s->stream));
   if (s->host_flags[0] != 0)
     return fail(s, SPCA_E_NUMERIC, "H is numerically rank deficient: no orthonormal basis of rank l for the power step");

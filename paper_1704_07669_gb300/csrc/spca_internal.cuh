@@ -161,7 +161,7 @@ struct FinalWork {
   double* Tu;         // L x L: T (= R^-T) of the last finalize
   double* M;          // l x k: sketch rows to left singular vectors (after a finalize)
   double* mrow;       // k: the centring term of that map
-  int* info;          // [0]: rank kept, [1]: route (0 chol, 1 eigen), [2]: jacobi sweeps
+  int* info;          // [0]: rank kept, [1]: route (0 chol, 1 eigen), [2]-[4]: solver sweeps, [6]: power step failed
   int nparts;
 };
 
@@ -174,7 +174,7 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k,
 cudaError_t centered_state(const State& s, const FinalWork& f, int64_t m, cudaStream_t st);
 
 // the power scheme with P = 1: Q = orth(H_bar) (n x L FP64, in FinalWork scratch) by Cholesky
-// QR twice; f.info[3] != 0 afterwards if H_bar was numerically rank deficient
+// QR twice; f.info[6] != 0 afterwards if H_bar was numerically rank deficient
 cudaError_t power_omega_run(const State& s, const FinalWork& f, int64_t m, cudaStream_t st, const double** Q);
 
 // the l x k map to U (and its centring term) from the last finalize's R^-T, eigenvectors and
