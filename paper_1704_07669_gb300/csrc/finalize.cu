@@ -1251,8 +1251,9 @@ cudaError_t centered_state(const State& s, const FinalWork& f, int64_t m, cudaSt
 
 // The dynamic shared memory limits of the one-block dense kernels, set once per process.
 void set_dense_attrs() {
-  static bool attr_done = false;
-  if (!attr_done) {
+  static std::atomic<uint64_t> done{0};
+  static std::mutex mu;
+  once_per_device(done, mu, [] {
     cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kMaxDenseSmem));
     cudaFuncSetAttribute(chol_inv_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(kMaxDenseSmem));
@@ -1267,8 +1268,8 @@ void set_dense_attrs() {
                          static_cast<int>(kMaxDenseSmem));
     cudaFuncSetAttribute(form_v_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(kMaxDenseSmem));
-    attr_done = true;
-  }
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, double* sigma_dev, double* V_dev,

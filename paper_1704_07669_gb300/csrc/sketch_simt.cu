@@ -811,17 +811,20 @@ cudaError_t simt_pass_t(const State& s, const SimtWork& w, const T* rows, float 
   // FP32 rows that allow 16-byte copies take the kernels with cp.async rings
   bool use_cp = false;
   if constexpr (std::is_same<T, float>::value) use_cp = vec_ok && (s.n % 4 == 0);
-  static bool g_attr = false;
-  if (!g_attr) {
-    cudaError_t e = allow_smem(g_partial_kernel<T>, kSmemG);
-    if (e != cudaSuccess) return e;
-    if constexpr (std::is_same<T, float>::value) {
-      e = allow_smem(g_partial_cp_kernel, kSmemGcp);
+  static std::atomic<uint64_t> g_attr{0};
+  static std::mutex g_mu;
+  {
+    const cudaError_t ea = once_per_device(g_attr, g_mu, [] {
+      cudaError_t e = allow_smem(g_partial_kernel<T>, kSmemG);
       if (e != cudaSuccess) return e;
-      e = allow_smem(h_partial_cp_kernel, kSmemHcp);
-      if (e != cudaSuccess) return e;
-    }
-    g_attr = true;
+      if constexpr (std::is_same<T, float>::value) {
+        e = allow_smem(g_partial_cp_kernel, kSmemGcp);
+        if (e != cudaSuccess) return e;
+        e = allow_smem(h_partial_cp_kernel, kSmemHcp);
+      }
+      return e;
+    });
+    if (ea != cudaSuccess) return ea;
   }
   prof->begin(SPCA_K_G_PARTIAL, st);
   if constexpr (std::is_same<T, float>::value) {
@@ -851,11 +854,11 @@ cudaError_t simt_pass_t(const State& s, const SimtWork& w, const T* rows, float 
   if (T_ < 1) T_ = 1;
   const int64_t rslice = ((rchunks + T_ - 1) / T_) * BK;
   T_ = static_cast<int>((m + rslice - 1) / rslice);
-  static bool h_attr = false;
-  if (!h_attr) {
-    cudaError_t e = allow_smem(h_partial_kernel<T>, kSmemH);
-    if (e != cudaSuccess) return e;
-    h_attr = true;
+  static std::atomic<uint64_t> h_attr{0};
+  static std::mutex h_mu;
+  {
+    const cudaError_t ea = once_per_device(h_attr, h_mu, [] { return allow_smem(h_partial_kernel<T>, kSmemH); });
+    if (ea != cudaSuccess) return ea;
   }
   prof->begin(SPCA_K_H_PARTIAL, st);
   if constexpr (std::is_same<T, float>::value) {

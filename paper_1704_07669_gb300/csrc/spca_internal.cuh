@@ -6,9 +6,28 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "spca.h"
 
 namespace spca {
+
+// Runs f once per device (kernel attributes are per device), from any number of host
+// threads: done holds one bit per device that has been set up (devices 0..63).
+template <class F>
+cudaError_t once_per_device(std::atomic<uint64_t>& done, std::mutex& mu, F f) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev >= 0 && dev < 64 ? (uint64_t(1) << dev) : 0;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(mu);
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = f();
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 constexpr int kMaxL = 256;          // largest l accepted
 constexpr int kDefaultBlockRows = 8192;
