@@ -262,18 +262,24 @@ def run_form(spca, math_name, A, seed, stream, steps_arg, warmup, ws):
     spca.spca_set_profiling(sess.handle, True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]   # per-pass times
     barrier(ws)
     torch.cuda.synchronize()
     ev0.record(stream)
-    for _ in range(steps):
+    marks[0].record(stream)
+    for i in range(steps):
         step()
+        marks[i + 1].record(stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
     spca.spca_set_profiling(sess.handle, False)
     ms = max_over_ranks(ev0.elapsed_time(ev1), ws)
+    per_pass = np.array([marks[i].elapsed_time(marks[i + 1]) for i in range(steps)])
     prof = sess.profile()
-    return sess, step, {"ms": ms, "steps": steps, "prof": prof, "sigma": sigma_d.cpu().numpy()}
+    return sess, step, {"ms": ms, "steps": steps, "prof": prof, "sigma": sigma_d.cpu().numpy(),
+                        "pass_ms_p50": float(np.percentile(per_pass, 50)),
+                        "pass_ms_p99": float(np.percentile(per_pass, 99))}
 
 
 SERVING = "64 sessions, n log-uniform in [512, 32768], l in {20, 40, 80, 140} (k = l - 10), FP32 row blocks " \
@@ -455,6 +461,8 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks.summary(), "kernels": kernels, "forms": forms, "serving": serving,
+            "pass_ms": {"p50": res["pass_ms_p50"], "p99": res["pass_ms_p99"],
+                        "note": "per-pass times of the timed passes (CUDA events on the session stream)"},
             "peaks_source": pk["source"],
             "tflops": 4.0 * m * N * (K + P) * steps * ws / (ms * 1e-3) / 1e12}
     print(json.dumps(line), flush=True)
