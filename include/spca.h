@@ -114,7 +114,10 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed,
  *                   (host pointer); ignored otherwise (may be NULL)
  *   rows_on_device  1: rows is a device pointer, read in place on the session
  *                   stream (the caller keeps it valid and unmodified until the
- *                   stream has passed this work, e.g. until spca_sync);
+ *                   stream has passed this work, e.g. until spca_sync). The rows
+ *                   must be ready when the call is made: a stream the library
+ *                   created is not ordered after the caller's streams (give the
+ *                   caller's stream in the options, or synchronise first);
  *                   0: rows is host memory, copied through the session's pinned
  *                   staging buffers; the call returns once the copy of the last
  *                   piece has been issued and the caller's buffer is no longer
