@@ -25,6 +25,13 @@ Readings where the paper is silent (each one is also listed in the design notes)
 * signs and order: singular values descending; each right singular vector is
   scaled by +-1 so that its entry of largest magnitude (lowest index on ties) is
   positive.
+* power scheme (Sec. 3.2, Sec. 4): "orth" is the Q factor of the QR of H; the
+  new Omega is, like the Gaussian one, defined as its value in the operand
+  format (``power_omega``). Only range(Omega) matters to the result, so any
+  orthonormal basis of H gives the same sigma and V.
+* streams too large to hold in FP64 are fed block by block (``ShiftedPass``);
+  a block repeated in a stream may be folded in once with its multiplicity,
+  the same sum as Eq. 11 over the stream.
 """
 import numpy as np
 import scipy.linalg as sla
