@@ -305,8 +305,8 @@ spca_status spca_omega_words(uint64_t seed, int64_t n, int32_t l, uint32_t* out)
 spca_status spca_omega(uint64_t seed, int64_t n, int32_t l, float* out);
 
 /*
- * spca_shift_static - the centering shift c of Sec. 2.1 exactly as a session
- * computes it from its first rows (FP32 of the FP64 column means of `rows`),
+ * spca_shift_static - the centering shift c exactly as a session computes it
+ * from its first rows (FP32 of the FP64 column means of `rows`),
  * without allocating anything. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory at that moment, such
  * as a serving loop that has committed its device memory to admitted sessions,

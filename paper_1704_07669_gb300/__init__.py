@@ -287,13 +287,26 @@ def spca_omega(seed, n, l, out):
 
 
 def spca_shift_static(rows, shift, block_scale=None, stream=None):
-    """The allocation-free shift: shift[:] = FP32 of the FP64 column means of the
+    """The allocation-free shift: shift[:n] = FP32 of the FP64 column means of the
     2-D device tensor ``rows`` (row stride = leading dimension), enqueued on
-    ``stream`` (a torch.cuda.Stream, a raw handle, or None for the default)."""
+    ``stream`` (a torch.cuda.Stream or a raw handle; None: torch's current stream
+    on the rows' device, so that the launch is ordered after the work that made
+    ``rows``)."""
+    if rows.dim() != 2 or not rows.is_cuda:
+        raise ValueError("rows must be a 2-D CUDA tensor")
     m, n = rows.shape
+    if rows.stride(1) != 1:
+        raise ValueError("rows must be row-major with unit column stride")
+    if not (getattr(shift, "is_cuda", False) and str(shift.dtype).endswith("float32")
+            and shift.is_contiguous() and shift.numel() >= n and shift.device == rows.device):
+        raise ValueError("shift must be a contiguous float32 CUDA tensor of at least n elements on the rows' device")
     scale = None if block_scale is None else ctypes.c_float(float(block_scale))
     bs = None if scale is None else ctypes.cast(ctypes.byref(scale), ctypes.c_void_p)
-    st = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    if stream is None:
+        import torch
+        st = torch.cuda.current_stream(rows.device).cuda_stream
+    else:
+        st = int(getattr(stream, "cuda_stream", stream))
     _check(lib().spca_shift_static(_ptr(rows)[0], int(m), int(n), int(rows.stride(0)), _dtype_code(rows), bs,
                                    _ptr(shift)[0], st))
 

@@ -73,3 +73,16 @@ def test_rejects_sizes_beyond_the_fixed_scratch():
         spca.spca_shift_static(A, out)
     assert ei.value.status == 1
     assert "exceeds the fixed scratch" in str(ei.value)
+
+
+def test_binding_rejects_views_and_outputs_it_cannot_pass():
+    A = _rows(64, 48, seed=9)
+    out = torch.zeros(48, device=DEV)
+    with pytest.raises(ValueError):
+        spca.spca_shift_static(A.t(), torch.zeros(64, device=DEV))   # column-strided view
+    with pytest.raises(ValueError):
+        spca.spca_shift_static(A, out[:40])                           # shift shorter than n
+    with pytest.raises(ValueError):
+        spca.spca_shift_static(A, out.double())                       # wrong dtype
+    with pytest.raises(ValueError):
+        spca.spca_shift_static(A.cpu(), out)                          # host rows
