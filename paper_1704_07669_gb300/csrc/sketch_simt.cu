@@ -197,10 +197,19 @@ __global__ void shift_partial_kernel(const T* __restrict__ rows, int64_t m, int6
     // (Knuth's two-sum keeps each add's rounding error, about 48 significant bits in all)
     float hi = 0.f, lo = 0.f;
     for (int64_t i = r0; i < r1; ++i) {
-      const float x = Elem<T>::get(rows, i * ld + j, scale);
+      float x, xe = 0.f;
+      if constexpr (std::is_same<T, __nv_fp8_e4m3>::value) {
+        // the stored value code * scale exactly, as a pair (two-product): the mean is of the
+        // rows as stored, not of their FP32 roundings
+        const float code = static_cast<float>(rows[i * ld + j]);
+        x = code * scale;
+        xe = fmaf(code, scale, -x);
+      } else {
+        x = Elem<T>::get(rows, i * ld + j, scale);
+      }
       const float s = hi + x;
       const float bb = s - hi;
-      lo += (hi - (s - bb)) + (x - bb);
+      lo += (hi - (s - bb)) + (x - bb) + xe;
       hi = s;
     }
     part[blockIdx.y * n + j] = static_cast<double>(hi) + static_cast<double>(lo);

@@ -841,6 +841,8 @@ __global__ void __launch_bounds__(T3_NT, 1) sketch_tc3_kernel(const __grid_const
   cluster_sync();   // no CTA leaves while a peer may still read its shared memory
 }
 
+}  // namespace
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   // looked up once per process (a function-local static is initialised by one thread)
@@ -855,6 +857,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   }();
   return fn;
 }
+
+namespace {
 
 thread_local char g_tc3_reason[192] = "";
 

@@ -31,9 +31,40 @@ size_t dtype_size(int dtype) {
 
 // features covered by the pre-swizzled Omega: the larger padding of the two kernels
 int64_t tc_npad(const TcWork& t) {
-  const int64_t a = static_cast<int64_t>(t.cfg.CS) * t.cfg.w;
+  const int64_t a = t.cfg_ok ? static_cast<int64_t>(t.cfg.CS) * t.cfg.w : 0;
   const int64_t b = t.v3 ? static_cast<int64_t>(t.cfg3.CS) * t.cfg3.w : 0;
-  return a > b ? a : b;
+  const int64_t c = t.use_grp ? static_cast<int64_t>(t.grp.nbt) * 64 : 0;
+  const int64_t ab = a > b ? a : b;
+  return ab > c ? ab : c;
+}
+
+// Configurations of the tensor-core kernels for (n, l, L) and the sizes (elements) of their
+// buffers; false when no kernel takes the shape.
+struct TcSizes {
+  int64_t npad, hpart, nctas, img, part, gbuf, cnt;
+};
+bool tc_setup(int64_t n, int l, int L, int fmt, TcWork* t, TcSizes* z) {
+  t->cfg_ok = tc_config(n, L, fmt, &t->cfg);
+  t->v3 = t->cfg_ok && tc3_config(n, L, fmt, &t->cfg3);
+  t->use_grp = spca::grp_config(n, l, L, fmt, &t->grp);
+  if (!t->cfg_ok && !t->use_grp) return false;
+  z->npad = tc_npad(*t);
+  const int64_t hp = t->cfg_ok ? int64_t(t->cfg.nclusters) * t->cfg.CS * t->cfg.w : 0;
+  const int64_t hp3 = t->v3 ? int64_t(t->cfg3.nclusters) * t->cfg3.CS * t->cfg3.w : 0;
+  const int64_t hpg = t->use_grp ? int64_t(t->grp.NG) * t->grp.nbt * 64 : 0;
+  z->hpart = hp > hp3 ? hp : hp3;
+  if (hpg > z->hpart) z->hpart = hpg;
+  int64_t nc = t->cfg_ok ? int64_t(t->cfg.nclusters) * t->cfg.CS : 0;
+  if (t->v3 && int64_t(t->cfg3.nclusters) * t->cfg3.CS > nc) nc = int64_t(t->cfg3.nclusters) * t->cfg3.CS;
+  if (t->use_grp && int64_t(t->grp.NG) * t->grp.S > nc) nc = int64_t(t->grp.NG) * t->grp.S;
+  z->nctas = nc;
+  const int64_t img3 = t->v3 ? hp3 * 256 : 0;
+  const int64_t imgg = t->use_grp ? static_cast<int64_t>(spca::grp_img_elems(t->grp)) : 0;
+  z->img = img3 > imgg ? img3 : imgg;
+  z->part = t->use_grp ? static_cast<int64_t>(spca::grp_part_elems(t->grp, L)) : 0;
+  z->gbuf = t->use_grp ? static_cast<int64_t>(spca::grp_gbuf_elems(t->grp, L, fmt)) : 0;
+  z->cnt = t->use_grp ? static_cast<int64_t>(spca::grp_cnt_elems(t->grp)) : 0;
+  return true;
 }
 
 }  // namespace
@@ -174,7 +205,7 @@ void free_all(spca_session* s) {
                   s->fin.sig, s->fin.info, s->fin.flip, s->fin.Tu, s->fin.M, s->fin.mrow, s->fin_sigma, s->fin_V,
                   s->dstage[0], s->dstage[1],
                   s->tcw.om16, s->tcw.Hpart, s->tcw.gram_part, s->tcw.sG_part, s->tcw.scale, s->tcw.scale_bits,
-                  s->tcw.img};
+                  s->tcw.img, s->tcw.zero8k, s->tcw.part, s->tcw.gbuf, s->tcw.cnt};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < 2; ++i) {
@@ -198,8 +229,19 @@ spca_status check_usable(spca_session* s) {
 spca_status flush_tc(spca_session* s) {
   if (!s->tc || s->pend.nseg == 0) return SPCA_OK;
   bool used = false;
-  if (s->tcw.v3) CU(tc3_pass(s->state(), s->tcw, s->pend, s->stream, &s->prof, &used));
-  if (!used) CU(tc_pass(s->state(), s->tcw, s->pend, s->stream, &s->prof));
+  if (s->tcw.use_grp) CU(grp_pass(s->state(), s->tcw, s->pend, s->stream, &s->prof, &used));
+  if (!used && s->tcw.v3) CU(tc3_pass(s->state(), s->tcw, s->pend, s->stream, &s->prof, &used));
+  if (!used) {
+    if (!s->tcw.cfg_ok) {
+      s->pend.nseg = 0;
+      s->pend.rows_total = 0;
+      return fail(s, SPCA_E_UNSUPPORTED,
+                  "the tensor-core pass at n = %lld, l = %d reads rows through tensor maps only: row blocks "
+                  "must start 16-byte aligned with a leading dimension that is a multiple of 4",
+                  (long long)s->n, s->l);
+    }
+    CU(tc_pass(s->state(), s->tcw, s->pend, s->stream, &s->prof));
+  }
   s->pend.nseg = 0;
   s->pend.rows_total = 0;
   return SPCA_OK;
@@ -249,8 +291,9 @@ size_t session_footprint(int64_t n, int k, int p, int math, int64_t max_block_ro
   const int l = k + p;
   const bool tc = (math == SPCA_MATH_BF16 || math == SPCA_MATH_FP16);
   const int L = tc ? pad_l(l + 1) : pad_l(l);
-  TcConfig cfg{};
-  if (tc && !tc_config(n, L, math == SPCA_MATH_FP16 ? 1 : 0, &cfg)) return 0;
+  TcWork t{};
+  TcSizes z{};
+  if (tc && !tc_setup(n, l, L, math == SPCA_MATH_FP16 ? 1 : 0, &t, &z)) return 0;
   const int64_t mb = max_block_rows > 0 ? max_block_rows : kDefaultBlockRows;
   size_t b = 0;
   auto add = [&](int64_t count, size_t es) {
@@ -267,17 +310,10 @@ size_t session_footprint(int64_t n, int k, int p, int math, int64_t max_block_ro
     const int64_t groups = (mb + 31) / 32;
     add(gp_rows * L, 4); add(mb * L, 4); add(groups * L * L, 8); add(groups * L, 8); add(T * n * L, 4); add(T * n, 4);
   } else {
-    TcWork t{};
-    t.cfg = cfg;
-    t.v3 = tc3_config(n, L, math == SPCA_MATH_FP16 ? 1 : 0, &t.cfg3);
-    const int64_t npad = tc_npad(t);
-    const int64_t hp = int64_t(cfg.nclusters) * cfg.CS * cfg.w;
-    const int64_t hp3 = t.v3 ? int64_t(t.cfg3.nclusters) * t.cfg3.CS * t.cfg3.w : 0;
-    int64_t nctas = int64_t(cfg.nclusters) * cfg.CS;
-    if (t.v3 && int64_t(t.cfg3.nclusters) * t.cfg3.CS > nctas) nctas = int64_t(t.cfg3.nclusters) * t.cfg3.CS;
-    add(npad * L, 2); add(1, 4); add(1, 4); add((hp > hp3 ? hp : hp3) * L, 4); add(nctas * L * L, 8);
-    add(nctas * L, 8);
-    if (t.v3) add(hp3 * 256, 2);
+    add(z.npad * L, 2); add(1, 4); add(1, 4); add(z.hpart * L, 4); add(z.nctas * L * L, 8);
+    add(z.nctas * L, 8);
+    if (z.img) add(z.img, 2);
+    if (t.use_grp) { add(4096, 2); add(z.part, 4); add(z.gbuf, 2); add(z.cnt, 4); }
   }
   add(int64_t(kShiftParts) * n, 8);
   const int64_t per = int64_t(L) * L * 8;
@@ -315,6 +351,8 @@ spca_status session_finalize_async(spca_session* s, double* sigma_dev, double* V
 }
 
 spca_status session_flags_status(spca_session* s, int flags) {
+  if (flags & 16)
+    return fail(s, SPCA_E_CUDA, "the grouped tensor-core kernel was launched with a configuration it does not take");
   if (flags & 8) return fail(s, SPCA_E_CUDA, "a copy of the tensor-core pass was out of its buffer (skipped)");
   if (flags & 2) return fail(s, SPCA_E_TIMEOUT, "a bounded device wait gave up during the pass");
   if (flags & 1) return fail(s, SPCA_E_NUMERIC, "non-finite values (NaN/Inf) reached the sketch");
@@ -355,13 +393,13 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   const bool tc_math = (o.math == SPCA_MATH_BF16 || o.math == SPCA_MATH_FP16);
   if (o.math != SPCA_MATH_FP32 && !tc_math)
     return fail(nullptr, SPCA_E_UNSUPPORTED, "math form %d is not available in this build", o.math);
-  TcConfig tcfg{};
+  TcWork tcw0{};
+  TcSizes tcz{};
   // the tensor-core pass keeps one spare column (index l) for the column sums
   const int L_tc = pad_l(static_cast<int>(l) + 1);
-  if (tc_math && !tc_config(n, L_tc, o.math == SPCA_MATH_FP16 ? 1 : 0, &tcfg))
-    return fail(nullptr, SPCA_E_UNSUPPORTED,
-                "the tensor-core pass needs l <= 63 and n <= 16 x 640 on a device with 16-CTA clusters "
-                "(n=%lld, l=%lld): %s", (long long)n, (long long)l, tc_config_reason());
+  if (tc_math && !tc_setup(n, static_cast<int>(l), L_tc, o.math == SPCA_MATH_FP16 ? 1 : 0, &tcw0, &tcz))
+    return fail(nullptr, SPCA_E_UNSUPPORTED, "no tensor-core kernel takes n=%lld, l=%lld: %s; %s", (long long)n,
+                (long long)l, grp_config_reason(), tc_config_reason());
 
   s = new (std::nothrow) spca_session();
   if (!s) return fail(nullptr, SPCA_E_NOMEM, "host allocation failed");
@@ -419,21 +457,23 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
     CC(dalloc(&w.cs_part, size_t(w.T) * n));
   } else {
     TcWork& t = s->tcw;
-    t.cfg = tcfg;
-    // the pipelined kernel where it fits (its partials and Omega padding may differ in size)
-    t.v3 = tc3_config(n, L, s->tcw.fmt, &t.cfg3);
-    const int64_t npad = tc_npad(t);
-    const int64_t hp = static_cast<int64_t>(tcfg.nclusters) * tcfg.CS * tcfg.w;
-    const int64_t hp3 = t.v3 ? static_cast<int64_t>(t.cfg3.nclusters) * t.cfg3.CS * t.cfg3.w : 0;
-    int64_t nctas = static_cast<int64_t>(tcfg.nclusters) * tcfg.CS;
-    if (t.v3 && int64_t(t.cfg3.nclusters) * t.cfg3.CS > nctas) nctas = int64_t(t.cfg3.nclusters) * t.cfg3.CS;
-    CC(dalloc(&t.om16, size_t(npad) * L));
+    const int fmt = t.fmt;
+    t = tcw0;   // the configurations (the grouped kernel preferred, the others as fallbacks)
+    t.fmt = fmt;
+    CC(dalloc(&t.om16, size_t(tcz.npad) * L));
     CC(dalloc(&t.scale, 1));
     CC(dalloc(&t.scale_bits, 1));
-    CC(dalloc(&t.Hpart, size_t(hp > hp3 ? hp : hp3) * L));
-    CC(dalloc(&t.gram_part, size_t(nctas) * L * L));
-    CC(dalloc(&t.sG_part, size_t(nctas) * L));
-    if (t.v3) CC(dalloc(&t.img, size_t(hp3) * 256));
+    CC(dalloc(&t.Hpart, size_t(tcz.hpart) * L));
+    CC(dalloc(&t.gram_part, size_t(tcz.nctas) * L * L));
+    CC(dalloc(&t.sG_part, size_t(tcz.nctas) * L));
+    if (tcz.img) CC(dalloc(&t.img, size_t(tcz.img)));
+    if (t.use_grp) {
+      CC(dalloc(&t.zero8k, 4096));
+      CC(cudaMemsetAsync(t.zero8k, 0, 8192, s->stream));
+      CC(dalloc(&t.part, size_t(tcz.part)));
+      CC(dalloc(&t.gbuf, size_t(tcz.gbuf)));
+      CC(dalloc(&t.cnt, size_t(tcz.cnt)));
+    }
   }
   CC(dalloc(&s->shift_part, size_t(kShiftParts) * n));
 
@@ -595,6 +635,8 @@ spca_status spca_finalize(spca_session* s, double* sigma, double* V, int32_t out
   // the non-finite flag is read after the finalisation kernels so that the stream never idles mid-call
   CU(cudaMemcpyAsync(s->host_flags, s->flags, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CU(cudaStreamSynchronize(s->stream));
+  if (s->host_flags[0] & 16)
+    return fail(s, SPCA_E_CUDA, "the grouped tensor-core kernel was launched with a configuration it does not take");
   if (s->host_flags[0] & 8) return fail(s, SPCA_E_CUDA, "a copy of the tensor-core pass was out of its buffer (skipped)");
   if (s->host_flags[0] & 2) return fail(s, SPCA_E_TIMEOUT, "a bounded device wait gave up during the pass");
   if (s->host_flags[0] & 1) return fail(s, SPCA_E_NUMERIC, "non-finite values (NaN/Inf) reached the sketch");
@@ -952,7 +994,14 @@ int64_t spca_rows_seen(const spca_session* s) { return s ? s->m : -1; }
 
 const char* spca_describe(spca_session* s) {
   if (!s) return "";
-  if (s->tc) {
+  if (s->tc && s->tcw.use_grp) {
+    const GrpConfig& g = s->tcw.grp;
+    snprintf(s->desc, sizeof(s->desc),
+             "math=%s kernel=grouped n=%lld l=%d L=%d group=%d groups=%d ctas=%d blocks_per_cta=%d mtiles=%d "
+             "stages=%d d1=%d fresh_h=%d smem=%u",
+             s->tcw.fmt == 1 ? "fp16" : "bf16", (long long)s->n, s->l, s->L, g.S, g.NG, g.S * g.NG, g.nbmax, g.nu,
+             g.ns1, g.nd1, g.nf, g.smem);
+  } else if (s->tc) {
     snprintf(s->desc, sizeof(s->desc),
              "math=%s kernel=%s n=%lld l=%d L=%d cluster=%d w=%d clusters=%d ctas=%d smem=%u",
              s->tcw.fmt == 1 ? "fp16" : "bf16", s->tcw.v3 ? "pipelined" : "resident", (long long)s->n, s->l, s->L,

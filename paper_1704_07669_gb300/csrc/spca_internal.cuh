@@ -117,10 +117,25 @@ struct TcConfig {
   uint32_t smem;      // dynamic shared memory per CTA
 };
 
+// the grouped kernel (sketch_grp.cu): NG groups of S CTAs; per CTA at most nbmax 64-feature
+// blocks (nu 128-feature M-tiles of H), ns1 FP32 stages, nd1 D1 buffers; nf: per-tile fresh H
+// buffers (1 or 2) added into a running H in TMEM (0: H drains to the partials every few tiles)
+struct GrpConfig {
+  int S, NG, nbt, nbmax, nu, ns1, nd1, nf;
+  uint32_t smem;
+};
+
 struct TcWork {
-  TcConfig cfg;          // the kernel holding each tile's operand (sketch_tc.cu)
+  TcConfig cfg;          // the kernel holding each tile's operand (sketch_tc.cu); valid when cfg_ok
+  bool cfg_ok;
   TcConfig cfg3;         // the pipelined kernel (sketch_tc3.cu), used when v3 is set
   bool v3;
+  GrpConfig grp;         // the grouped kernel (sketch_grp.cu), preferred when use_grp is set
+  bool use_grp;
+  uint16_t* zero8k;      // grouped kernel: 8 KB of zeros
+  float* part;           // grouped kernel: the groups' partial rings
+  uint16_t* gbuf;        // grouped kernel: the groups' G' rings
+  unsigned* cnt;         // grouped kernel: the groups' counters
   int fmt;               // 0: BF16 operands; 1: FP16 operands on values scaled by *scale
   float* scale;          // device scalar: power-of-two operand scale (FP16 form)
   unsigned int* scale_bits;   // device scratch for the largest row norm
@@ -159,6 +174,16 @@ cudaError_t launch_tc_finish(const State& s, const TcWork& w, int ncl, int64_t n
 // the pipelined kernel: configuration, and one pass (sets *used = false, launching nothing,
 // when a row block cannot be read through a tensor map)
 bool tc3_config(int64_t n, int L, int fmt, TcConfig* cfg);
+// the grouped kernel: configuration for (n, l, L), its buffer sizes (elements), and one pass
+// (sets *used = false, launching nothing, when a row block cannot be read through a tensor map)
+bool grp_config(int64_t n, int l, int L, int fmt, GrpConfig* cfg);
+const char* grp_config_reason();
+size_t grp_img_elems(const GrpConfig& c);
+size_t grp_part_elems(const GrpConfig& c, int L);
+size_t grp_gbuf_elems(const GrpConfig& c, int L, int fmt);
+size_t grp_cnt_elems(const GrpConfig& c);
+cudaError_t grp_pass(const State& s, const TcWork& w, const TcPending& pend, cudaStream_t st, Prof* prof,
+                     bool* used);
 const char* tc3_config_reason();
 cudaError_t tc3_pass(const State& s, const TcWork& w, const TcPending& pend, cudaStream_t st, Prof* prof,
                      bool* used);

@@ -49,14 +49,20 @@ def alone(A, k, p, seed, blocks, math):
         return s.finalize()
 
 
-# (n, k, p): the first ones fit the fused tensor-core kernel (FP16 form), the last ones do not
-# (l > 63 or n > 10240) and are served by the FP32 path
+# (n, k, p): the first ones fit a tensor-core kernel (FP16 form, including n = 12000 on the
+# grouped kernel), the ones with l > 63 do not and are served by the FP32 path
 MIX = [(300, 8, 8), (700, 10, 10), (1500, 20, 20), (3000, 30, 10), (6000, 50, 10), (9000, 40, 20),
        (900, 70, 10), (12000, 20, 10), (2500, 100, 20)]
 
 
 def expected_math(n, k, p):
-    return "fp16" if k + p + 1 <= 64 and n <= 10240 else "fp32"
+    """The server's automatic choice: the FP16 tensor-core pass where a tensor-core kernel takes
+    the shape (session creation succeeds), the FP32 path elsewhere."""
+    try:
+        with spca.Session(n, k, p, 1, math="fp16", max_block_rows=4096):
+            return "fp16"
+    except spca.SpcaError:
+        return "fp32"
 
 
 def test_results_alone_and_in_the_mix():
