@@ -117,6 +117,28 @@ def oracle_pass_seconds(A_rows_f32, seed):
     return time.perf_counter() - t0
 
 
+OMEGA_FORM = {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}
+
+
+def oracle_precision(A_dev, seed, results):
+    """The error of each timed form against the FP64 oracle on the whole timed matrix (the same
+    stored rows, Omega in the form's operand format): sigma_i relative error (all k and the
+    leading 10) and the sine of the largest principal angle between the leading 10 directions.
+    Part of the CPU oracle leg of the benchmark (host cores, outside every timed region)."""
+    from oracle import spca as O
+    A64 = A_dev.cpu().double().numpy()
+    out = {}
+    for math_name, (sigma, V) in results.items():
+        t0 = time.perf_counter()
+        ref = O.single_pass_pca(A64, K, P, seed, BLOCK, center_columns=True, finalize="gram",
+                                omega_form=OMEGA_FORM[math_name])
+        rel = np.abs(sigma - ref["sigma"]) / ref["sigma"]
+        out[math_name] = {"sigma_rel_max": float(rel.max()), "sigma_rel_lead10": float(rel[:10].max()),
+                          "sin_theta_V10": float(O.max_principal_sine(V[:, :10], ref["V"][:, :10])),
+                          "oracle_s": time.perf_counter() - t0}
+    return out
+
+
 def cpu_baseline(A_sample_f32, seed, what):
     secs = oracle_pass_seconds(A_sample_f32, seed)
     gb = A_sample_f32.shape[0] * A_sample_f32.shape[1] * 4 / 1e9
@@ -211,7 +233,7 @@ def roofline_for(math_name, prof, bytes_total, rows_total, pk):
             "algorithmic_bytes_per_launch": bytes_total / max(dom_launches, 1)}
 
 
-TC_KERNEL_SOURCES = ("sketch_tc3.cu", "tc_ptx.cuh")   # the pipelined kernel that runs the pass
+TC_KERNEL_SOURCES = ("sketch_grp.cu", "tc_ptx.cuh")   # the grouped kernel that runs the pass
 
 
 def tc_source_sha256():
@@ -278,12 +300,22 @@ def run_form(spca, math_name, A, seed, stream, steps_arg, warmup, ws):
     per_pass = np.array([marks[i].elapsed_time(marks[i + 1]) for i in range(steps)])
     prof = sess.profile()
     return sess, step, {"ms": ms, "steps": steps, "prof": prof, "sigma": sigma_d.cpu().numpy(),
+                        "V": V_d.cpu().numpy().T,
                         "pass_ms_p50": float(np.percentile(per_pass, 50)),
                         "pass_ms_p99": float(np.percentile(per_pass, 99))}
 
 
 SERVING = "64 sessions, n log-uniform in [512, 32768], l in {20, 40, 80, 140} (k = l - 10), FP32 row blocks " \
           "of 256-4096 rows (uniform), low-rank-plus-noise per session seed, Poisson arrivals"
+
+
+def tensor_core_takes(spca, n, l):
+    """Whether the serving loop's automatic choice puts a session of this shape on the tensor cores."""
+    try:
+        with spca.Session(n, l - 10, 10, 1, math="fp16", max_block_rows=4096):
+            return True
+    except spca.SpcaError:
+        return False
 
 
 def run_serving(spca, dev, seconds=4.0, load=0.5, seed=17040769 + 4):
@@ -370,10 +402,55 @@ def run_serving(spca, dev, seconds=4.0, load=0.5, seed=17040769 + 4):
                 "finalize_p50_ms": st["finalize_p50_ms"], "finalize_p99_ms": st["finalize_p99_ms"],
                 "latency_note": "percentiles over the Poisson phase (plus one 256-row admission block per "
                                 "session before it) and the final finalize of every session",
-                "tc_sessions": int(sum(1 for i in range(S) if int(ls[i]) + 1 <= 64 and int(ns[i]) <= 10240)),
+                "tc_sessions": int(sum(1 for i in range(S) if tensor_core_takes(spca, int(ns[i]), int(ls[i])))),
                 "device_budget_bytes": st["device_bytes_budget"]})
     del pools
     return out
+
+
+def h2d_copy_gbs(host, dev):
+    """A plain pinned host-to-device copy's rate (three copies after two warm-up copies)."""
+    buf = torch.empty(host.shape, dtype=host.dtype, device=dev)
+    for _ in range(2):
+        buf.copy_(host, non_blocking=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        buf.copy_(host, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    del buf
+    return 3 * host.numel() * host.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
+def run_streamed(spca, dev, math_name):
+    """The 937500 x 40000 FP32 stream (150 GB, larger than the device) from pinned host memory
+    through spca_update with host pointers (the session's double-buffered copies), against a
+    plain pinned host-to-device copy measured in the same run."""
+    from paper_1704_07669_gb300 import synth
+    w = synth.workload_c4(device=dev)
+    pool, schedule = w["pool"], w["schedule"]
+    n, k, p, seed = w["n"], w["k"], w["p"], w["seed"]
+    torch.cuda.synchronize()
+    copy_gbs = h2d_copy_gbs(pool[0], dev)
+    rows_np = [b.numpy() for b in pool]
+    with spca.Session(n, k, p, seed, math=math_name) as s:
+        s.update(rows_np[0][:1])         # the staging buffers are made by the first host update
+        s.sync()
+        s.reset(seed)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for b, rows in schedule:
+            s.update(rows_np[b][:rows])
+        sigma, V = s.finalize()          # includes the result's copy to the host
+        secs = time.perf_counter() - t0
+        desc = spca.spca_describe(s.handle)
+    nbytes = 4.0 * w["m"] * n
+    del pool, rows_np
+    return {"workload": w["name"], "math": math_name, "value": nbytes / secs / 1e9, "unit": "GB/s",
+            "seconds": secs, "h2d_copy_GBps": copy_gbs, "frac_of_h2d": nbytes / secs / 1e9 / copy_gbs,
+            "kernel": desc, "note": "end to end: host rows -> device by the session's pinned staging, the pass, "
+                                    "the FP64 finalisation, sigma and V back to the host"}
 
 
 def run_ours(args):
@@ -397,9 +474,11 @@ def run_ours(args):
 
     # the other arithmetic forms, measured first on the same data (reported under "forms")
     forms = {}
+    results = {}
     for other in [f for f in args.forms.split(",") if f and f != args.math]:
         s_o, _, r_o = run_form(spca, other, A, seed, stream, args.steps, args.warmup, ws)
         s_o.close()
+        results[other] = (r_o["sigma"], r_o["V"])
         forms[other] = {"value": ws * bytes_A * r_o["steps"] / (r_o["ms"] * 1e-3) / 1e9, "unit": "GB/s",
                         "ms_per_step": r_o["ms"] / r_o["steps"], "steps": r_o["steps"],
                         "roofline": roofline_for(other, r_o["prof"], bytes_A * r_o["steps"], m * r_o["steps"], pk),
@@ -409,6 +488,7 @@ def run_ours(args):
         time.sleep(0.3)
         sess, step, res = run_form(spca, args.math, A, seed, stream, args.steps, args.warmup, ws)
     ms, steps, prof = res["ms"], res["steps"], res["prof"]
+    results[args.math] = (res["sigma"], res["V"])
     launches = int(sum(v[1] for v in prof.values()))
     value = ws * bytes_A * steps / (ms * 1e-3) / 1e9
     roofline = roofline_for(args.math, prof, bytes_A * steps, m * steps, pk)
@@ -441,6 +521,12 @@ def run_ours(args):
            "d2h_bytes_per_step": 8 * (K + K * N)}
 
     # the optional parts report a failure inside the line instead of losing the measurement
+    streamed = None
+    if rank == 0 and not args.no_streamed:
+        try:
+            streamed = run_streamed(spca, dev, args.math)
+        except Exception as exc:   # noqa: BLE001 - any failure of this part is reported, not raised
+            streamed = {"error": f"{type(exc).__name__}: {exc}"}
     serving = None
     if rank == 0 and not args.no_serving:
         try:
@@ -449,12 +535,19 @@ def run_ours(args):
             serving = {"error": f"{type(exc).__name__}: {exc}"}
 
     cpu = None
+    precision = None
     if rank == 0 and not args.no_cpu_baseline:
+        # the CPU oracle leg: the oracle timed on a bounded sample, and the oracle's result on the
+        # whole matrix for the error of each timed form
         sample_rows = min(8 * BLOCK, m)
         try:
             cpu = cpu_baseline(A[:sample_rows].cpu().numpy(), seed, "first 8 row blocks of the timed matrix")
         except Exception as exc:   # noqa: BLE001
             cpu = {"error": f"{type(exc).__name__}: {exc}", "kind": "oracle"}
+        try:
+            precision = oracle_precision(A, seed, results)
+        except Exception as exc:   # noqa: BLE001
+            precision = {"error": f"{type(exc).__name__}: {exc}"}
 
     sess.close()
     if rank != 0:
@@ -467,7 +560,8 @@ def run_ours(args):
                        "l2": f"inputs larger than L2 ({bytes_A / 1e9:.1f} GB), no flush",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks.summary(), "kernels": kernels, "forms": forms, "serving": serving,
+            "precision_vs_oracle": precision,
+            "clocks": clocks.summary(), "kernels": kernels, "forms": forms, "serving": serving, "streamed": streamed,
             "pass_ms": {"p50": res["pass_ms_p50"], "p99": res["pass_ms_p99"],
                         "note": "per-pass times of the timed passes (CUDA events on the session stream)"},
             "peaks_source": pk["source"],
@@ -489,6 +583,7 @@ def main():
     ap.add_argument("--m", type=int, default=M, help="rows of the workload (profiling runs use fewer)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--no-streamed", action="store_true", help="skip the 150 GB host-stream measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         if args.steps is None:

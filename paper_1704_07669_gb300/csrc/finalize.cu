@@ -1086,6 +1086,490 @@ __global__ void __launch_bounds__(EIG_T) eig_f32_kernel(const double* __restrict
   }
 }
 
+// The same FP32 Jacobi solve for r <= EIG2_MAXR, organised so that a round needs one
+// barrier and shared memory is read and written without bank conflicts. Pairs sit at fixed
+// positions (i, np + i) of the de = 2 np padded indices (an odd r gets a zero dummy index);
+// after every round the matrix moves one step along the circle ordering (position 0 stays,
+// the others form a cycle top 1 .. top np-1, bottom np-1 .. bottom 0), so that m = de - 1
+// rounds meet every pair once and bring every index back to where it started. The matrix
+// lives in two buffers of odd row stride: a round reads one and writes the other, each 2 x 2
+// block (a, b), a <= b, becoming R_a M R_b^T at its moved place together with its mirror
+// image (so the matrix stays exactly symmetric). Meanwhile one warp works out the next
+// round's rotations from the same input: the three entries that the next round's pair
+// will hold are entries of rotated 2 x 2 blocks of this round, which it forms with the same
+// arithmetic as the update, and it appends them to a log in global memory. The eigenvector
+// matrix is not formed here: eig_replay_kernel applies the logged rotations to the rows of
+// the identity, one warp per row, in parallel over the GPU. Stopping rules as in
+// eig_f32_kernel; info[4] = sweeps, info[5] = rounds made.
+constexpr int EIG2_T = 1024;
+constexpr int EIG2_MAXR = 128;
+constexpr int EIG2_RW = EIG2_T / 32 - 1;            // the rotation warp; warps 0 .. EIG2_RW - 1 update
+constexpr int EIG2_NU = EIG2_RW * 32;               // update threads
+constexpr int EIG2_MAXK = (32 * 65 + EIG2_NU - 1) / EIG2_NU;   // blocks per update thread at r = 128
+constexpr int EIG2_SWEEPS = 16;
+
+__host__ __device__ inline size_t eig2_smem(int l) {
+  const size_t de = static_cast<size_t>(l + (l & 1));
+  return sizeof(float) * 2 * de * (de + 1) + sizeof(int) * de;
+}
+
+// rotations the log can hold for r <= l: every round of EIG2_SWEEPS sweeps and one more
+__host__ __device__ inline size_t eig2_log_len(int l) {
+  const size_t de = static_cast<size_t>(l + (l & 1));
+  return (EIG2_SWEEPS * (de - 1) + 1) * (de / 2);
+}
+
+// Cycle coordinate of position pos != 0 (top i -> i - 1, bottom i -> 2 np - 2 - i) and back.
+__device__ __forceinline__ int circ_cyc(int pos, int np) { return pos < np ? pos - 1 : 3 * np - 2 - pos; }
+__device__ __forceinline__ int circ_pos(int c, int np) { return c < np - 1 ? c + 1 : 3 * np - 2 - c; }
+
+// Position reached from `pos` after k rounds, |k| < m = 2 np - 1 (k < 0: where it came from).
+__device__ __forceinline__ int circ_move(int pos, int k, int np) {
+  if (pos == 0) return 0;
+  const int m = 2 * np - 1;
+  int c = circ_cyc(pos, np) + k;
+  if (c >= m) c -= m;
+  else if (c < 0) c += m;
+  return circ_pos(c, np);
+}
+
+// o = R_a M R_b^T for the 2 x 2 block M = [m00 m01; m10 m11], R = [c -s; s c], with every
+// rounding fixed (no contraction left to the compiler) so that the update and the rotation
+// warp get the same values.
+__device__ __forceinline__ void rot_block(float m00, float m01, float m10, float m11, float ca, float sa, float cb,
+                                          float sb, float& o00, float& o01, float& o10, float& o11) {
+  const float r00 = __fmaf_rn(ca, m00, __fmul_rn(-sa, m10)), r01 = __fmaf_rn(ca, m01, __fmul_rn(-sa, m11));
+  const float r10 = __fmaf_rn(sa, m00, __fmul_rn(ca, m10)), r11 = __fmaf_rn(sa, m01, __fmul_rn(ca, m11));
+  o00 = __fmaf_rn(cb, r00, __fmul_rn(-sb, r01));
+  o01 = __fmaf_rn(sb, r00, __fmul_rn(cb, r01));
+  o10 = __fmaf_rn(cb, r10, __fmul_rn(-sb, r11));
+  o11 = __fmaf_rn(sb, r10, __fmul_rn(cb, r11));
+}
+
+// Entry (i, j) of R_a M R_b^T alone (M at `M`, its bottom row npl floats on, its right
+// column np on), with exactly the operations rot_block uses for it.
+__device__ __forceinline__ float rot_entry(const float* M, int np, int npl, bool i, bool j, float2 ra, float2 rb) {
+  const float a0 = i ? ra.y : ra.x, a1 = i ? ra.x : -ra.y;   // row i of R_a
+  const float b0 = j ? rb.y : rb.x, b1 = j ? rb.x : -rb.y;   // row j of R_b
+  const float r0 = __fmaf_rn(a0, M[0], __fmul_rn(a1, M[npl]));
+  const float r1 = __fmaf_rn(a0, M[np], __fmul_rn(a1, M[npl + np]));
+  return __fmaf_rn(b0, r0, __fmul_rn(b1, r1));
+}
+
+__device__ __forceinline__ float2 eig2_rotation(float app, float aqq, float apq, float eps2, bool& rotated) {
+  float c = 1.f, s = 0.f;
+  const float a2 = apq * apq;
+  rotated = a2 > 1e-37f && a2 > eps2 * fabsf(app * aqq);
+  if (rotated) jacobi_rotation32(app, aqq, apq, c, s);
+  return make_float2(c, s);
+}
+
+// Double-float numbers (hi + lo, |lo| <= ulp(hi) / 2): the polish keeps its diagonal in this
+// form, since FP64 instructions issue at a small fraction of the FP32 rate on this GPU and
+// would sit on the critical path of every round. Knuth's two-sum and the FMA two-product.
+__device__ __forceinline__ float2 df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {   // a + b, both double-float
+  const float2 s = df_two_sum(a.x, b.x);
+  const float lo = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
+  const float hi = __fadd_rn(s.x, lo);
+  return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s.x)));
+}
+__device__ __forceinline__ float2 df_prod(float a, float b) {   // a b exactly, as hi + lo
+  const float p = __fmul_rn(a, b);
+  return make_float2(p, __fmaf_rn(a, b, -p));
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// The polish's rotation (the rules of jacobi_mixed): double-float diagonal, FP32 pivot; a
+// pair is left alone when a_pq^2 <= eps_rel^2 |a_pp a_qq|, or when rotating it would change
+// neither eigenvalue by more than tau1 relative nor the vectors by more than tau2 rad (the
+// tests scaled so that nothing underflows for entries of the scaled matrix down to about
+// 1e-30). del = t a_pq exactly, the change of the two diagonal entries (a_pp - del, a_qq + del).
+constexpr double POL_EPS2 = 1e-36, POL_TAU1 = 1e-8, POL_TAU2 = 1e-6;
+__device__ __forceinline__ float2 mixed_rotation(float2 app, float2 aqq, float apq, float2& del, bool& rotated) {
+  const float2 gd = df_add(aqq, df_neg(app));
+  const float gap = fabsf(gd.x), mn = fminf(fabsf(app.x), fabsf(aqq.x)), aa = fabsf(apq);
+  // |a_pq| > 1e-18 sqrt|a_pp a_qq|; a_pq^2 <= tau1 mn gap as (|a_pq| / sqrt(mn))^2 <= tau1 gap
+  bool work = aa > 0.f && aa > 1e-18f * sqrtf(fabsf(app.x)) * sqrtf(fabsf(aqq.x));
+  if (work) {
+    const float q = aa * rsqrtf(fmaxf(mn, 1e-37f));
+    if (q * q <= static_cast<float>(POL_TAU1) * gap && aa <= static_cast<float>(POL_TAU2) * gap) work = false;
+  }
+  rotated = work;
+  del = make_float2(0.f, 0.f);
+  if (!work) return make_float2(1.f, 0.f);
+  const float theta = __fdiv_rn(gd.x, 2.f * apq);
+  const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+  const float x = fmaf(t, t, 1.f);
+  float y = rsqrtf(x);
+  y = y * fmaf(-0.5f * x * y, y, 1.5f);
+  y = y * fmaf(-0.5f * x * y, y, 1.5f);
+  del = df_prod(t, apq);
+  return make_float2(y, t * y);
+}
+
+// MIXED = false: the FP32 solve of C (eigenvectors through the log; info[4] = sweeps).
+// MIXED = true: the polish of the nearly diagonal C1 = W^T C W - its diagonal in FP64 (moved
+// with the matrix, by position), the off-diagonal part in FP32, a rotated pair's block set
+// to zero; on return lam (descending), sig = sqrt(lam), rank[j] = the place of index j in
+// that order, info[3] = sweeps. Both: info[5] = rounds made (the log's length).
+template <bool MIXED>
+__global__ void __launch_bounds__(EIG2_T) jacobi_circle_kernel(const double* __restrict__ C, float2* __restrict__ rlog,
+                                                               int* __restrict__ info, int L, double* __restrict__ lam,
+                                                               double* __restrict__ sig, int* __restrict__ rank) {
+  extern __shared__ float e2[];
+  __shared__ float red[2 * (EIG2_T / 32)];
+  __shared__ double scale;
+  __shared__ float2 rot[2][EIG2_MAXR / 2];   // by round parity: (c, s) of each pair
+  __shared__ float2 rdel[2][EIG2_MAXR / 2];  // MIXED, by round parity: t a_pq of each pair (double-float)
+  __shared__ float2 dgs[2][EIG2_MAXR];       // MIXED, by round parity: the diagonal by position (double-float)
+  __shared__ int rflag[2];                   // by round parity: any rotation in that round
+  __shared__ int needed;
+  const int r = info[0];
+  const int de = r + (r & 1), np = de >> 1, m = de - 1, lda = de + 1, dd = de * lda, npl = np * lda;
+  int* pn = reinterpret_cast<int*>(e2 + 2 * dd);   // position after one round
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid < 32) {   // scaled by a power of two so that the largest diagonal entry is in [1, 2)
+    double dm = 0.0;
+    for (int i = tid; i < r; i += 32) dm = fmax(dm, fabs(C[i * L + i]));
+    for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    if (tid == 0) scale = pow2_scale(dm);
+  }
+  __syncthreads();
+  const double sc = scale;
+  for (int i = warp; i < de; i += EIG2_T / 32)
+    for (int j = lane; j < de; j += 32) {
+      const bool in = i < r && j < r && (!MIXED || i != j);
+      e2[i * lda + j] = in ? static_cast<float>(sc * C[i * L + j]) : 0.f;
+    }
+  if (MIXED)
+    for (int i = tid; i < de; i += blockDim.x) {
+      const double v = i < r ? sc * C[i * L + i] : 0.0;
+      const float hi = static_cast<float>(v);
+      dgs[0][i] = make_float2(hi, static_cast<float>(v - static_cast<double>(hi)));
+    }
+  for (int p = tid; p < de; p += blockDim.x) pn[p] = circ_move(p, 1, np);
+  __syncthreads();
+  const float eps2 = 3e-8f * 3e-8f;
+  // the update threads' blocks (a, b), a <= b: the triangle of pairs folded into nf / 2 rows
+  // of nf + 1 (nf = np rounded up to even), taken in order; offsets fixed for the whole solve
+  int u_ab[EIG2_MAXK], u_src[EIG2_MAXK], u_d0[EIG2_MAXK], u_d1[EIG2_MAXK], u_m0[EIG2_MAXK], u_m1[EIG2_MAXK];
+  // the rotation warp's: the next round's pair j = lane + 32 h holds the indices now at
+  // positions px (top) and py (bottom), of this round's pairs al and be
+  int w_ofs[2][3], w_pair[2];
+  if (warp < EIG2_RW) {
+    const int nf = np + (np & 1), fcols = nf + 1, items = (nf >> 1) * fcols;
+#pragma unroll
+    for (int k = 0; k < EIG2_MAXK; ++k) {
+      const int it = tid + k * EIG2_NU;
+      u_ab[k] = -1;
+      if (it < items) {
+        const int fr = it / fcols, fc = it - fr * fcols;
+        int pa, pb;
+        if (fc < nf - fr) {
+          pa = fr;
+          pb = fr + fc;
+        } else {
+          pa = nf - 1 - fr;
+          pb = pa + fc - (nf - fr);
+        }
+        if (pb < np) {
+          const int Pa = pn[pa] * lda, Pna = pn[np + pa] * lda, Pb = pn[pb], Pnb = pn[np + pb];
+          const int Ra = pn[pa], Rna = pn[np + pa], Rb = pn[pb] * lda, Rnb = pn[np + pb] * lda;
+          u_ab[k] = pa | (pb << 8);
+          u_src[k] = pa * lda + pb;
+          u_d0[k] = (Pa + Pb) | ((Pa + Pnb) << 16);     // o00, o01 in place
+          u_d1[k] = (Pna + Pb) | ((Pna + Pnb) << 16);   // o10, o11 in place
+          u_m0[k] = (Rb + Ra) | ((Rnb + Ra) << 16);     // o00, o01 mirrored
+          u_m1[k] = (Rb + Rna) | ((Rnb + Rna) << 16);   // o10, o11 mirrored
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      const int px = j < np ? circ_move(j, -1, np) : 0, py = j < np ? circ_move(np + j, -1, np) : np;
+      const int al = px < np ? px : px - np, be = py < np ? py : py - np;
+      const int rx = px < np ? 0 : 1, ry = py < np ? 0 : 1;
+      const int lo = al < be ? al : be, hi = al < be ? be : al;
+      w_ofs[h][0] = al * lda + al;
+      w_ofs[h][1] = be * lda + be;
+      w_ofs[h][2] = lo * lda + hi;
+      // the stored a_pq is entry (rx, ry) of block (al, be), or (ry, rx) of its mirror (be,
+      // al); with one pair only (al == be, r <= 2) it is entry (0, 1) of that pair's block
+      const int iu = al < be ? rx : (al > be ? ry : 0), ju = al < be ? ry : (al > be ? rx : 1);
+      w_pair[h] = al | (be << 8) | (rx << 16) | (ry << 17) | (iu << 18) | (ju << 19) | ((al < be ? 1 : 0) << 20) |
+                  ((al == be ? 1 : 0) << 21);
+    }
+    bool any = false;   // the first round's rotations, from the pairs (i, np + i) as they stand
+    for (int j = lane; j < np; j += 32) {
+      bool rt;
+      float2 cs;
+      if (MIXED) {
+        float2 del;
+        cs = mixed_rotation(dgs[0][j], dgs[0][np + j], e2[j * lda + np + j], del, rt);
+        rdel[0][j] = del;
+      } else {
+        cs = eig2_rotation(e2[j * lda + j], e2[(np + j) * lda + np + j], e2[j * lda + np + j], eps2, rt);
+      }
+      rot[0][j] = cs;
+      rlog[j] = cs;
+      any |= rt;
+    }
+    any = __any_sync(0xffffffffu, any);
+    if (lane == 0) rflag[0] = any ? 1 : 0;
+  }
+  __syncthreads();
+#ifdef SPCA_FIN_TRACE
+  const long long t0 = clock64();
+#endif
+  int g = 0;   // rounds made: the parity picks the buffers
+  int sweep = 0;
+  for (; sweep < EIG2_SWEEPS && r > 1; ++sweep) {
+    const float* Ac = e2 + (g & 1) * dd;   // positions are the identity between sweeps
+    float off = 0.f, tot = 0.f;
+    for (int i = warp; i < de; i += EIG2_T / 32)
+      for (int j = lane; j < de; j += 32) {
+        const float v = Ac[i * lda + j];
+        tot = fmaf(v, v, tot);
+        if (i != j) off = fmaf(v, v, off);
+      }
+    if (MIXED) {   // sums in FP32 (norms; FP64 instructions issued by every thread are slow here)
+      const float2* dg = dgs[g & 1];
+      for (int i = tid; i < de; i += blockDim.x) tot = fmaf(dg[i].x, dg[i].x, tot);
+      blk_sum2(off, tot, red);
+      if (off <= 1e-26f * tot || tot == 0.f) break;   // tot: the off-diagonal part and the diagonal
+      // look at every pair at once (FP32 estimates) and stop if none needs a rotation
+      if (tid == 0) needed = 0;
+      __syncthreads();
+      for (int i = warp; i < r; i += EIG2_T / 32) {
+        const float ai = dg[i].x;
+        for (int j = i + 1 + lane; j < r; j += 32) {
+          const float aa = fabsf(Ac[i * lda + j]), aj = dg[j].x;
+          const float gap = fabsf(aj - ai), mn = fminf(fabsf(ai), fabsf(aj));
+          const bool work = aa > 1e-18f * sqrtf(fabsf(ai)) * sqrtf(fabsf(aj)) &&
+                            !(aa * aa <= static_cast<float>(POL_TAU1) * mn * gap &&
+                              aa <= static_cast<float>(POL_TAU2) * gap);
+          if (work) needed = 1;
+        }
+      }
+      __syncthreads();
+      if (!needed) break;
+    } else {
+      blk_sum2(off, tot, red);
+      if (off <= 1e-10f * tot || tot == 0.f) break;
+    }
+    bool any_sweep = false;
+    for (int t = 0; t < m; ++t, ++g) {
+      const float* A = e2 + (g & 1) * dd;
+      float* An = e2 + ((g + 1) & 1) * dd;
+      const float2* ro = rot[g & 1];
+      const bool any = rflag[g & 1] != 0;
+      any_sweep |= any;
+      if (warp == EIG2_RW) {
+        bool anyn = false;
+        float2* lg = rlog + static_cast<size_t>(g + 1) * np;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = lane + 32 * h;
+          if (j < np) {
+            const int wp = w_pair[h], al = wp & 0xff, be = (wp >> 8) & 0xff;
+            const bool rx = (wp >> 16) & 1, ry = (wp >> 17) & 1, alo = (wp >> 20) & 1;
+            const float2 ra = ro[al], rb = ro[be];
+            float apq = rot_entry(A + w_ofs[h][2], np, npl, (wp >> 18) & 1, (wp >> 19) & 1, alo ? ra : rb, alo ? rb : ra);
+            if ((wp >> 21) & 1) apq = ra.y != 0.f ? 0.f : apq;   // one pair only: zeroed if rotated
+            bool rt;
+            float2 cs;
+            if (MIXED) {
+              const float2* dg = dgs[g & 1];
+              const float2 da = rdel[g & 1][al], db = rdel[g & 1][be];
+              const float2 app = df_add(dg[al + rx * np], rx ? da : df_neg(da));
+              const float2 aqq = df_add(dg[be + ry * np], ry ? db : df_neg(db));
+              float2 del;
+              cs = mixed_rotation(app, aqq, apq, del, rt);
+              rdel[(g + 1) & 1][j] = del;
+              dgs[(g + 1) & 1][j] = app;
+              dgs[(g + 1) & 1][np + j] = aqq;
+            } else {
+              const float app = rot_entry(A + w_ofs[h][0], np, npl, rx, rx, ra, ra);
+              const float aqq = rot_entry(A + w_ofs[h][1], np, npl, ry, ry, rb, rb);
+              cs = eig2_rotation(app, aqq, apq, eps2, rt);
+            }
+            rot[(g + 1) & 1][j] = cs;
+            lg[j] = cs;
+            anyn |= rt;
+          }
+        }
+        anyn = __any_sync(0xffffffffu, anyn);
+        if (lane == 0) rflag[(g + 1) & 1] = anyn ? 1 : 0;
+      } else {
+#pragma unroll
+        for (int k = 0; k < EIG2_MAXK; ++k) {
+          if (u_ab[k] < 0) continue;
+          const int pa = u_ab[k] & 0xff, pb = u_ab[k] >> 8;
+          const float2 ra = ro[pa], rb = ro[pb];
+          const float* M = A + u_src[k];
+          float o00, o01, o10, o11;
+          rot_block(M[0], M[np], M[npl], M[npl + np], ra.x, ra.y, rb.x, rb.y, o00, o01, o10, o11);
+          if (pa == pb) {   // the pair's own block: symmetric, its off-diagonal entry zeroed if rotated
+            if (ra.y != 0.f) {
+              o01 = 0.f;
+              if (MIXED) {   // the diagonal lives in FP64 outside this matrix
+                o00 = 0.f;
+                o11 = 0.f;
+              }
+            }
+            o10 = o01;
+          }
+          An[u_d0[k] & 0xffff] = o00;
+          An[u_d0[k] >> 16] = o01;
+          An[u_d1[k] & 0xffff] = o10;
+          An[u_d1[k] >> 16] = o11;
+          An[u_m0[k] & 0xffff] = o00;
+          An[u_m0[k] >> 16] = o01;
+          An[u_m1[k] & 0xffff] = o10;
+          An[u_m1[k] >> 16] = o11;
+        }
+      }
+      __syncthreads();
+    }
+    if (!any_sweep) {
+      ++sweep;
+      break;
+    }
+  }
+#ifdef SPCA_FIN_TRACE
+  if (tid == 0)
+    printf("%s d=%d sweeps=%d rounds=%d cycles=%lld\n", MIXED ? "polish_circle" : "eig_f32_circle", r, sweep, g,
+           clock64() - t0);
+#endif
+  if (MIXED) {   // eigenvalues by descending value, ties by index
+    const float2* dg = dgs[g & 1];
+    for (int i = tid; i < r; i += blockDim.x) {   // compared as (hi, lo) pairs: normalised, so in order
+      int rk = 0;
+      const float2 vi = dg[i];
+      for (int j = 0; j < r; ++j) {
+        const float2 u = dg[j];
+        if (u.x > vi.x || (u.x == vi.x && (u.y > vi.y || (u.y == vi.y && j < i)))) ++rk;
+      }
+      const double v = static_cast<double>(vi.x) + static_cast<double>(vi.y);
+      lam[rk] = v / sc;
+      sig[rk] = sqrt(fmax(v / sc, 0.0));
+      rank[i] = rk;
+    }
+    for (int i = r + tid; i < L; i += blockDim.x) sig[i] = 0.0;
+  }
+  if (tid == 0) {
+    info[MIXED ? 3 : 4] = sweep;
+    info[5] = g;
+  }
+}
+
+// W0 (L x L, zero outside r x r) = the product of the logged rotations, applied in order to
+// the rows of the identity, one warp per row; with `rank` its columns are put in that order.
+// A row is kept by position, like the matrix of the solve: lane b holds positions b and
+// np + b (and b + 32, np + b + 32 when np > 32) in registers, rotates them with its pair's
+// logged rotation and passes them one step along the circle with shuffles; after whole
+// sweeps the positions are the indices again. The log is staged in shared memory a chunk of
+// rounds at a time, the next chunk loading (cp.async) while the current one is applied.
+constexpr int RPL_W = 4;      // warps (rows) per block
+constexpr int RPL_RC = 48;    // rounds per chunk
+
+__host__ __device__ inline size_t replay_smem(int l) {
+  const size_t de = static_cast<size_t>(l + (l & 1));
+  return sizeof(float2) * 2 * RPL_RC * (de / 2);
+}
+
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(sdst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void rot_pair(float2 cs, float& t, float& b) {
+  const float x = t, y = b;
+  t = cs.x * x - cs.y * y;
+  b = cs.y * x + cs.x * y;
+}
+
+__global__ void __launch_bounds__(RPL_W * 32) eig_replay_kernel(const float2* __restrict__ rlog,
+                                                               const int* __restrict__ info, int L,
+                                                               const int* __restrict__ rank,
+                                                               double* __restrict__ W0) {
+  extern __shared__ float2 rp[];
+  const int r = info[0], G = info[5];
+  const int de = r + (r & 1), np = de >> 1;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * RPL_W + (threadIdx.x >> 5);
+  const bool live = i < r;
+  const unsigned full = 0xffffffffu;
+  // T0, B0: positions lane, np + lane; T1, B1: positions 32 + lane, np + 32 + lane
+  float T0 = (lane == i) ? 1.f : 0.f, B0 = (np + lane == i) ? 1.f : 0.f;
+  float T1 = (32 + lane == i) ? 1.f : 0.f, B1 = (np + 32 + lane == i) ? 1.f : 0.f;
+  const bool two = np > 32;
+  const int nchunks = (G + RPL_RC - 1) / RPL_RC;
+  auto load = [&](int c) {
+    float2* dst = rp + (c & 1) * RPL_RC * np;
+    const int g0 = c * RPL_RC, n = min(RPL_RC, G - g0) * np;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) cp_async8(dst + e, rlog + static_cast<size_t>(g0) * np + e);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  if (nchunks > 0) load(0);
+  for (int c = 0; c < nchunks; ++c) {
+    if (c + 1 < nchunks) {
+      load(c + 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();
+    const float2* ck = rp + (c & 1) * RPL_RC * np;
+    const int n = min(RPL_RC, G - c * RPL_RC);
+    if (live) {
+      for (int gg = 0; gg < n; ++gg) {
+        const float2* cr = ck + gg * np;
+        if (lane < np) rot_pair(cr[lane], T0, B0);
+        if (two && 32 + lane < np) rot_pair(cr[32 + lane], T1, B1);
+        if (np == 1) continue;   // one pair: the circle is a single position
+        // one step along the circle: top p -> p + 1 (p >= 1), top np-1 -> bottom np-1,
+        // bottom q -> q - 1 (q >= 1), bottom 0 -> top 1, top 0 stays
+        const float t0u = __shfl_up_sync(full, T0, 1), t1u = __shfl_up_sync(full, T1, 1);
+        const float b0d = __shfl_down_sync(full, B0, 1), b1d = __shfl_down_sync(full, B1, 1);
+        const float t0l = __shfl_sync(full, T0, 31), b0f = __shfl_sync(full, B0, 0), b1f = __shfl_sync(full, B1, 0);
+        const float nT0 = lane == 0 ? T0 : (lane == 1 ? b0f : t0u);
+        const float nT1 = lane == 0 ? t0l : t1u;
+        float nB0 = lane == 31 ? b1f : b0d;
+        float nB1 = b1d;
+        if (lane == np - 1) nB0 = T0;
+        if (32 + lane == np - 1) nB1 = T1;
+        T0 = nT0;
+        T1 = nT1;
+        B0 = nB0;
+        B1 = nB1;
+      }
+    }
+    __syncthreads();   // the buffer is reloaded two chunks on
+  }
+  if (i < L) {   // position p = index p again; column j of the product goes to column rank[j]
+    double* row = W0 + static_cast<size_t>(i) * L;
+    for (int j = lane; j < L; j += 32) row[j] = 0.0;
+    __syncwarp();
+    if (live) {
+      const float v[4] = {T0, B0, T1, B1};
+      const int pos[4] = {lane, np + lane, 32 + lane, np + 32 + lane};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int j = pos[h];
+        const bool mine = (h & 1) ? (lane + (h >> 1) * 32 < np) : (lane + (h >> 1) * 32 < np);
+        if (mine && j < r) row[rank ? rank[j] : j] = static_cast<double>(v[h]);
+      }
+    }
+  }
+}
+
 // Out = alpha op(A) op(B) + beta D on the leading r x r block (ld L, zero elsewhere), with
 // r = *rdev when rdev is given, else rhost; one block per row, FP64. Row i of op(A) is
 // staged in shared memory, and op(B) too when `stage` is set (as rows of r). D may be NULL.
@@ -1260,6 +1744,12 @@ void set_dense_attrs() {
     cudaFuncSetAttribute(small_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(kGemmSmemMax));
     cudaFuncSetAttribute(eig_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kMaxDenseSmem));
+    cudaFuncSetAttribute(jacobi_circle_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(eig2_smem(EIG2_MAXR)));
+    cudaFuncSetAttribute(jacobi_circle_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(eig2_smem(EIG2_MAXR)));
+    cudaFuncSetAttribute(eig_replay_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(replay_smem(EIG2_MAXR)));
     cudaFuncSetAttribute(eig_polish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(kMaxDenseSmem));
     cudaFuncSetAttribute(bt_and_c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1334,8 +1824,17 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
   // partials are consumed by now, and T, X, W)
   float* s64 = reinterpret_cast<float*>(f.Cpart + 2 * LL);   // E, W of the polish: 2 L^2 floats
   double* W1 = f.Cpart + 3 * LL;
-  eig_f32_kernel<<<1, EIG_T, smem32e ? dense32e : 0, st>>>(f.C, s32, s32 + LL, s32 + 2 * LL, f.W, f.info, s.L,
-                                                          smem32e);
+  // the rotation log of the fast solver sits in Cpart after the polish's scratch
+  float2* rlog = reinterpret_cast<float2*>(f.Cpart + 4 * LL);
+  const bool fast_eig = s.l <= EIG2_MAXR && sizeof(double) * static_cast<size_t>(f.nparts - 4) * LL >=
+                                               sizeof(float2) * eig2_log_len(s.l);
+  const int rpl_grid = (L + RPL_W - 1) / RPL_W;
+  if (fast_eig) {
+    jacobi_circle_kernel<false><<<1, EIG2_T, eig2_smem(s.l), st>>>(f.C, rlog, f.info, s.L, nullptr, nullptr, nullptr);
+    eig_replay_kernel<<<rpl_grid, RPL_W * 32, replay_smem(s.l), st>>>(rlog, f.info, L, nullptr, f.W);
+  } else
+    eig_f32_kernel<<<1, EIG_T, smem32e ? dense32e : 0, st>>>(f.C, s32, s32 + LL, s32 + 2 * LL, f.W, f.info, s.L,
+                                                            smem32e);
   // Newton-Schulz, twice: W <- 1.5 W - 0.5 W (W^T W)  (W: f.W -> f.T -> f.W)
   small_gemm_kernel<<<gb, gt, gemm_smem, st>>>(f.W, 1, f.W, 0, nullptr, 1.0, 0.0, f.info, 0, s.L, gstage, f.X);
   small_gemm_kernel<<<gb, gt, gemm_smem, st>>>(f.W, 0, f.X, 0, f.W, -0.5, 1.5, f.info, 0, s.L, gstage, f.T);
@@ -1344,8 +1843,14 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
   // C1 = W^T C W
   small_gemm_kernel<<<gb, gt, gemm_smem, st>>>(f.C, 0, f.W, 0, nullptr, 1.0, 0.0, f.info, 0, s.L, gstage, f.X);
   small_gemm_kernel<<<gb, gt, gemm_smem, st>>>(f.W, 1, f.X, 0, nullptr, 1.0, 0.0, f.info, 0, s.L, gstage, f.T);
-  eig_polish_kernel<<<1, POL_T, smem64 ? dense64 : 0, st>>>(f.T, s64, s64 + LL, W1, f.lam, f.sig, f.info, s.L,
-                                                            smem64);
+  if (fast_eig) {   // the polish's order of the eigenvalues in the scratch of the old polish
+    int* rank = reinterpret_cast<int*>(s64);
+    jacobi_circle_kernel<true><<<1, EIG2_T, eig2_smem(s.l), st>>>(f.T, rlog, f.info, s.L, f.lam, f.sig, rank);
+    eig_replay_kernel<<<rpl_grid, RPL_W * 32, replay_smem(s.l), st>>>(rlog, f.info, L, rank, W1);
+  } else {
+    eig_polish_kernel<<<1, POL_T, smem64 ? dense64 : 0, st>>>(f.T, s64, s64 + LL, W1, f.lam, f.sig, f.info, s.L,
+                                                              smem64);
+  }
   // Z = W W1 (into f.X): the eigenvectors of C, used to form V
   small_gemm_kernel<<<gb, gt, gemm_smem, st>>>(f.W, 0, W1, 0, nullptr, 1.0, 0.0, f.info, 0, s.L, gstage, f.X);
   // a block of rows of Bt, 1/sigma and (when it fits) W's leading l x k block in shared
@@ -1359,7 +1864,7 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
   else
     form_v_kernel<false><<<fv_grid, 256, fv_base, st>>>(f.Bt, f.X, f.sig, f.info, s.n, k, s.L, V_dev);
   sign_fix_kernel<<<k, SIGN_T, 0, st>>>(V_dev, s.n, f.flip);
-  prof->launches[SPCA_K_FINALIZE] += 24;  // launches above beyond the one begin() counted (not the copy)
+  prof->launches[SPCA_K_FINALIZE] += fast_eig ? 26 : 24;  // launches above beyond the one begin() counted (not the copy)
   prof->end(SPCA_K_FINALIZE, st);
   e = cudaMemcpyAsync(sigma_dev, f.sig, sizeof(double) * k, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;

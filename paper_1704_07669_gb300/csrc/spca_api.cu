@@ -521,6 +521,33 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   return SPCA_OK;
 }
 
+namespace {
+
+// Staged rows are laid out with a leading dimension rounded up to 4 elements, so that every
+// staged FP32 row starts on a 16-byte boundary (a tensor map can describe it).
+int64_t stage_ld(int64_t n) { return ((n + 3) / 4) * 4; }
+
+// The two pinned host buffers and two device buffers of the staged paths (made once).
+spca_status ensure_staging(spca_session* s, size_t row_bytes) {
+  if (s->pinned[0]) return SPCA_OK;
+  size_t want = kStageBytes;
+  if (want < row_bytes) want = row_bytes;
+  s->stage_bytes = want;
+  for (int i = 0; i < 2; ++i) {
+    if (cudaMallocHost(&s->pinned[i], want) != cudaSuccess || cudaMalloc(&s->dstage[i], want) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(s, SPCA_E_NOMEM, "staging allocation of %zu bytes failed", want);
+    }
+    CU(cudaEventCreateWithFlags(&s->copied[i], cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&s->consumed[i], cudaEventDisableTiming));
+    CU(cudaEventRecord(s->consumed[i], s->stream));
+    CU(cudaEventRecord(s->copied[i], s->copy_stream));
+  }
+  return SPCA_OK;
+}
+
+}  // namespace
+
 spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t ld, int32_t dtype,
                         const float* block_scale, int32_t rows_on_device, float* G_out) {
   spca_status st = check_usable(s);
@@ -550,10 +577,34 @@ spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t 
     cudaGetLastError();
     if (!ok_attr || (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged))
       return fail(s, SPCA_E_INVALID, "rows_on_device=1 but rows is not a device pointer");
-    for (int64_t r0 = 0; r0 < m_i; r0 += mb) {
-      const int64_t mr = (m_i - r0) < mb ? (m_i - r0) : mb;
-      const char* base = static_cast<const char*>(rows) + size_t(r0) * ld * es;
-      st = run_piece(s, base, mr, ld, dtype, scale, G_out ? G_out + r0 * s->l : nullptr, true);
+    // rows a tensor map cannot describe (not 16-byte aligned, or ld not a multiple of 4) go
+    // through the staging buffers when only the tensor-map kernel takes the shape
+    const bool tma_ok = (reinterpret_cast<uintptr_t>(rows) % 16 == 0) && (ld % 4 == 0);
+    if (!(s->tc && s->tcw.use_grp && !s->tcw.cfg_ok && !tma_ok)) {
+      for (int64_t r0 = 0; r0 < m_i; r0 += mb) {
+        const int64_t mr = (m_i - r0) < mb ? (m_i - r0) : mb;
+        const char* base = static_cast<const char*>(rows) + size_t(r0) * ld * es;
+        st = run_piece(s, base, mr, ld, dtype, scale, G_out ? G_out + r0 * s->l : nullptr, true);
+        if (st != SPCA_OK) return st;
+      }
+      return SPCA_OK;
+    }
+    st = flush_tc(s);   // blocks batched before these stay in order
+    if (st != SPCA_OK) return st;
+    const int64_t lds = stage_ld(s->n);
+    const size_t row_st = size_t(lds) * es;
+    st = ensure_staging(s, row_st);
+    if (st != SPCA_OK) return st;
+    int64_t piece = static_cast<int64_t>(s->stage_bytes / row_st);
+    if (piece > mb) piece = mb;
+    for (int64_t r0 = 0; r0 < m_i; r0 += piece) {
+      const int64_t mr = (m_i - r0) < piece ? (m_i - r0) : piece;
+      const int b = s->next_stage;
+      s->next_stage ^= 1;
+      const char* src = static_cast<const char*>(rows) + size_t(r0) * ld * es;
+      CU(cudaMemcpy2DAsync(s->dstage[b], row_st, src, size_t(ld) * es, size_t(s->n) * es, mr,
+                           cudaMemcpyDeviceToDevice, s->stream));
+      st = run_piece(s, s->dstage[b], mr, lds, dtype, scale, G_out ? G_out + r0 * s->l : nullptr, false);
       if (st != SPCA_OK) return st;
     }
     return SPCA_OK;
@@ -561,22 +612,11 @@ spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t 
   // Host rows: copy pieces through two staging buffers so the copy of piece i+1
   // overlaps the kernels of piece i.
   const size_t row_bytes = size_t(s->n) * es;
-  if (!s->pinned[0]) {
-    size_t want = kStageBytes;
-    if (want < row_bytes) want = row_bytes;
-    s->stage_bytes = want;
-    for (int i = 0; i < 2; ++i) {
-      if (cudaMallocHost(&s->pinned[i], want) != cudaSuccess || cudaMalloc(&s->dstage[i], want) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(s, SPCA_E_NOMEM, "staging allocation of %zu bytes failed", want);
-      }
-      CU(cudaEventCreateWithFlags(&s->copied[i], cudaEventDisableTiming));
-      CU(cudaEventCreateWithFlags(&s->consumed[i], cudaEventDisableTiming));
-      CU(cudaEventRecord(s->consumed[i], s->stream));
-      CU(cudaEventRecord(s->copied[i], s->copy_stream));
-    }
-  }
-  int64_t piece = static_cast<int64_t>(s->stage_bytes / row_bytes);
+  const int64_t lds = stage_ld(s->n);
+  const size_t row_st = size_t(lds) * es;
+  st = ensure_staging(s, row_st);
+  if (st != SPCA_OK) return st;
+  int64_t piece = static_cast<int64_t>(s->stage_bytes / row_st);
   if (piece > mb) piece = mb;
   cudaPointerAttributes attr;
   std::memset(&attr, 0, sizeof(attr));
@@ -590,21 +630,21 @@ spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t 
     const char* src = static_cast<const char*>(rows) + size_t(r0) * ld * es;
     CU(cudaStreamWaitEvent(s->copy_stream, s->consumed[b], 0));
     if (host_pinned) {
-      CU(cudaMemcpy2DAsync(s->dstage[b], row_bytes, src, size_t(ld) * es, row_bytes, mr, cudaMemcpyHostToDevice,
+      CU(cudaMemcpy2DAsync(s->dstage[b], row_st, src, size_t(ld) * es, row_bytes, mr, cudaMemcpyHostToDevice,
                            s->copy_stream));
     } else {
       CU(cudaEventSynchronize(s->copied[b]));   // pinned[b] free again
       char* dst = static_cast<char*>(s->pinned[b]);
-      if (ld == s->n) {
-        std::memcpy(dst, src, row_bytes * mr);
+      if (ld == lds && lds == s->n) {
+        std::memcpy(dst, src, row_st * mr);
       } else {
-        for (int64_t r = 0; r < mr; ++r) std::memcpy(dst + r * row_bytes, src + size_t(r) * ld * es, row_bytes);
+        for (int64_t r = 0; r < mr; ++r) std::memcpy(dst + r * row_st, src + size_t(r) * ld * es, row_bytes);
       }
-      CU(cudaMemcpyAsync(s->dstage[b], dst, row_bytes * mr, cudaMemcpyHostToDevice, s->copy_stream));
+      CU(cudaMemcpyAsync(s->dstage[b], dst, row_st * mr, cudaMemcpyHostToDevice, s->copy_stream));
     }
     CU(cudaEventRecord(s->copied[b], s->copy_stream));
     CU(cudaStreamWaitEvent(s->stream, s->copied[b], 0));
-    st = run_piece(s, s->dstage[b], mr, s->n, dtype, scale, G_out ? G_out + r0 * s->l : nullptr, false);
+    st = run_piece(s, s->dstage[b], mr, lds, dtype, scale, G_out ? G_out + r0 * s->l : nullptr, false);
     if (st != SPCA_OK) return st;
     CU(cudaEventRecord(s->consumed[b], s->stream));
   }

@@ -308,3 +308,21 @@ def test_tc_full_size_100000x10000_against_oracle(math, c2_oracle):
     print(f"{math}: sigma rel max {rel.max():.3e}, leading 10 {rel[:10].max():.3e}")
     assert_sigma(sigma, ref["sigma"], math)
     assert O.max_principal_sine(V[:, :10], ref["V"][:, :10]) <= 5e-2
+
+
+@pytest.mark.parametrize("math", TC_MATHS)
+def test_tc_rows_no_tensor_map_describes_at_large_n(math):
+    """n = 15205 (odd) is taken by the grouped kernel only, which reads rows through tensor maps:
+    device rows with ld = n and host rows go through the session's staging buffers, laid out
+    with a leading dimension padded to 16 bytes; the result equals the oracle's."""
+    A = synth.low_rank_plus_noise(1500, 15205, synth.spectrum("type4", 80), noise_std=1e-4, mean_std=0.5,
+                                  seed=77, dtype=torch.float32)
+    Ad = A.to(DEV)
+    ref = oracle_tc(A, 20, 10, 5, 500, math=math)
+    with spca.Session(15205, 20, 10, 5, math=math) as s:
+        assert "kernel=grouped" in spca.spca_describe(s.handle)
+        s.update(Ad[:500])
+        s.update(A[500:1000].numpy())            # host rows
+        s.update(Ad[1000:])
+        sigma, V = s.finalize()
+    assert_sigma(sigma, ref["sigma"], math)
