@@ -1572,7 +1572,8 @@ __global__ void __launch_bounds__(RPL_W * 32) eig_replay_kernel(const float2* __
 
 // Out = alpha op(A) op(B) + beta D on the leading r x r block (ld L, zero elsewhere), with
 // r = *rdev when rdev is given, else rhost; one block per row, FP64. Row i of op(A) is
-// staged in shared memory, and op(B) too when `stage` is set (as rows of r). D may be NULL.
+// staged in shared memory, and op(B) too when `stage` is set (as r rows of odd stride, by
+// asynchronous copies). D may be NULL.
 constexpr int GEMM_T = 128;
 constexpr size_t kGemmSmemMax = 200 * 1024;
 __global__ void __launch_bounds__(GEMM_T) small_gemm_kernel(const double* __restrict__ A, int ta,
@@ -1581,30 +1582,62 @@ __global__ void __launch_bounds__(GEMM_T) small_gemm_kernel(const double* __rest
                                                             const int* __restrict__ rdev, int rhost, int L,
                                                             int stage, double* __restrict__ Out) {
   extern __shared__ double gsm[];
-  double* sa = gsm;           // r
-  double* sb = gsm + kMaxL;   // r x r: sb[t * r + j] = op(B)[t][j]
+  __shared__ double part[GEMM_T];
+  double* sa = gsm;           // r: row i of op(A)
+  double* sb = gsm + kMaxL;   // op(B)[t][j] at sb[t * ldb + j], ldb odd (column writes spread over banks)
   const int r = rdev ? *rdev : rhost;
+  const int ldb = r | 1;
   const int i = blockIdx.x;
-  if (i < r) {
-    for (int t = threadIdx.x; t < r; t += blockDim.x) sa[t] = ta ? A[t * L + i] : A[i * L + t];
-    if (stage) {
-      for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-        const int t = e / r, j = e - t * r;
-        sb[e] = tb ? B[j * L + t] : B[t * L + j];
-      }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = GEMM_T / 32;
+  if (i < r) {   // asynchronous copies, all in flight at once
+    for (int t = threadIdx.x; t < r; t += blockDim.x) cp_async8(sa + t, ta ? A + t * L + i : A + i * L + t);
+    if (stage) {   // a warp per row of B as stored (coalesced), lanes along it
+      for (int u = warp; u < r; u += nw)
+        for (int v = lane; v < r; v += 32) cp_async8(tb ? sb + v * ldb + u : sb + u * ldb + v, B + u * L + v);
     }
   }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
+  if (stage && r <= GEMM_T / 2) {   // two threads per output, each over half of t, two accumulators each
+    const int j = threadIdx.x % (GEMM_T / 2), h = threadIdx.x / (GEMM_T / 2);
+    const int t0 = h * (r >> 1), t1 = h ? r : (r >> 1);
+    double acc0 = 0.0, acc1 = 0.0;
+    if (i < r && j < r) {
+      int t = t0;
+      for (; t + 1 < t1; t += 2) {
+        acc0 = fma(sa[t], sb[t * ldb + j], acc0);
+        acc1 = fma(sa[t + 1], sb[(t + 1) * ldb + j], acc1);
+      }
+      if (t < t1) acc0 = fma(sa[t], sb[t * ldb + j], acc0);
+    }
+    part[threadIdx.x] = acc0 + acc1;
+    __syncthreads();
+    for (int jj = threadIdx.x; jj < L; jj += blockDim.x) {
+      double acc = 0.0;
+      if (i < r && jj < r) {
+        acc = alpha * (part[jj] + part[jj + GEMM_T / 2]);
+        if (D) acc = fma(beta, D[i * L + jj], acc);
+      }
+      Out[i * L + jj] = acc;
+    }
+    return;
+  }
   for (int j = threadIdx.x; j < L; j += blockDim.x) {
     double acc = 0.0;
     if (i < r && j < r) {
+      double acc1 = 0.0;
       if (stage) {
-#pragma unroll 4
-        for (int t = 0; t < r; ++t) acc = fma(sa[t], sb[t * r + j], acc);
+        int t = 0;
+        for (; t + 1 < r; t += 2) {
+          acc = fma(sa[t], sb[t * ldb + j], acc);
+          acc1 = fma(sa[t + 1], sb[(t + 1) * ldb + j], acc1);
+        }
+        if (t < r) acc = fma(sa[t], sb[t * ldb + j], acc);
       } else {
         for (int t = 0; t < r; ++t) acc = fma(sa[t], tb ? B[j * L + t] : B[t * L + j], acc);
       }
-      acc *= alpha;
+      acc = alpha * (acc + acc1);
       if (D) acc = fma(beta, D[i * L + j], acc);
     }
     Out[i * L + j] = acc;
@@ -1784,7 +1817,7 @@ cudaError_t finalize_run(const State& s, const FinalWork& f, int64_t m, int k, d
   }
   const int l = s.l, L = s.L;
   const int rank_ok = r_max >= l ? 1 : 0;
-  const size_t gemm_full = sizeof(double) * (kMaxL + static_cast<size_t>(l) * l);
+  const size_t gemm_full = sizeof(double) * (kMaxL + static_cast<size_t>(l) * (l | 1));
   const int gstage = gemm_full <= kGemmSmemMax ? 1 : 0;
   const size_t gemm_smem = gstage ? gemm_full : sizeof(double) * kMaxL;
   // mixed-precision route (buffers: Y1 W, X1 T, Y2 X, T2 C, X2 W, F X, T T)
