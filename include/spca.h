@@ -127,7 +127,15 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed,
  *                   as this pass computes them, c being the session's shift
  *                   (the FP32 column mean of the first rows seen when centering
  *                   is on, else 0).
- * m_i = 0 is a no-op. Errors: SPCA_E_INVALID, SPCA_E_CUDA, SPCA_E_STATE.
+ * Tensor-core sessions read BF16 and FP8 rows in their storage format when the
+ * grouped kernel takes (n, l) (spca_describe says "kernel=grouped"): the operand is
+ * (value - c) s rounded once to the operand format, value = code x block_scale for
+ * FP8. A block of another format than the pending ones is launched separately.
+ * Device rows whose start or row pitch is not a multiple of 16 bytes are copied to
+ * the session's staging buffers first. Other tensor-core sessions read FP32 rows
+ * only (SPCA_E_UNSUPPORTED otherwise).
+ * m_i = 0 is a no-op. Errors: SPCA_E_INVALID, SPCA_E_CUDA, SPCA_E_STATE,
+ * SPCA_E_UNSUPPORTED.
  */
 spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t ld,
                         int32_t dtype, const float* block_scale, int32_t rows_on_device,

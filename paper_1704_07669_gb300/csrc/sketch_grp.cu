@@ -4,9 +4,10 @@
 // into 64-feature blocks; CTA j of every group owns the blocks [j NBT / S, (j + 1) NBT / S)
 // for the whole launch. Group g takes the 128-row tiles g, g + NG, g + 2 NG, ... in order.
 // Per tile i of a group:
-//  - phase 1 (every CTA of the group, its own blocks): TMA streams the FP32 rows (two
-//    32-feature boxes per block) into a stage ring; converter warps subtract the shift c,
-//    scale and round into a 16-bit operand block (K-major, 128-byte swizzle); MMA1
+//  - phase 1 (every CTA of the group, its own blocks): TMA streams the stored rows into a
+//    stage ring (FP32: two 32-feature boxes per block; BF16: one 64-feature box; FP8 E4M3:
+//    one 64-feature box of codes, decoded with the block's scale); converter warps subtract
+//    the shift c, scale and round into a 16-bit operand block (K-major, 128-byte swizzle); MMA1
 //    accumulates D1 = A_hat[:, own] Omega[own, :] in TMEM; a copier warp writes each
 //    converted block to the CTA's image ring in global memory (kept in L2);
 //  - the epilogue warps move D1 to the CTA's slot of the group's partial ring in global
@@ -29,6 +30,7 @@
 // skips its later waits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 
 #include <cstdio>
 #include <cstring>
@@ -44,7 +46,7 @@ namespace {
 
 constexpr int GR_ROWS = 128;
 constexpr uint32_t BLK16 = GR_ROWS * 64 * 2;     // 16-bit operand block: 128 rows x 64 features
-constexpr uint32_t STG = GR_ROWS * 32 * 4;       // FP32 stage: 128 rows x 32 features
+constexpr uint32_t STG = GR_ROWS * 32 * 4;       // stage slot: 128 rows x 32 FP32 (or 64 BF16, 64 FP8) features
 constexpr uint32_t P2U = 16384;                  // phase-2 unit: 2 blocks x 64 rows x 128 B
 constexpr int RING_R = 4;                        // group rings (partials, G', counters)
 #ifndef SPCA_GRP_IMG_R
@@ -55,6 +57,8 @@ constexpr int OM_R = 2;                          // Omega blocks in flight
 constexpr int NS2 = 3;                           // phase-2 unit slots
 constexpr int GRAM_BLK = 3;                      // 4 x 2 Gram blocks per reducer thread at most
 constexpr int MAX_SEGS = 48;
+// storage formats of the rows (the session's dtype): FP32, BF16, FP8 E4M3 codes x a block scale
+constexpr int IN_F32 = 0, IN_BF16 = 1, IN_F8 = 2;
 
 // warp roles (21 warps)
 constexpr int W_P1 = 0, W_P2 = 1, W_MMA1 = 2, W_MMA2 = 3;
@@ -104,10 +108,12 @@ struct GrpSeg {
   int64_t m;
   float* gout;
   int64_t tile0;
+  float dscale;                 // FP8 rows: the block's scale (a stored value is code x dscale); else 1
 };
 
 struct GrpArgs {
-  CUtensorMap maps[MAX_SEGS];   // FP32 rows, box 32 features x 128 rows, 128-byte swizzle
+  CUtensorMap maps[MAX_SEGS];   // the rows: FP32 box 32 x 128 and BF16 box 64 x 128 (128-byte swizzle),
+                                // FP8 box 64 x 128 (no swizzle); features x rows
   GrpSeg seg[MAX_SEGS];
   int nseg;
   int64_t ntiles;
@@ -223,6 +229,11 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
 __device__ __forceinline__ void discard_l2(const void* p) {
   asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
+// two E4M3 codes (low byte first) to floats, exactly (through the FP16 conversion)
+__device__ __forceinline__ float2 fp8x2_e4m3_to_float2(uint16_t two) {
+  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(two), __NV_E4M3);
+  return __half22float2(__half2(h));
+}
 __device__ __forceinline__ void st_global_v2u(void* p, uint32_t a, uint32_t b) {
   asm volatile("st.global.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(a), "r"(b) : "memory");
 }
@@ -266,9 +277,11 @@ enum {
 constexpr int BAR_SLOTS = 80;
 static_assert(B_COUNT <= BAR_SLOTS, "barrier slots");
 
-template <int FMT>
+template <int FMT, int INP>
 __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_constant__ GrpArgs a) {
   constexpr int GS = FMT == FMT_F16 ? 2 : 1;
+  constexpr int SPB = INP == IN_F32 ? 2 : 1;                  // stages per 64-feature block
+  constexpr uint32_t SBYTES = INP == IN_F8 ? STG / 2 : STG;   // bytes a stage receives
   extern __shared__ __align__(1024) uint8_t smem_g[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_g) + 1023) & ~uintptr_t(1023));
   const int L = a.L, l = a.l, S = a.S;
@@ -384,10 +397,10 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
         const int32_t y0 = static_cast<int32_t>((tile - a.seg[sgi].tile0) * GR_ROWS);
         GRP_TRACE(i, 0);
         for (int b = 0; b < NB; ++b) {
-          for (int hf = 0; hf < 2; ++hf) {
+          for (int hf = 0; hf < SPB; ++hf) {
             const uint32_t s = spos % a.ns1, k = spos / a.ns1;
             if (k >= 1 && !dead && !mbar_wait_fast(bar(B_S1_EMPTY + s), (k - 1) & 1u)) dead = true;
-            mbar_expect_tx(bar(B_S1_FULL + s), STG);
+            mbar_expect_tx(bar(B_S1_FULL + s), SBYTES);
             tma_load_2d_hint(su32(base + lay.st1) + s * STG, tmap, static_cast<int32_t>(f0 + 64 * b + 32 * hf), y0,
                              bar(B_S1_FULL + s), drop);
             ++spos;
@@ -876,49 +889,99 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
   } else if (warp >= W_CV0 && warp < W_CV0 + CV_W) {
     // ------------------------------------------------------------ converters
     const int ct = tid - W_CV0 * 32;   // 0..127
-    const int cq = ct & 3;             // 32-byte piece (8 features) of a 128-byte stage row
-    const int rb = ct >> 2;            // rows rb + 32 k
     uint32_t spos = 0, opos = 0;
     for (int i = 0; i < nt; ++i) {
       const int64_t tile = grp + static_cast<int64_t>(i) * NG;
       const int sgi = find_seg(a, tile);
       const int64_t row0 = (tile - a.seg[sgi].tile0) * GR_ROWS;
       const int64_t mseg = a.seg[sgi].m;
+      const float xs = INP == IN_F8 ? a.seg[sgi].dscale * op_scale : op_scale;   // stored value -> scaled operand
       for (int b = 0; b < NB; ++b) {
         const uint32_t p = opos & 1u;
         if (opos >= 2 && !dead && !mbar_wait_fast(bar(B_OP_EMPTY + p), ((opos >> 1) - 1) & 1u)) dead = true;
         uint8_t* op = base + lay.op + p * BLK16;
-        for (int hf = 0; hf < 2; ++hf) {
+        // (x - c) s = fma(x, s, -c s) rounds once like the subtraction does (s a power of two; for
+        // FP8, x = code and s = block scale x s, exact because the code has 4 significant bits
+        // and the scale is taken as given). All loads of a stage first (they overlap), then the
+        // conversions and stores; the stage goes back to the producer only after the stores.
+        auto put8 = [&](int r, int fb, const float (&xv)[8], bool valid) {
+          float v[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = valid ? fmaf(xv[e], xs, -sShift[64 * b + fb + e] * op_scale) : 0.f;
+          *reinterpret_cast<uint4*>(op + static_cast<uint32_t>(r >> 3) * 1024u +
+                                    sw128(static_cast<uint32_t>(r & 7), static_cast<uint32_t>(fb) * 2u)) =
+              make_uint4(pack2<FMT>(v[0], v[1]), pack2<FMT>(v[2], v[3]), pack2<FMT>(v[4], v[5]),
+                         pack2<FMT>(v[6], v[7]));
+        };
+        for (int hf = 0; hf < SPB; ++hf) {
           const uint32_t s = spos % a.ns1;
           if (!dead && !mbar_wait_fast(bar(B_S1_FULL + s), (spos / a.ns1) & 1u)) dead = true;
           const uint8_t* stg = base + lay.st1 + s * STG;
-          const int fb = 32 * hf + 8 * cq;   // first feature of the piece within the block
-          float cs[8];
+          if constexpr (INP == IN_F32) {
+            // 128-byte rows of 32 features: thread = (8-feature piece cq, rows rb + 32 k)
+            const int cq = ct & 3, rb = ct >> 2;
+            const int fb = 32 * hf + 8 * cq;
+            float4 x[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) cs[e] = -sShift[64 * b + fb + e] * op_scale;
-          // (x - c) s = fma(x, s, -c s) rounds once like the subtraction does (s a power of two).
-          // All loads of the stage first (they overlap), then the conversions and stores; the
-          // stage goes back to the producer only after the stores that use every loaded value.
-          float4 x[8];
+            for (int k = 0; k < 4; ++k) {
+              const int r = rb + 32 * k;
+              x[2 * k] = *reinterpret_cast<const float4*>(stg + r * 128 + (((2 * cq) ^ (r & 7)) << 4));
+              x[2 * k + 1] = *reinterpret_cast<const float4*>(stg + r * 128 + (((2 * cq + 1) ^ (r & 7)) << 4));
+            }
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int r = rb + 32 * k;
-            x[2 * k] = *reinterpret_cast<const float4*>(stg + r * 128 + (((2 * cq) ^ (r & 7)) << 4));
-            x[2 * k + 1] = *reinterpret_cast<const float4*>(stg + r * 128 + (((2 * cq + 1) ^ (r & 7)) << 4));
-          }
+            for (int k = 0; k < 4; ++k) {
+              const int r = rb + 32 * k;
+              const float xv[8] = {x[2 * k].x, x[2 * k].y, x[2 * k].z, x[2 * k].w,
+                                   x[2 * k + 1].x, x[2 * k + 1].y, x[2 * k + 1].z, x[2 * k + 1].w};
+              put8(r, fb, xv, row0 + r < mseg);
+            }
+          } else if constexpr (INP == IN_BF16) {
+            // 128-byte rows of 64 features: thread = (16-byte chunk c8 = 8 features, rows rb + 16 k)
+            const int c8 = ct & 7, rb = ct >> 3;
+            uint4 x[8];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int r = rb + 32 * k;
-            const bool valid = row0 + r < mseg;
-            const float xv[8] = {x[2 * k].x, x[2 * k].y, x[2 * k].z, x[2 * k].w,
-                                 x[2 * k + 1].x, x[2 * k + 1].y, x[2 * k + 1].z, x[2 * k + 1].w};
-            float v[8];
+            for (int k = 0; k < 8; ++k) {
+              const int r = rb + 16 * k;
+              x[k] = *reinterpret_cast<const uint4*>(stg + r * 128 + ((c8 ^ (r & 7)) << 4));
+            }
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = valid ? fmaf(xv[e], op_scale, cs[e]) : 0.f;
-            *reinterpret_cast<uint4*>(op + static_cast<uint32_t>(r >> 3) * 1024u +
-                                      sw128(static_cast<uint32_t>(r & 7), static_cast<uint32_t>(fb) * 2u)) =
-                make_uint4(pack2<FMT>(v[0], v[1]), pack2<FMT>(v[2], v[3]), pack2<FMT>(v[4], v[5]),
-                           pack2<FMT>(v[6], v[7]));
+            for (int k = 0; k < 8; ++k) {
+              const int r = rb + 16 * k;
+              const uint32_t w[4] = {x[k].x, x[k].y, x[k].z, x[k].w};
+              float xv[8];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                xv[2 * e] = __uint_as_float(w[e] << 16);
+                xv[2 * e + 1] = __uint_as_float(w[e] & 0xFFFF0000u);
+              }
+              put8(r, 8 * c8, xv, row0 + r < mseg);
+            }
+          } else {
+            // 64-byte rows of 64 codes, unswizzled: thread = (16-code chunk c4, rows rb + 32 k)
+            const int c4 = ct & 3, rb = ct >> 2;
+            uint4 x[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x[k] = *reinterpret_cast<const uint4*>(stg + (rb + 32 * k) * 64 + c4 * 16);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const int r = rb + 32 * k;
+              const uint32_t w[4] = {x[k].x, x[k].y, x[k].z, x[k].w};
+              float xv[16];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float2 lo = fp8x2_e4m3_to_float2(static_cast<uint16_t>(w[e] & 0xFFFFu));
+                const float2 hi = fp8x2_e4m3_to_float2(static_cast<uint16_t>(w[e] >> 16));
+                xv[4 * e] = lo.x;
+                xv[4 * e + 1] = lo.y;
+                xv[4 * e + 2] = hi.x;
+                xv[4 * e + 3] = hi.y;
+              }
+              const bool valid = row0 + r < mseg;
+              const float x0[8] = {xv[0], xv[1], xv[2], xv[3], xv[4], xv[5], xv[6], xv[7]};
+              const float x1[8] = {xv[8], xv[9], xv[10], xv[11], xv[12], xv[13], xv[14], xv[15]};
+              put8(r, 16 * c4, x0, valid);
+              put8(r, 16 * c4 + 8, x1, valid);
+            }
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(bar(B_S1_EMPTY + s));
@@ -973,7 +1036,7 @@ bool grp_config(int64_t n, int l, int L, int fmt, GrpConfig* cfg) {
     snprintf(g_grp_reason, sizeof(g_grp_reason), "cooperative launch is not available");
     return false;
   }
-  const auto kern = fmt == FMT_F16 ? sketch_grp_kernel<FMT_F16> : sketch_grp_kernel<FMT_BF16>;
+  const auto kern = fmt == FMT_F16 ? sketch_grp_kernel<FMT_F16, IN_F32> : sketch_grp_kernel<FMT_BF16, IN_F32>;
   cudaFuncAttributes fa{};
   if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
     cudaGetLastError();
@@ -1023,7 +1086,22 @@ bool grp_config(int64_t n, int l, int L, int fmt, GrpConfig* cfg) {
     }
   }
   if (best == 0.0) return false;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess) {
+  // every storage format's variant of the kernel (same code size and static shared memory)
+  const bool attr_ok =
+      fmt == FMT_F16
+          ? (cudaFuncSetAttribute(sketch_grp_kernel<FMT_F16, IN_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_max) == cudaSuccess &&
+             cudaFuncSetAttribute(sketch_grp_kernel<FMT_F16, IN_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_max) == cudaSuccess &&
+             cudaFuncSetAttribute(sketch_grp_kernel<FMT_F16, IN_F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_max) == cudaSuccess)
+          : (cudaFuncSetAttribute(sketch_grp_kernel<FMT_BF16, IN_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_max) == cudaSuccess &&
+             cudaFuncSetAttribute(sketch_grp_kernel<FMT_BF16, IN_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_max) == cudaSuccess &&
+             cudaFuncSetAttribute(sketch_grp_kernel<FMT_BF16, IN_F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_max) == cudaSuccess);
+  if (!attr_ok) {
     cudaGetLastError();
     snprintf(g_grp_reason, sizeof(g_grp_reason), "cannot raise the shared-memory limit");
     return false;
@@ -1062,21 +1140,27 @@ cudaError_t grp_pass(const State& s, const TcWork& w, const TcPending& pend, cud
   GrpArgs args;
   std::memset(&args, 0, sizeof(args));
   const GrpConfig& cfg = w.grp;
+  const int inp = pend.dtype == SPCA_BF16 ? IN_BF16 : (pend.dtype == SPCA_F8E4M3 ? IN_F8 : IN_F32);
+  if (pend.dtype != SPCA_F32 && inp == IN_F32) return cudaSuccess;   // a storage format this kernel does not read
+  const int es = inp == IN_F32 ? 4 : (inp == IN_BF16 ? 2 : 1);
   int64_t tiles = 0;
   for (int i = 0; i < pend.nseg; ++i) {
     const uintptr_t addr = reinterpret_cast<uintptr_t>(pend.rows[i]);
-    if ((addr & 15u) != 0 || (pend.ld[i] % 4) != 0) return cudaSuccess;
+    if ((addr & 15u) != 0 || (pend.ld[i] * es) % 16 != 0) return cudaSuccess;
     cuuint64_t dims[2] = {static_cast<cuuint64_t>(s.n), static_cast<cuuint64_t>(pend.m[i])};
-    cuuint64_t strides[1] = {static_cast<cuuint64_t>(pend.ld[i]) * 4};
-    cuuint32_t box[2] = {32, GR_ROWS};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(pend.ld[i]) * es};
+    cuuint32_t box[2] = {inp == IN_F32 ? 32u : 64u, GR_ROWS};
     cuuint32_t estr[2] = {1, 1};
-    const CUresult r = encode_fn()(&args.maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                                   const_cast<float*>(pend.rows[i]), dims, strides, box, estr,
-                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+    const CUtensorMapDataType dt = inp == IN_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : (inp == IN_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
+    const CUresult r = encode_fn()(&args.maps[i], dt, 2, const_cast<void*>(pend.rows[i]), dims, strides, box, estr,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                   inp == IN_F8 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaSuccess;
     args.seg[i].m = pend.m[i];
     args.seg[i].gout = pend.gout[i];
+    args.seg[i].dscale = inp == IN_F8 ? pend.dscale[i] : 1.f;
     args.seg[i].tile0 = tiles;
     tiles += (pend.m[i] + GR_ROWS - 1) / GR_ROWS;
   }
@@ -1128,8 +1212,14 @@ cudaError_t grp_pass(const State& s, const TcWork& w, const TcPending& pend, cud
   lc.attrs = at;
   lc.numAttrs = 1;
   prof->begin(SPCA_K_TC_SKETCH, st);
-  e = w.fmt == FMT_F16 ? cudaLaunchKernelEx(&lc, sketch_grp_kernel<FMT_F16>, args)
-                       : cudaLaunchKernelEx(&lc, sketch_grp_kernel<FMT_BF16>, args);
+  if (w.fmt == FMT_F16)
+    e = inp == IN_F32    ? cudaLaunchKernelEx(&lc, sketch_grp_kernel<FMT_F16, IN_F32>, args)
+        : inp == IN_BF16 ? cudaLaunchKernelEx(&lc, sketch_grp_kernel<FMT_F16, IN_BF16>, args)
+                         : cudaLaunchKernelEx(&lc, sketch_grp_kernel<FMT_F16, IN_F8>, args);
+  else
+    e = inp == IN_F32    ? cudaLaunchKernelEx(&lc, sketch_grp_kernel<FMT_BF16, IN_F32>, args)
+        : inp == IN_BF16 ? cudaLaunchKernelEx(&lc, sketch_grp_kernel<FMT_BF16, IN_BF16>, args)
+                         : cudaLaunchKernelEx(&lc, sketch_grp_kernel<FMT_BF16, IN_F8>, args);
   prof->end(SPCA_K_TC_SKETCH, st);
   if (e != cudaSuccess) return e;
   *used = true;

@@ -29,6 +29,7 @@
 // runs the same number of them), so no wait can hang the GPU.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cstdio>
@@ -633,13 +634,20 @@ __global__ void omega_from_q_op_kernel(const double* __restrict__ Q, int64_t n, 
 // the Gaussian Omega, 1 for an orthonormal one), so
 // s = 2^floor(log2(2^14 / (1.25 ||omega_c|| max_r ||a_r - c||))) keeps s G below 2^14 with
 // four-fold headroom under the FP16 maximum.
-__global__ void row_norm_max_kernel(const float* __restrict__ rows, int64_t m, int64_t n, int64_t ld,
+__device__ __forceinline__ float stored_value(const float* p, int64_t i, float) { return p[i]; }
+__device__ __forceinline__ float stored_value(const __nv_bfloat16* p, int64_t i, float) { return __bfloat162float(p[i]); }
+__device__ __forceinline__ float stored_value(const __nv_fp8_e4m3* p, int64_t i, float scale) {
+  return static_cast<float>(p[i]) * scale;
+}
+
+template <typename T>
+__global__ void row_norm_max_kernel(const T* __restrict__ rows, float dscale, int64_t m, int64_t n, int64_t ld,
                                     const float* __restrict__ shift, unsigned int* __restrict__ out_bits) {
   __shared__ float red[256];   // only a power of two is taken from the result: FP32 suffices
   for (int64_t r = blockIdx.x; r < m; r += gridDim.x) {
     float s = 0.f;
     for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-      const float d = rows[r * ld + j] - shift[j];
+      const float d = stored_value(rows, r * ld + j, dscale) - shift[j];
       s = fmaf(d, d, s);
     }
     red[threadIdx.x] = s;
@@ -760,13 +768,22 @@ cudaError_t launch_omega_from_q_op(int fmt, const double* Q, int64_t n, int64_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_op_scale(const float* rows, int64_t m, int64_t n, int64_t ld, const float* shift,
-                            unsigned int* bits, float* scale, double omega_norm, cudaStream_t st, Prof* prof) {
+cudaError_t launch_op_scale(const void* rows, int dtype, float dscale, int64_t m, int64_t n, int64_t ld,
+                            const float* shift, unsigned int* bits, float* scale, double omega_norm, cudaStream_t st,
+                            Prof* prof) {
   if (prof) prof->begin(SPCA_K_SHIFT, st);
   cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
-  const int blocks = static_cast<int>(m < 152 * 8 ? m : 152 * 8);
-  row_norm_max_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(rows, m, n, ld, shift, bits);
+  const int blocks = static_cast<int>(m < 152 * 8 ? m : 152 * 8) < 1 ? 1 : static_cast<int>(m < 152 * 8 ? m : 152 * 8);
+  if (dtype == SPCA_BF16)
+    row_norm_max_kernel<<<blocks, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(rows), 1.f, m, n, ld, shift, bits);
+  else if (dtype == SPCA_F8E4M3)
+    row_norm_max_kernel<<<blocks, 256, 0, st>>>(static_cast<const __nv_fp8_e4m3*>(rows), dscale, m, n, ld, shift,
+                                                 bits);
+  else if (dtype == SPCA_F32)
+    row_norm_max_kernel<<<blocks, 256, 0, st>>>(static_cast<const float*>(rows), 1.f, m, n, ld, shift, bits);
+  else
+    return cudaErrorInvalidValue;
   op_scale_kernel<<<1, 1, 0, st>>>(bits, omega_norm, scale);
   if (prof) {
     prof->launches[SPCA_K_SHIFT] += 1;
@@ -782,7 +799,7 @@ cudaError_t tc_pass(const State& s, const TcWork& w, const TcPending& pend, cuda
   int64_t tiles = 0;
   bool vec_ok = true;
   for (int i = 0; i < pend.nseg; ++i) {
-    args.seg[i].rows = pend.rows[i];
+    args.seg[i].rows = static_cast<const float*>(pend.rows[i]);
     args.seg[i].m = pend.m[i];
     args.seg[i].ld = pend.ld[i];
     args.seg[i].gout = pend.gout[i];

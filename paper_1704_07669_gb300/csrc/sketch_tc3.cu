@@ -950,7 +950,7 @@ cudaError_t tc3_pass(const State& s, const TcWork& w, const TcPending& pend, cud
     cuuint32_t box[2] = {64, T3_ROWS};
     cuuint32_t estr[2] = {1, 1};
     const CUresult r = encode_fn()(&args.maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                                   const_cast<float*>(pend.rows[i]), dims, strides, box, estr,
+                                   const_cast<void*>(pend.rows[i]), dims, strides, box, estr,
                                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaSuccess;

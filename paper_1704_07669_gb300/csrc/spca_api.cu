@@ -230,6 +230,13 @@ spca_status flush_tc(spca_session* s) {
   if (!s->tc || s->pend.nseg == 0) return SPCA_OK;
   bool used = false;
   if (s->tcw.use_grp) CU(grp_pass(s->state(), s->tcw, s->pend, s->stream, &s->prof, &used));
+  if (!used && s->pend.dtype != SPCA_F32) {   // the other tensor-core kernels read FP32 rows only
+    s->pend.nseg = 0;
+    s->pend.rows_total = 0;
+    return fail(s, SPCA_E_UNSUPPORTED,
+                "BF16 and FP8 rows reach the tensor cores through the grouped kernel only, which needs 16-byte "
+                "aligned row blocks whose rows are a multiple of 16 bytes apart");
+  }
   if (!used && s->tcw.v3) CU(tc3_pass(s->state(), s->tcw, s->pend, s->stream, &s->prof, &used));
   if (!used) {
     if (!s->tcw.cfg_ok) {
@@ -256,20 +263,23 @@ spca_status run_piece(spca_session* s, const void* rows, int64_t m, int64_t ld, 
     s->shift_set = true;
   }
   if (s->tc && s->tcw.fmt == 1 && !s->scale_set) {
-    CU(launch_op_scale(static_cast<const float*>(rows), m, s->n, ld, s->shift, s->tcw.scale_bits, s->tcw.scale,
+    CU(launch_op_scale(rows, dtype, scale, m, s->n, ld, s->shift, s->tcw.scale_bits, s->tcw.scale,
                        s->omega_orth ? 1.0 : std::sqrt(static_cast<double>(s->n)), s->stream, &s->prof));
     s->scale_set = true;
   }
   if (s->tc) {
-    if (s->pend.nseg == kTcPendingMax) {
+    // one launch reads one storage format: a block of another format flushes the batch first
+    if (s->pend.nseg == kTcPendingMax || (s->pend.nseg > 0 && s->pend.dtype != dtype)) {
       spca_status st = flush_tc(s);
       if (st != SPCA_OK) return st;
     }
     const int i = s->pend.nseg++;
-    s->pend.rows[i] = static_cast<const float*>(rows);
+    s->pend.dtype = dtype;
+    s->pend.rows[i] = rows;
     s->pend.m[i] = m;
     s->pend.ld[i] = ld;
     s->pend.gout[i] = G_out;
+    s->pend.dscale[i] = scale;
     s->pend.rows_total += m;
     s->m += m;
     if (!defer || s->pend.rows_total >= kTcPendingRows) return flush_tc(s);
@@ -525,7 +535,11 @@ namespace {
 
 // Staged rows are laid out with a leading dimension rounded up to 4 elements, so that every
 // staged FP32 row starts on a 16-byte boundary (a tensor map can describe it).
-int64_t stage_ld(int64_t n) { return ((n + 3) / 4) * 4; }
+// leading dimension of the staged copies: rows a multiple of 16 bytes apart (tensor maps)
+int64_t stage_ld(int64_t n, size_t es) {
+  const int64_t q = es >= 16 ? 1 : static_cast<int64_t>(16 / es);
+  return ((n + q - 1) / q) * q;
+}
 
 // The two pinned host buffers and two device buffers of the staged paths (made once).
 spca_status ensure_staging(spca_session* s, size_t row_bytes) {
@@ -567,8 +581,10 @@ spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t 
   }
   if (rows_on_device != 0 && rows_on_device != 1) return fail(s, SPCA_E_INVALID, "rows_on_device must be 0 or 1");
   CU(cudaSetDevice(s->device));
-  if (s->tc && dtype != SPCA_F32)
-    return fail(s, SPCA_E_UNSUPPORTED, "the tensor-core pass reads FP32 rows in this build (dtype %d)", dtype);
+  if (s->tc && dtype != SPCA_F32 && !(s->tcw.use_grp && (dtype == SPCA_BF16 || dtype == SPCA_F8E4M3)))
+    return fail(s, SPCA_E_UNSUPPORTED,
+                "this tensor-core session reads FP32 rows (the grouped kernel, which also reads BF16 and FP8 rows, "
+                "does not take n = %lld, l = %d)", (long long)s->n, s->l);
   const int64_t mb = s->simt.mb;
   if (rows_on_device) {
     cudaPointerAttributes attr;
@@ -577,10 +593,11 @@ spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t 
     cudaGetLastError();
     if (!ok_attr || (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged))
       return fail(s, SPCA_E_INVALID, "rows_on_device=1 but rows is not a device pointer");
-    // rows a tensor map cannot describe (not 16-byte aligned, or ld not a multiple of 4) go
-    // through the staging buffers when only the tensor-map kernel takes the shape
-    const bool tma_ok = (reinterpret_cast<uintptr_t>(rows) % 16 == 0) && (ld % 4 == 0);
-    if (!(s->tc && s->tcw.use_grp && !s->tcw.cfg_ok && !tma_ok)) {
+    // rows a tensor map cannot describe (not 16-byte aligned, or rows not a multiple of 16
+    // bytes apart) go through the staging buffers when only the tensor-map kernel reads them
+    const bool tma_ok = (reinterpret_cast<uintptr_t>(rows) % 16 == 0) && ((ld * static_cast<int64_t>(es)) % 16 == 0);
+    const bool grp_only = s->tc && s->tcw.use_grp && (!s->tcw.cfg_ok || dtype != SPCA_F32);
+    if (!(grp_only && !tma_ok)) {
       for (int64_t r0 = 0; r0 < m_i; r0 += mb) {
         const int64_t mr = (m_i - r0) < mb ? (m_i - r0) : mb;
         const char* base = static_cast<const char*>(rows) + size_t(r0) * ld * es;
@@ -591,7 +608,7 @@ spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t 
     }
     st = flush_tc(s);   // blocks batched before these stay in order
     if (st != SPCA_OK) return st;
-    const int64_t lds = stage_ld(s->n);
+    const int64_t lds = stage_ld(s->n, es);
     const size_t row_st = size_t(lds) * es;
     st = ensure_staging(s, row_st);
     if (st != SPCA_OK) return st;
@@ -612,7 +629,7 @@ spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t 
   // Host rows: copy pieces through two staging buffers so the copy of piece i+1
   // overlaps the kernels of piece i.
   const size_t row_bytes = size_t(s->n) * es;
-  const int64_t lds = stage_ld(s->n);
+  const int64_t lds = stage_ld(s->n, es);
   const size_t row_st = size_t(lds) * es;
   st = ensure_staging(s, row_st);
   if (st != SPCA_OK) return st;

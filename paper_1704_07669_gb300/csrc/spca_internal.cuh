@@ -152,10 +152,12 @@ constexpr int64_t kTcPendingRows = 65536;
 struct TcPending {
   int nseg = 0;
   int64_t rows_total = 0;
-  const float* rows[kTcPendingMax];
+  int dtype = 0;                  // spca_dtype of every pending block (FP32 unless the grouped kernel runs)
+  const void* rows[kTcPendingMax];
   int64_t m[kTcPendingMax];
   int64_t ld[kTcPendingMax];
   float* gout[kTcPendingMax];
+  float dscale[kTcPendingMax];    // FP8 blocks: the block scale; else 1
 };
 
 // Whether (n, L) fits the fused kernel; fills the launch configuration.
@@ -165,8 +167,9 @@ cudaError_t launch_omega_op(int fmt, uint64_t seed, int64_t n, int64_t npad, int
                             cudaStream_t st, Prof* prof);
 // FP16 form: s = power of two from the largest shifted row norm of the given rows and a bound
 // on the norm of Omega's columns
-cudaError_t launch_op_scale(const float* rows, int64_t m, int64_t n, int64_t ld, const float* shift,
-                            unsigned int* bits, float* scale, double omega_norm, cudaStream_t st, Prof* prof);
+cudaError_t launch_op_scale(const void* rows, int dtype, float dscale, int64_t m, int64_t n, int64_t ld,
+                            const float* shift, unsigned int* bits, float* scale, double omega_norm, cudaStream_t st,
+                            Prof* prof);
 cudaError_t tc_pass(const State& s, const TcWork& w, const TcPending& pend, cudaStream_t st, Prof* prof);
 // H partials -> FP64 state and Gram partials -> state, for a launch of ncl clusters
 cudaError_t launch_tc_finish(const State& s, const TcWork& w, int ncl, int64_t npad, int nctas, cudaStream_t st,
