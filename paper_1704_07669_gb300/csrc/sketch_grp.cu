@@ -86,8 +86,9 @@ __host__ __device__ inline int gram_pairs(int l) {
 }
 
 // ns1: FP32 stages; nbmax: blocks per CTA; gs: 1, or 2 when G' is split (hi + lo); rpc: reducer
-// rows per CTA at most
-__host__ __device__ inline GrpLayout grp_layout(int L, int l, int nbmax, int ns1, int gs, int rpc) {
+// rows per CTA at most; npairs: the reducers' Gram blocks (0: the Gram matrix is formed after
+// the launch from the G' rows)
+__host__ __device__ inline GrpLayout grp_layout(int L, int npairs, int nbmax, int ns1, int gs, int rpc) {
   GrpLayout t;
   uint32_t o = 0;
   t.st1 = o; o += static_cast<uint32_t>(ns1) * STG;
@@ -97,7 +98,7 @@ __host__ __device__ inline GrpLayout grp_layout(int L, int l, int nbmax, int ns1
   t.p2 = o; o += static_cast<uint32_t>(NS2) * P2U;
   t.shift = o; o += static_cast<uint32_t>(nbmax) * 64u * 4u;
   t.red = o; o += ((static_cast<uint32_t>(rpc) * static_cast<uint32_t>(L) * 4u) + 15u) & ~15u;
-  t.gram = o; o += static_cast<uint32_t>(gram_pairs(l)) * 8u * 8u;   // double-float Gram accumulators
+  t.gram = o; o += static_cast<uint32_t>(npairs) * 8u * 8u;   // double-float Gram accumulators
   o = (o + 15u) & ~15u;
   t.bars = o; o += 80u * 8u;   // BAR_SLOTS
   t.total = o + 1024u;   // the base is rounded up to 1024 bytes in the kernel
@@ -132,6 +133,8 @@ struct GrpArgs {
   uint16_t* gbuf;               // per group: RING_R slots x gs x 2 x L x 64 16-bit
   unsigned* cnt;                // per group: RING_R x 3 counters (arrived, reduced, loaded)
   const float* scale;
+  int npairs;                   // the reducers' Gram blocks (gram_pairs(l)), or 0 with gfull
+  float* gfull;                 // npairs == 0: G' rows of the launch, tile t at rows 128 t (ld L), unscaled
   float* Hpart;                 // per group: nbt*64 x L (FP32)
   double* gram_part;            // per CTA: L x L
   double* sG_part;              // per CTA: L
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
   const int NB = blk1 - blk0;   // >= 1: the configuration keeps S <= the number of blocks
   const int q0 = (32 * j) / S, q1 = (32 * (j + 1)) / S;   // reducer row quads
   const int rpc = 4 * (q1 - q0);
-  const GrpLayout lay = grp_layout(L, l, a.nbmax, a.ns1, GS, (32 + S - 1) / S * 4);
+  const GrpLayout lay = grp_layout(L, a.npairs, a.nbmax, a.ns1, GS, (32 + S - 1) / S * 4);
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + lay.bars);
   auto bar = [&](int i) { return su32(&bars[i]); };
   float* sShift = reinterpret_cast<float*>(base + lay.shift);
@@ -700,7 +703,7 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
     // p = rt + k RED_T is this thread's; its 8 entries are double-float pairs in shared memory
     // (sGram[(k RED_T + rt) 8 + e]). A row of G' then costs a 16-byte and an 8-byte load and
     // feeds 8 independent product-sums.
-    const int npairs = gram_pairs(l);
+    const int npairs = a.npairs;
     auto block_ab = [&](int pidx, int& ba, int& bb) {
       ba = static_cast<int>((sqrtf(4.f * static_cast<float>(pidx) + 1.f) - 1.f) * 0.5f);
       while (ba * (ba + 1) > pidx) --ba;
@@ -821,6 +824,13 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
       if (rt == 0) GRP_TRACE(i, 14);
       if (rt < l)
         for (int rr = 0; rr < rpc; ++rr) sg.add(sRed[rr * L + rt]);
+      if (a.gfull != nullptr) {   // the Gram matrix is formed after the launch from these rows
+        float* gf = a.gfull + (tile * GR_ROWS + 4 * q0) * L;
+        for (int it = rt; it < rpc * L; it += RED_T) {
+          const int rr = it / L, c = it % L;
+          gf[rr * L + c] = c < l ? sRed[rr * L + c] * inv_s : 0.f;
+        }
+      }
       if (a.seg[sgi].gout != nullptr) {
         for (int it = rt; it < rpc * l; it += RED_T) {
           const int rr = it / l, c = it % l;
@@ -1003,6 +1013,75 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
   }
 }
 
+// The Gram matrix and nothing else from the G' rows of a launch (when l is too large for the
+// reducers to hold its blocks): block p of the grid sums rows [r0, r1) of its share in the
+// same 4 x 2 double-float blocks of the lower triangle as the reducers, 32 rows staged in
+// shared memory at a time, and leaves gram_part[p] (both triangles, FP64) with sG_part[p] = 0.
+constexpr int GRR_T = 512;
+constexpr int GRR_ROWS = 32;
+__global__ void __launch_bounds__(GRR_T) gram_rows_kernel(const float* __restrict__ G, int64_t rows, int l, int L,
+                                                          double* __restrict__ gram_part,
+                                                          double* __restrict__ sG_part) {
+  extern __shared__ __align__(16) float gr_s[];   // GRR_ROWS x L
+  const int npairs = gram_pairs(l);
+  const int64_t per = (rows + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * per;
+  const int64_t r1 = r0 + per < rows ? r0 + per : rows;
+  constexpr int KMAX = 3;   // blocks per thread: gram_pairs(l) <= 3 x 512 for l <= 128 (na = 32: 1056)
+  F2Prod acc[KMAX][8];
+  int ba[KMAX], bb[KMAX];
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    const int pidx = threadIdx.x + k * GRR_T;
+    ba[k] = -1;
+    bb[k] = 0;
+    if (pidx < npairs) {
+      int a = static_cast<int>((sqrtf(4.f * static_cast<float>(pidx) + 1.f) - 1.f) * 0.5f);
+      while (a * (a + 1) > pidx) --a;
+      while ((a + 1) * (a + 2) <= pidx) ++a;
+      ba[k] = a;
+      bb[k] = pidx - a * (a + 1);
+    }
+  }
+  for (int64_t c0 = r0; c0 < r1; c0 += GRR_ROWS) {
+    const int nr = static_cast<int>(r1 - c0 < GRR_ROWS ? r1 - c0 : GRR_ROWS);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * L / 4; e += GRR_T)
+      reinterpret_cast<float4*>(gr_s)[e] = reinterpret_cast<const float4*>(G + c0 * L)[e];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      if (ba[k] < 0) continue;
+      for (int r = 0; r < nr; ++r) {
+        const float4 xa = *reinterpret_cast<const float4*>(gr_s + r * L + 4 * ba[k]);
+        const float2 xb = *reinterpret_cast<const float2*>(gr_s + r * L + 2 * bb[k]);
+        const float va[4] = {xa.x, xa.y, xa.z, xa.w}, vb[2] = {xb.x, xb.y};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) acc[k][u * 2 + v].add_prod(va[u], vb[v]);
+      }
+    }
+  }
+  const int LL = L * L;
+  double* out = gram_part + static_cast<int64_t>(blockIdx.x) * LL;
+  for (int e = threadIdx.x; e < LL; e += GRR_T) out[e] = 0.0;
+  for (int c = threadIdx.x; c < L; c += GRR_T) sG_part[static_cast<int64_t>(blockIdx.x) * L + c] = 0.0;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    if (ba[k] < 0) continue;
+    for (int u = 0; u < 4; ++u)
+      for (int v = 0; v < 2; ++v) {
+        const int c1 = 4 * ba[k] + u, c2 = 2 * bb[k] + v;
+        if (c1 >= l || c2 > c1) continue;
+        const double val = static_cast<double>(acc[k][u * 2 + v].hi) + static_cast<double>(acc[k][u * 2 + v].lo);
+        out[c1 * L + c2] = val;
+        out[c2 * L + c1] = val;
+      }
+  }
+}
+
 thread_local char g_grp_reason[192] = "";
 
 }  // namespace
@@ -1022,10 +1101,10 @@ bool grp_config(int64_t n, int l, int L, int fmt, GrpConfig* cfg) {
     snprintf(g_grp_reason, sizeof(g_grp_reason), "padded l = %d exceeds 128", L);
     return false;
   }
-  if (gram_pairs(l) > GRP_MAX_PAIRS) {
-    snprintf(g_grp_reason, sizeof(g_grp_reason), "l = %d: the Gram blocks exceed the reducers' share", l);
-    return false;
-  }
+  // the reducers hold the Gram blocks of l <= 76; larger l forms the Gram matrix after each
+  // launch from the G' rows the reducers write out
+  const bool gram_in = gram_pairs(l) <= GRP_MAX_PAIRS;
+  const int npairs = gram_in ? gram_pairs(l) : 0;
   const int gs = fmt == FMT_F16 ? 2 : 1;
   int dev = 0, sms = 0, optin = 0, coop = 0;
   cudaGetDevice(&dev);
@@ -1061,8 +1140,8 @@ bool grp_config(int64_t n, int l, int L, int fmt, GrpConfig* cfg) {
     const int nd1 = opt_nd1[oi], nf = opt_nf[oi];
     const int rpc = (32 + S - 1) / S * 4;
     int ns1 = 0;
-    for (int k = 16; k >= 3; --k) {
-      if (static_cast<int>(grp_layout(L, l, nbmax, k, gs, rpc).total) <= smem_max) {
+    for (int k = 16; k >= 2; --k) {
+      if (static_cast<int>(grp_layout(L, npairs, nbmax, k, gs, rpc).total) <= smem_max) {
         ns1 = k;
         break;
       }
@@ -1082,7 +1161,8 @@ bool grp_config(int64_t n, int l, int L, int fmt, GrpConfig* cfg) {
       pick.ns1 = ns1;
       pick.nd1 = nd1;
       pick.nf = nf;
-      pick.smem = grp_layout(L, l, nbmax, ns1, gs, rpc).total;
+      pick.smem = grp_layout(L, npairs, nbmax, ns1, gs, rpc).total;
+      pick.gram_in = gram_in;
     }
   }
   if (best == 0.0) return false;
@@ -1126,6 +1206,14 @@ size_t grp_gbuf_elems(const GrpConfig& c, int L, int fmt) {
   return static_cast<size_t>(c.NG) * RING_R * (fmt == FMT_F16 ? 2 : 1) * 2 * L * 64;
 }
 size_t grp_cnt_elems(const GrpConfig& c) { return static_cast<size_t>(c.NG) * RING_R * 3; }
+// G' rows of one launch when the Gram matrix is formed after it: the tiles of every block a
+// launch can hold (the batch closes at kTcPendingRows rows; a block has at most
+// max_block_rows rows and one ragged tile)
+size_t grp_gfull_rows(const GrpConfig& c, int64_t max_block_rows) {
+  if (c.gram_in) return 0;
+  const int64_t mb = max_block_rows > kTcPendingRows ? max_block_rows : kTcPendingRows;
+  return static_cast<size_t>(mb + (kTcPendingRows + GR_ROWS - 1) / GR_ROWS * GR_ROWS + kTcPendingMax * GR_ROWS);
+}
 
 // One cooperative launch over the pending row blocks; *used = false (nothing launched) when a
 // block cannot be described by a tensor map.
@@ -1164,6 +1252,7 @@ cudaError_t grp_pass(const State& s, const TcWork& w, const TcPending& pend, cud
     args.seg[i].tile0 = tiles;
     tiles += (pend.m[i] + GR_ROWS - 1) / GR_ROWS;
   }
+  if (!cfg.gram_in && tiles * GR_ROWS > w.gfull_rows) return cudaErrorInvalidValue;   // sized at creation
   const int NG = static_cast<int>(tiles < cfg.NG ? tiles : cfg.NG);
   args.nseg = pend.nseg;
   args.ntiles = tiles;
@@ -1187,6 +1276,8 @@ cudaError_t grp_pass(const State& s, const TcWork& w, const TcPending& pend, cud
   args.gbuf = w.gbuf;
   args.cnt = w.cnt;
   args.scale = w.fmt == FMT_F16 ? w.scale : nullptr;
+  args.npairs = cfg.gram_in ? gram_pairs(s.l) : 0;
+  args.gfull = cfg.gram_in ? nullptr : w.gfull;
   args.Hpart = w.Hpart;
   args.gram_part = w.gram_part;
   args.sG_part = w.sG_part;
@@ -1246,7 +1337,21 @@ cudaError_t grp_pass(const State& s, const TcWork& w, const TcPending& pend, cud
     }
   }
 #endif
-  return launch_tc_finish(s, w, NG, static_cast<int64_t>(cfg.nbt) * 64, NG * cfg.S, st, prof);
+  e = launch_tc_finish(s, w, NG, static_cast<int64_t>(cfg.nbt) * 64, NG * cfg.S, st, prof);
+  if (e != cudaSuccess || cfg.gram_in) return e;
+  // the Gram matrix from the launch's G' rows (their partials reuse the reducers' slots, which
+  // launch_tc_finish has consumed)
+  const int64_t grows = tiles * GR_ROWS;
+  int64_t P = (grows + 255) / 256;
+  if (P > static_cast<int64_t>(NG) * cfg.S) P = static_cast<int64_t>(NG) * cfg.S;
+  if (P < 1) P = 1;
+  prof->begin(SPCA_K_GRAM_ACCUM, st);
+  gram_rows_kernel<<<static_cast<unsigned>(P), GRR_T, sizeof(float) * GRR_ROWS * s.L, st>>>(w.gfull, grows, s.l, s.L,
+                                                                                            w.gram_part, w.sG_part);
+  e = launch_gram_accum(w.gram_part, w.sG_part, static_cast<int>(P), s.L, s.gram, s.sG, st);
+  prof->end(SPCA_K_GRAM_ACCUM, st);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
 }
 
 }  // namespace spca

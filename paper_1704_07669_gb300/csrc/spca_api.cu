@@ -205,7 +205,7 @@ void free_all(spca_session* s) {
                   s->fin.sig, s->fin.info, s->fin.flip, s->fin.Tu, s->fin.M, s->fin.mrow, s->fin_sigma, s->fin_V,
                   s->dstage[0], s->dstage[1],
                   s->tcw.om16, s->tcw.Hpart, s->tcw.gram_part, s->tcw.sG_part, s->tcw.scale, s->tcw.scale_bits,
-                  s->tcw.img, s->tcw.zero8k, s->tcw.part, s->tcw.gbuf, s->tcw.cnt};
+                  s->tcw.img, s->tcw.zero8k, s->tcw.part, s->tcw.gbuf, s->tcw.cnt, s->tcw.gfull};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < 2; ++i) {
@@ -323,7 +323,11 @@ size_t session_footprint(int64_t n, int k, int p, int math, int64_t max_block_ro
     add(z.npad * L, 2); add(1, 4); add(1, 4); add(z.hpart * L, 4); add(z.nctas * L * L, 8);
     add(z.nctas * L, 8);
     if (z.img) add(z.img, 2);
-    if (t.use_grp) { add(4096, 2); add(z.part, 4); add(z.gbuf, 2); add(z.cnt, 4); }
+    if (t.use_grp) {
+      add(4096, 2); add(z.part, 4); add(z.gbuf, 2); add(z.cnt, 4);
+      const int64_t gr = static_cast<int64_t>(grp_gfull_rows(t.grp, mb));
+      if (gr) add(gr * L, 4);
+    }
   }
   add(int64_t(kShiftParts) * n, 8);
   const int64_t per = int64_t(L) * L * 8;
@@ -483,6 +487,8 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
       CC(dalloc(&t.part, size_t(tcz.part)));
       CC(dalloc(&t.gbuf, size_t(tcz.gbuf)));
       CC(dalloc(&t.cnt, size_t(tcz.cnt)));
+      t.gfull_rows = static_cast<int64_t>(grp_gfull_rows(t.grp, mb));
+      if (t.gfull_rows) CC(dalloc(&t.gfull, size_t(t.gfull_rows) * L));
     }
   }
   CC(dalloc(&s->shift_part, size_t(kShiftParts) * n));

@@ -123,6 +123,7 @@ struct TcConfig {
 struct GrpConfig {
   int S, NG, nbt, nbmax, nu, ns1, nd1, nf;
   uint32_t smem;
+  bool gram_in;          // the reducers accumulate the Gram matrix; else G' rows go to TcWork::gfull
 };
 
 struct TcWork {
@@ -136,6 +137,8 @@ struct TcWork {
   float* part;           // grouped kernel: the groups' partial rings
   uint16_t* gbuf;        // grouped kernel: the groups' G' rings
   unsigned* cnt;         // grouped kernel: the groups' counters
+  float* gfull;          // grouped kernel without in-kernel Gram: the launch's G' rows (tiles x 128 x L)
+  int64_t gfull_rows;    // rows gfull holds
   int fmt;               // 0: BF16 operands; 1: FP16 operands on values scaled by *scale
   float* scale;          // device scalar: power-of-two operand scale (FP16 form)
   unsigned int* scale_bits;   // device scratch for the largest row norm
@@ -185,6 +188,7 @@ size_t grp_img_elems(const GrpConfig& c);
 size_t grp_part_elems(const GrpConfig& c, int L);
 size_t grp_gbuf_elems(const GrpConfig& c, int L, int fmt);
 size_t grp_cnt_elems(const GrpConfig& c);
+size_t grp_gfull_rows(const GrpConfig& c, int64_t max_block_rows);
 cudaError_t grp_pass(const State& s, const TcWork& w, const TcPending& pend, cudaStream_t st, Prof* prof,
                      bool* used);
 const char* tc3_config_reason();
