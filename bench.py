@@ -150,7 +150,7 @@ def cpu_baseline(A_sample_f32, seed, what):
 # ------------------------------------------------------------------------------------------ arms
 
 def dist_setup():
-    """Rank layout from the torchrun environment; one process per GPU, replicas of the pass."""
+    """Rank layout from the torchrun environment; one process per GPU, each over its own rows."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -257,10 +257,14 @@ def traffic_record(math_name):
 
 
 def run_form(spca, math_name, A, seed, stream, steps_arg, warmup, ws):
-    """Time whole passes (reset, all row blocks, finalize) of one arithmetic form."""
+    """Time whole passes (reset, all row blocks, finalize) of one arithmetic form. With N ranks
+    each rank passes over its own rows and the exchange step merges every rank's sketch into
+    rank 0's, which alone finalizes (the rows of all ranks form one matrix)."""
+    from paper_1704_07669_gb300 import shard
     m = A.shape[0]
     dev = A.device
     sess = spca.Session(N, K, P, seed, math=math_name, stream=stream)
+    scratch = shard.scratch_like(sess) if ws > 1 and torch.distributed.get_rank() == 0 else None
     sigma_d = torch.zeros(K, dtype=torch.float64, device=dev)
     V_d = torch.zeros((K, N), dtype=torch.float64, device=dev)
 
@@ -268,6 +272,8 @@ def run_form(spca, math_name, A, seed, stream, steps_arg, warmup, ws):
         spca.spca_reset(sess.handle, seed)
         for r0 in range(0, m, BLOCK):
             spca.spca_update(sess.handle, A[r0:r0 + BLOCK])
+        if ws > 1 and not shard.merge_across_ranks(sess, scratch=scratch):
+            return
         spca.spca_finalize(sess.handle, sigma_d, V_d, out_on_device=True)
 
     for _ in range(max(warmup, 1)):
@@ -466,9 +472,10 @@ def run_ours(args):
     pk = peaks()
     m = args.m
 
+    # each rank its own rows of the workload's recipe; one Omega (one session seed) for all ranks
     w = synth.workload_c2(m=m, device=dev, seed=synth.SEED_BASE + 1 + rank)
     A = w["A"]
-    seed = w["seed"]
+    seed = synth.SEED_BASE + 1
     stream = torch.cuda.Stream(device=dev)
     bytes_A = m * N * 4
 
@@ -503,10 +510,15 @@ def run_ours(args):
     e2e_steps = 2
     rows_np = A_host.numpy()
 
+    from paper_1704_07669_gb300 import shard
+    scratch = shard.scratch_like(sess) if ws > 1 and rank == 0 else None
+
     def e2e_step():
         spca.spca_reset(sess.handle, seed)
         for r0 in range(0, m, BLOCK):
             spca.spca_update(sess.handle, rows_np[r0:r0 + BLOCK])
+        if ws > 1 and not shard.merge_across_ranks(sess, scratch=scratch):
+            return
         spca.spca_finalize(sess.handle, sig_h, V_h, out_on_device=False)
 
     e2e_step()
@@ -536,7 +548,7 @@ def run_ours(args):
 
     cpu = None
     precision = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         # the CPU oracle leg: the oracle timed on a bounded sample, and the oracle's result on the
         # whole matrix for the error of each timed form
         sample_rows = min(8 * BLOCK, m)
@@ -558,7 +570,9 @@ def run_ours(args):
             "dtype": {"fp32": "f32", "fp16": "f16"}.get(args.math, "bf16"), "data": "synthetic",
             "config": {"workload": workload, "math": args.math,
                        "l2": f"inputs larger than L2 ({bytes_A / 1e9:.1f} GB), no flush",
-                       "parallelism": "replicas" if ws > 1 else "single"},
+                       "parallelism": (f"rows sharded over {ws} ranks ({m} rows each), one exchange step: "
+                                       "rank checkpoints gathered and merged on rank 0, which finalizes")
+                       if ws > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "precision_vs_oracle": precision,
             "clocks": clocks.summary(), "kernels": kernels, "forms": forms, "serving": serving, "streamed": streamed,

@@ -319,6 +319,7 @@ class Session:
     def __init__(self, n, k, p, seed, math=SPCA_MATH_FP32, center=True, max_block_rows=0, stream=None):
         self.n, self.k, self.p = int(n), int(k), int(p)
         self.l = self.k + self.p
+        self.seed, self.math, self.center, self.max_block_rows = int(seed), math, bool(center), int(max_block_rows)
         self.handle = spca_create(n, k, p, seed, math=math, center=int(center), max_block_rows=max_block_rows,
                                   stream=stream)
         self.own_stream = stream is None   # the library's own stream: not ordered after torch's

@@ -914,10 +914,15 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
         // FP8, x = code and s = block scale x s, exact because the code has 4 significant bits
         // and the scale is taken as given). All loads of a stage first (they overlap), then the
         // conversions and stores; the stage goes back to the producer only after the stores.
-        auto put8 = [&](int r, int fb, const float (&xv)[8], bool valid) {
+        // cs: -c s of the 8 features fb..fb+7 (taken once per stage and reused for every row)
+        auto shift8 = [&](int fb, float (&cs)[8]) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) cs[e] = -sShift[64 * b + fb + e] * op_scale;
+        };
+        auto put8 = [&](int r, int fb, const float (&xv)[8], const float (&cs)[8], bool valid) {
           float v[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) v[e] = valid ? fmaf(xv[e], xs, -sShift[64 * b + fb + e] * op_scale) : 0.f;
+          for (int e = 0; e < 8; ++e) v[e] = valid ? fmaf(xv[e], xs, cs[e]) : 0.f;
           *reinterpret_cast<uint4*>(op + static_cast<uint32_t>(r >> 3) * 1024u +
                                     sw128(static_cast<uint32_t>(r & 7), static_cast<uint32_t>(fb) * 2u)) =
               make_uint4(pack2<FMT>(v[0], v[1]), pack2<FMT>(v[2], v[3]), pack2<FMT>(v[4], v[5]),
@@ -931,6 +936,8 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
             // 128-byte rows of 32 features: thread = (8-feature piece cq, rows rb + 32 k)
             const int cq = ct & 3, rb = ct >> 2;
             const int fb = 32 * hf + 8 * cq;
+            float cs[8];
+            shift8(fb, cs);
             float4 x[8];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -943,11 +950,13 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
               const int r = rb + 32 * k;
               const float xv[8] = {x[2 * k].x, x[2 * k].y, x[2 * k].z, x[2 * k].w,
                                    x[2 * k + 1].x, x[2 * k + 1].y, x[2 * k + 1].z, x[2 * k + 1].w};
-              put8(r, fb, xv, row0 + r < mseg);
+              put8(r, fb, xv, cs, row0 + r < mseg);
             }
           } else if constexpr (INP == IN_BF16) {
             // 128-byte rows of 64 features: thread = (16-byte chunk c8 = 8 features, rows rb + 16 k)
             const int c8 = ct & 7, rb = ct >> 3;
+            float cs[8];
+            shift8(8 * c8, cs);
             uint4 x[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
@@ -964,11 +973,14 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
                 xv[2 * e] = __uint_as_float(w[e] << 16);
                 xv[2 * e + 1] = __uint_as_float(w[e] & 0xFFFF0000u);
               }
-              put8(r, 8 * c8, xv, row0 + r < mseg);
+              put8(r, 8 * c8, xv, cs, row0 + r < mseg);
             }
           } else {
             // 64-byte rows of 64 codes, unswizzled: thread = (16-code chunk c4, rows rb + 32 k)
             const int c4 = ct & 3, rb = ct >> 2;
+            float cs0[8], cs1[8];
+            shift8(16 * c4, cs0);
+            shift8(16 * c4 + 8, cs1);
             uint4 x[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) x[k] = *reinterpret_cast<const uint4*>(stg + (rb + 32 * k) * 64 + c4 * 16);
@@ -989,8 +1001,8 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
               const bool valid = row0 + r < mseg;
               const float x0[8] = {xv[0], xv[1], xv[2], xv[3], xv[4], xv[5], xv[6], xv[7]};
               const float x1[8] = {xv[8], xv[9], xv[10], xv[11], xv[12], xv[13], xv[14], xv[15]};
-              put8(r, 16 * c4, x0, valid);
-              put8(r, 16 * c4 + 8, x1, valid);
+              put8(r, 16 * c4, x0, cs0, valid);
+              put8(r, 16 * c4 + 8, x1, cs1, valid);
             }
           }
           __syncwarp();

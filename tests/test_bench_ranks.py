@@ -1,6 +1,6 @@
 """The multi-rank host logic of bench.py on CPU: two gloo ranks, the rank layout read from the
 torchrun environment, the barrier, and the max-over-ranks timing that makes the job's time its
-slowest rank's. (The pass itself does not shard; N GPUs run N replicas.)"""
+slowest rank's. (The row-sharded exchange step itself is covered by tests/test_shard_gloo.py.)"""
 import os
 import socket
 
