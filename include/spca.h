@@ -178,6 +178,29 @@ spca_status spca_finalize(spca_session* s, double* sigma, double* V, int32_t out
 spca_status spca_left_vectors(spca_session* s, const float* G, int64_t m, double* U, int32_t out_on_device);
 
 /*
+ * spca_left_vectors_pass - U of given rows by a second pass over them, for callers
+ * that kept no sketch rows (G_out): U = A_bar V Sigma^-1, the truncated SVD
+ * A_bar ~ U diag(sigma) V^T solved for U with the sigma and V of the last
+ * spca_finalize (Alg. 4 step 18 forms U from the stored sketch instead; with an
+ * exactly rank-r matrix, r <= k, both give its left singular vectors).
+ *   rows   device, m x n row-major with leading dimension ld >= n, of type dtype
+ *          (block_scale as in spca_update for FP8 rows); any rows, e.g. the rows
+ *          of the pass block by block: row r of U belongs to row r of rows
+ *   U      device, m x k doubles, COLUMN-major with leading dimension ldu >= m
+ *          (column i at U + i*ldu)
+ * With centering, the column means mu = c + s_hat / m_seen of all rows seen are
+ * subtracted: (a - mu) V Sigma^-1 = (a - c) W - (s_hat / m_seen)^T W, W = V Sigma^-1
+ * in FP32 (products in FP32, sums of the slices and the centring term in FP64).
+ * Columns for zero sigma are 0. Runs on the session stream and returns without
+ * waiting: U is complete once the stream has passed the work (spca_sync). The
+ * first call on a tensor-core session allocates a workspace of 65536 x L floats.
+ * Errors: SPCA_E_STATE (no finalize since the state last changed),
+ * SPCA_E_INVALID (NULL or host pointers, sizes), SPCA_E_NOMEM, SPCA_E_CUDA.
+ */
+spca_status spca_left_vectors_pass(spca_session* s, const void* rows, int64_t m, int64_t ld, int32_t dtype,
+                                   const float* block_scale, double* U, int64_t ldu);
+
+/*
  * spca_power_step - the power scheme with P = 1 (Sec. 3.2 and Sec. 4): for
  * Alg. 4, run the while loop once more with Omega replaced by H after "orth".
  * Replaces Omega by the orthonormal basis of the centred H_bar of the rows seen

@@ -301,6 +301,19 @@ def svd_truncate(Q, B, k):
     return U, S[:k].copy(), V[:, :k].copy()
 
 
+def left_vectors_second_pass(A, V, sigma, center_columns=True):
+    """U = A_bar V diag(sigma)^-1 (FP64): the left singular vectors from a second pass over
+    the rows, for a caller that kept no sketch rows. The truncated SVD A_bar ~ U diag(sigma)
+    V^T of Alg. 4 step 19 with V^T V = I gives U = A_bar V diag(sigma)^-1 when A_bar lies in
+    the span of V (exactly for a rank-r matrix, r <= k); otherwise it is the projection the
+    second pass computes, where step 18's U = Q U~ projects onto range(Q) instead. Columns for
+    zero sigma are 0."""
+    A_bar = center(A) if center_columns else np.asarray(A, dtype=np.float64)
+    sigma = np.asarray(sigma, dtype=np.float64)
+    inv = np.where(sigma > 0, 1.0 / np.where(sigma > 0, sigma, 1.0), 0.0)
+    return (A_bar @ np.asarray(V, dtype=np.float64)) * inv[None, :]
+
+
 def sign_fix(V, U=None):
     """Scale each column of V by +-1 so its largest-|.| entry (lowest index on ties) is > 0."""
     V = np.array(V, dtype=np.float64, copy=True)

@@ -71,6 +71,7 @@ def lib():
             "spca_update": (i32, [vp, vp, i64, i64, i32, vp, i32, vp]),
             "spca_finalize": (i32, [vp, vp, vp, i32]),
             "spca_left_vectors": (i32, [vp, vp, i64, vp, i32]),
+            "spca_left_vectors_pass": (i32, [vp, vp, i64, i64, i32, vp, vp, i64]),
             "spca_power_step": (i32, [vp]),
             "spca_state_bytes": (i32, [vp, ctypes.POINTER(ctypes.c_size_t)]),
             "spca_save_state": (i32, [vp, vp, ctypes.c_size_t]),
@@ -200,6 +201,21 @@ def spca_left_vectors(handle, G, U, m=None, out_on_device=None):
         m = G.shape[0]
     on = bool(udev) if out_on_device is None else bool(out_on_device)
     _check(lib().spca_left_vectors(handle, ga, int(m), ua, int(on)), handle)
+
+
+def spca_left_vectors_pass(handle, rows, U, block_scale=None):
+    """U rows of the device rows `rows` (m x n, any storage dtype) by a second pass, into U: a
+    CUDA float64 tensor of shape (k, m) (column-major m x k; ldu = its row stride)."""
+    addr, on_dev = _ptr(rows)
+    ua, udev = _ptr(U)
+    if not on_dev or not udev:
+        raise ValueError("spca_left_vectors_pass: rows and U must be CUDA tensors")
+    m = int(rows.shape[0])
+    ld = rows.stride(0)
+    scale = None if block_scale is None else ctypes.c_float(float(block_scale))
+    _check(lib().spca_left_vectors_pass(handle, addr, m, int(ld), int(_dtype_code(rows)),
+                                        ctypes.cast(ctypes.byref(scale), ctypes.c_void_p) if scale is not None else None,
+                                        ua, int(U.stride(0))), handle)
 
 
 def spca_power_step(handle):
@@ -345,6 +361,18 @@ class Session:
         Uc = np.zeros((self.k, m))      # column-major m x k == row-major k x m
         spca_left_vectors(self.handle, G, Uc, m=m, out_on_device=False)
         return Uc.T.copy()
+
+    def left_vectors_pass(self, rows, block_scale=None):
+        """U (m x k float64 CUDA tensor) of the CUDA rows `rows` by a second pass over them (after
+        a finalize): (rows - column means) V diag(sigma)^-1. Ordered on the session stream; the
+        result is read after sync()."""
+        import torch
+        if self.own_stream:
+            _wait_for_torch(rows)
+        m = int(rows.shape[0])
+        Uc = torch.empty((self.k, m), dtype=torch.float64, device=rows.device)
+        spca_left_vectors_pass(self.handle, rows, Uc, block_scale=block_scale)
+        return Uc.T
 
     def save_state(self):
         """A checkpoint (bytes) that load_state restores into a session of the same parameters."""

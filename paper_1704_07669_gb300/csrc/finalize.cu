@@ -1961,6 +1961,44 @@ cudaError_t power_omega_run(const State& s, const FinalWork& f, int64_t m, cudaS
   return cudaGetLastError();
 }
 
+// After a finalize: W = V Sigma^-1 in FP32 (n x L, zero beyond the rank and past k) for a
+// second pass over the rows, and corr = (s_hat / m)^T W in FP64 (from the FP32 W, so that the
+// centring term matches the products it corrects; 0 without centring).
+__global__ void upass_w_kernel(const double* __restrict__ V, const double* __restrict__ sigma, int64_t n, int k, int L,
+                               float* __restrict__ W) {
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < n * L;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t c = idx / L;
+    const int j = static_cast<int>(idx - c * L);
+    float w = 0.f;
+    if (j < k && sigma[j] > 0.0) w = static_cast<float>(V[static_cast<int64_t>(j) * n + c] / sigma[j]);
+    W[idx] = w;
+  }
+}
+
+__global__ void upass_corr_kernel(const float* __restrict__ W, const double* __restrict__ colsum, int64_t m, int64_t n,
+                                  int L, double* __restrict__ corr) {
+  __shared__ double red[256];
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  if (m > 0)
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) acc += colsum[c] * static_cast<double>(W[c * L + j]);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) corr[j] = m > 0 ? red[0] / static_cast<double>(m) : 0.0;
+}
+
+cudaError_t launch_upass_prep(const State& s, const double* V, const double* sigma, int k, int64_t m_center,
+                              float* W, double* corr, cudaStream_t st) {
+  upass_w_kernel<<<grid_for(s.n * s.L, 256), 256, 0, st>>>(V, sigma, s.n, k, s.L, W);
+  upass_corr_kernel<<<s.L, 256, 0, st>>>(W, s.colsum, m_center, s.n, s.L, corr);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_u_map(const State& s, const FinalWork& f, int k, int64_t m, cudaStream_t st) {
   u_map_kernel<<<k, 64, 0, st>>>(f.Tu, f.X, f.info, f.flip, s.sG, m, s.l, s.L, k, f.M, f.mrow);
   return cudaGetLastError();

@@ -885,6 +885,49 @@ cudaError_t simt_pass_t(const State& s, const SimtWork& w, const T* rows, float 
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ second pass: U = A_bar V Sigma^-1
+
+// U (column i at U + i ldu, FP64) of a block of rows: the FP32 split-K partials of
+// (a - c) W summed over the slices, minus the centring term corr (FP64): with
+// mu = c + s_hat / m the column means, (a - mu) W = (a - c) W - (s_hat / m)^T W.
+__global__ void u_finish_kernel(const float* __restrict__ Gpart, int S, int64_t mstride, int64_t m, int L, int k,
+                                const double* __restrict__ corr, double* __restrict__ U, int64_t ldu) {
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < m * k;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = idx / k;
+    const int j = static_cast<int>(idx - r * k);
+    double v = 0.0;
+    for (int s = 0; s < S; ++s) v += static_cast<double>(Gpart[(static_cast<int64_t>(s) * mstride + r) * L + j]);
+    U[static_cast<int64_t>(j) * ldu + r] = v - corr[j];
+  }
+}
+
+template <typename T>
+cudaError_t u_pass_t(const T* rows, float scale, int64_t m, int64_t n, int64_t ld, const float* shift, const float* W,
+                     int L, int k, const double* corr, float* Gpart, int64_t gp_rows, double* U, int64_t ldu,
+                     cudaStream_t st) {
+  const bool vec_ok = (reinterpret_cast<uintptr_t>(rows) % 16 == 0) && (ld % 4 == 0);
+  const int col_tiles = (L + BN - 1) / BN;
+  for (int64_t p0 = 0; p0 < m; p0 += gp_rows) {   // pieces whose partials fit the workspace
+    const int64_t mp = m - p0 < gp_rows ? m - p0 : gp_rows;
+    const int row_tiles = static_cast<int>((mp + BM - 1) / BM);
+    const int64_t kchunks = (n + BK - 1) / BK;
+    const int64_t mstride = static_cast<int64_t>(row_tiles) * BM;
+    int S = static_cast<int>(608 / (row_tiles * col_tiles));
+    if (S > gp_rows / mstride) S = static_cast<int>(gp_rows / mstride);
+    if (S > kchunks) S = static_cast<int>(kchunks);
+    if (S < 1) S = 1;
+    const int64_t kslice = ((kchunks + S - 1) / S) * BK;
+    S = static_cast<int>((n + kslice - 1) / kslice);
+    const T* src = rows + p0 * ld;
+    g_partial_kernel<T><<<dim3(row_tiles, S, col_tiles), NT, kSmemG, st>>>(src, mp, n, ld, shift, scale, vec_ok, W, L,
+                                                                           kslice, Gpart, mstride);
+    u_finish_kernel<<<grid_for(mp * k, 256), 256, 0, st>>>(Gpart, S, mstride, mp, L, k, corr, U + p0, ldu);
+  }
+  return cudaGetLastError();
+}
+
+
 template <typename T>
 cudaError_t shift_t(const T* rows, int64_t m, int64_t n, int64_t ld, float scale, float* shift, double* part,
                     cudaStream_t st, Prof* prof) {
@@ -903,6 +946,35 @@ cudaError_t shift_t(const T* rows, int64_t m, int64_t n, int64_t ld, float scale
 }
 
 }  // namespace
+
+cudaError_t launch_u_pass(const void* rows, int dtype, float scale, int64_t m, int64_t n, int64_t ld,
+                          const float* shift, const float* W, int L, int k, const double* corr, float* Gpart,
+                          int64_t gp_rows, double* U, int64_t ldu, cudaStream_t st) {
+  static std::atomic<uint64_t> attr{0};
+  static std::mutex mu;
+  const cudaError_t ea = once_per_device(attr, mu, [] {
+    cudaError_t e = allow_smem(g_partial_kernel<float>, kSmemG);
+    if (e == cudaSuccess) e = allow_smem(g_partial_kernel<__nv_bfloat16>, kSmemG);
+    if (e == cudaSuccess) e = allow_smem(g_partial_kernel<__nv_fp8_e4m3>, kSmemG);
+    if (e == cudaSuccess) e = allow_smem(g_partial_kernel<double>, kSmemG);
+    return e;
+  });
+  if (ea != cudaSuccess) return ea;
+  switch (dtype) {
+    case SPCA_F32:
+      return u_pass_t(static_cast<const float*>(rows), scale, m, n, ld, shift, W, L, k, corr, Gpart, gp_rows, U, ldu, st);
+    case SPCA_F64:
+      return u_pass_t(static_cast<const double*>(rows), scale, m, n, ld, shift, W, L, k, corr, Gpart, gp_rows, U, ldu,
+                      st);
+    case SPCA_BF16:
+      return u_pass_t(static_cast<const __nv_bfloat16*>(rows), scale, m, n, ld, shift, W, L, k, corr, Gpart, gp_rows, U,
+                      ldu, st);
+    case SPCA_F8E4M3:
+      return u_pass_t(static_cast<const __nv_fp8_e4m3*>(rows), scale, m, n, ld, shift, W, L, k, corr, Gpart, gp_rows,
+                      U, ldu, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_omega_f32(uint64_t seed, int64_t n, int l, int L, float* out, int64_t ld, cudaStream_t st,
                              Prof* prof) {

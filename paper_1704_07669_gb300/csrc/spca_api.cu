@@ -145,6 +145,9 @@ struct spca_session {
   FinalWork fin{};
   double* fin_sigma = nullptr;
   double* fin_V = nullptr;
+  float* upass_W = nullptr;       // n x L: V Sigma^-1 of the last finalize (FP32), for spca_left_vectors_pass
+  double* upass_corr = nullptr;   // L: its centring term
+  float* upass_gpart = nullptr;   // tensor-core sessions: split-K partials of the second pass (made on first use)
 
   // host staging
   void* pinned[2] = {nullptr, nullptr};
@@ -203,6 +206,7 @@ void free_all(spca_session* s) {
                   s->simt.gram_part, s->simt.sG_part, s->simt.Hpart, s->simt.cs_part, s->shift_part, s->fin.Hbar,
                   s->fin.gbar, s->fin.T, s->fin.X, s->fin.W, s->fin.lam, s->fin.Bt, s->fin.Cpart, s->fin.C,
                   s->fin.sig, s->fin.info, s->fin.flip, s->fin.Tu, s->fin.M, s->fin.mrow, s->fin_sigma, s->fin_V,
+                  s->upass_W, s->upass_corr, s->upass_gpart,
                   s->dstage[0], s->dstage[1],
                   s->tcw.om16, s->tcw.Hpart, s->tcw.gram_part, s->tcw.sG_part, s->tcw.scale, s->tcw.scale_bits,
                   s->tcw.img, s->tcw.zero8k, s->tcw.part, s->tcw.gbuf, s->tcw.cnt, s->tcw.gfull};
@@ -312,6 +316,7 @@ size_t session_footprint(int64_t n, int k, int p, int math, int64_t max_block_ro
   };
   if (!tc) add(n * L, 4);
   add(n * L, 8); add(n, 4); add(n, 8); add(L, 8); add(int64_t(L) * L, 8); add(4, 4);
+  add(n * L, 4); add(L, 8);   // the second pass's V Sigma^-1 and centring term
   if (!tc) {
     const int64_t mb_pad = ((mb + 127) / 128) * 128;
     const int64_t gp_rows = mb_pad > 65536 ? mb_pad : 65536;
@@ -518,6 +523,8 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   CC(dalloc(&f.mrow, L));
   CC(dalloc(&s->fin_sigma, k));
   CC(dalloc(&s->fin_V, size_t(n) * k));
+  CC(dalloc(&s->upass_W, size_t(n) * L));
+  CC(dalloc(&s->upass_corr, L));
 
   CC(cudaMemsetAsync(s->H, 0, sizeof(double) * n * L, s->stream));
   CC(cudaMemsetAsync(s->shift, 0, sizeof(float) * n, s->stream));
@@ -691,6 +698,7 @@ spca_status spca_finalize(spca_session* s, double* sigma, double* V, int32_t out
   double* vd = out_on_device ? V : s->fin_V;
   CU(finalize_run(s->state(), s->fin, s->opt.center ? s->m : 0, s->k, sd, vd, s->stream, &s->prof, s->m,
                   s->opt.center != 0));
+  CU(launch_upass_prep(s->state(), vd, sd, s->k, s->opt.center ? s->m : 0, s->upass_W, s->upass_corr, s->stream));
   if (!out_on_device) {
     CU(cudaMemcpyAsync(sigma, sd, sizeof(double) * s->k, cudaMemcpyDeviceToHost, s->stream));
     CU(cudaMemcpyAsync(V, vd, sizeof(double) * s->n * s->k, cudaMemcpyDeviceToHost, s->stream));
@@ -739,6 +747,52 @@ spca_status spca_left_vectors(spca_session* s, const float* G, int64_t m, double
                          cudaMemcpyDeviceToHost, s->stream));
   }
   CU(cudaStreamSynchronize(s->stream));
+  return SPCA_OK;
+}
+
+spca_status spca_left_vectors_pass(spca_session* s, const void* rows, int64_t m, int64_t ld, int32_t dtype,
+                                   const float* block_scale, double* U, int64_t ldu) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  if (!s->u_ready) return fail(s, SPCA_E_STATE, "spca_left_vectors_pass needs a spca_finalize after the last update");
+  if (m < 0) return fail(s, SPCA_E_INVALID, "m < 0");
+  if (m == 0) return SPCA_OK;
+  if (!rows || !U) return fail(s, SPCA_E_INVALID, "rows and U must be non-NULL");
+  if (ld < s->n) return fail(s, SPCA_E_INVALID, "ld (%lld) < n (%lld)", (long long)ld, (long long)s->n);
+  if (ldu < m) return fail(s, SPCA_E_INVALID, "ldu (%lld) < m (%lld)", (long long)ldu, (long long)m);
+  if (dtype_size(dtype) == 0) return fail(s, SPCA_E_INVALID, "unknown dtype %d", dtype);
+  float scale = 1.0f;
+  if (dtype == SPCA_F8E4M3) {
+    if (!block_scale) return fail(s, SPCA_E_INVALID, "FP8 rows need a block_scale");
+    scale = *block_scale;
+    if (!(scale > 0.0f) || scale != scale) return fail(s, SPCA_E_INVALID, "block_scale must be positive");
+  }
+  CU(cudaSetDevice(s->device));
+  for (const void* p : {static_cast<const void*>(rows), static_cast<const void*>(U)}) {
+    cudaPointerAttributes attr;
+    std::memset(&attr, 0, sizeof(attr));
+    const bool ok = cudaPointerGetAttributes(&attr, p) == cudaSuccess;
+    cudaGetLastError();
+    if (!ok || (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged))
+      return fail(s, SPCA_E_INVALID, "rows and U must be device memory");
+  }
+  float* gpart = s->simt.Gpart;
+  int64_t gp_rows = s->simt.gp_rows;
+  if (!gpart) {   // tensor-core sessions keep no split-K workspace: one for this pass, made once
+    gp_rows = 65536;
+    if (!s->upass_gpart) {
+      const cudaError_t e = cudaMalloc(&s->upass_gpart, sizeof(float) * size_t(gp_rows) * s->L);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        s->upass_gpart = nullptr;
+        return fail(s, e == cudaErrorMemoryAllocation ? SPCA_E_NOMEM : SPCA_E_CUDA, "second-pass workspace: %s",
+                    cudaGetErrorString(e));
+      }
+    }
+    gpart = s->upass_gpart;
+  }
+  CU(launch_u_pass(rows, dtype, scale, m, s->n, ld, s->shift, s->upass_W, s->L, s->k, s->upass_corr, gpart, gp_rows,
+                   U, ldu, s->stream));
   return SPCA_OK;
 }
 

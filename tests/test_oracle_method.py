@@ -178,6 +178,25 @@ def test_exact_rank_recovered_exactly(finalize):
     assert O.max_principal_sine(r["V"], V[:, :8]) < 1e-11
 
 
+def test_second_pass_left_vectors_of_an_exact_rank_matrix():
+    # rank(A) = r <= k: A = U_r S V_r^T exactly, so A V S^-1 with the method's V and sigma is
+    # U_r up to the sign each v_i carries, and equals Alg. 4 step 18's Q U~
+    A, U, sig, V = synth.exact_rank(150, 80, 6, seed=9)
+    r = O.single_pass_pca(A, 8, 4, 14, 25, center_columns=False, finalize="gram", keep_U=True)
+    U2 = O.left_vectors_second_pass(A, r["V"], r["sigma"], center_columns=False)
+    signs = np.sign(np.sum(r["V"][:, :6] * V, axis=0))
+    assert np.max(np.abs(U2[:, :6] - U * signs[None, :])) < 1e-10
+    assert np.all(U2[:, 6:] == 0.0)          # sigma_7.. = 0: no direction
+    assert np.max(np.abs(U2[:, :6] - r["U"][:, :6])) < 1e-10
+    # with centering the column means come off first: a rank-r matrix plus 1 mu^T
+    mu = np.linspace(-1.0, 2.0, 80)
+    rc = O.single_pass_pca(A + mu[None, :], 8, 4, 14, 25, center_columns=True, finalize="gram")
+    U3 = O.left_vectors_second_pass(A + mu[None, :], rc["V"], rc["sigma"])
+    Ub = O.center(A) @ rc["V"][:, :5] / rc["sigma"][None, :5]
+    assert np.max(np.abs(U3[:, :5] - Ub)) < 1e-12
+    assert np.max(np.abs(U3[:, :5].T @ U3[:, :5] - np.eye(5))) < 1e-9
+
+
 def test_rank_below_l_uses_eigen_route_and_pads_zero_sigma():
     A, U, sig, V = synth.exact_rank(150, 80, 5, seed=8)
     Om = O.omega(80, 12, seed=12)
