@@ -264,6 +264,20 @@ spca_status spca_get_state(spca_session* s, double* H_bar, double* gram_bar,
  */
 spca_status spca_merge(spca_session* dst, const spca_session* src);
 
+/*
+ * spca_wait_selftest - exercise the bounded wait that every cross-CTA and pipeline
+ * wait of the tensor-core pass uses: one thread waits, with limit limit_ns, for a
+ * device counter that nothing writes, gives up, and the call reports it. Returns
+ * SPCA_E_TIMEOUT after about limit_ns (the expected outcome; the device stays
+ * usable) and never SPCA_OK. The pass kernels' own limit is half a second, or
+ * SPCA_WAIT_LIMIT_MS milliseconds (1 .. 60000) from the environment at
+ * spca_create; a wait that runs out there ends the launch early and the next
+ * synchronising call returns SPCA_E_TIMEOUT. Not part of the paper: an
+ * operational check. cuda_stream may be NULL (the legacy default stream).
+ * Errors: SPCA_E_INVALID (limit_ns outside [1, 6e10]), SPCA_E_CUDA.
+ */
+spca_status spca_wait_selftest(int64_t limit_ns, void* cuda_stream);
+
 /* Wait until all work issued on the session's stream is done. */
 spca_status spca_sync(spca_session* s);
 

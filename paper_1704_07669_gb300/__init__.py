@@ -90,6 +90,7 @@ def lib():
             "spca_omega_words": (i32, [u64, i64, i32, vp]),
             "spca_omega": (i32, [u64, i64, i32, vp]),
             "spca_shift_static": (i32, [vp, i64, i64, i64, i32, vp, vp, vp]),
+            "spca_wait_selftest": (i32, [i64, vp]),
             "spca_server_default_options": (None, [ctypes.POINTER(ServerOptions)]),
             "spca_server_create": (i32, [ctypes.POINTER(ServerOptions), ctypes.POINTER(vp)]),
             "spca_server_open": (i32, [vp, i64, i32, i32, u64, ctypes.POINTER(i32)]),
@@ -216,6 +217,12 @@ def spca_left_vectors_pass(handle, rows, U, block_scale=None):
     _check(lib().spca_left_vectors_pass(handle, addr, m, int(ld), int(_dtype_code(rows)),
                                         ctypes.cast(ctypes.byref(scale), ctypes.c_void_p) if scale is not None else None,
                                         ua, int(U.stride(0))), handle)
+
+
+def spca_wait_selftest(limit_ns, stream=None):
+    """The bounded-wait self-test: raises SpcaError with status SPCA_E_TIMEOUT after about limit_ns."""
+    st = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(lib().spca_wait_selftest(int(limit_ns), st))
 
 
 def spca_power_step(handle):

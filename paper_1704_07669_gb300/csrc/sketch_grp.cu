@@ -136,6 +136,7 @@ struct GrpArgs {
   int npairs;                   // the reducers' Gram blocks (gram_pairs(l)), or 0 with gfull
   float* gfull;                 // npairs == 0: G' rows of the launch, tile t at rows 128 t (ld L), unscaled
   float* Hpart;                 // per group: nbt*64 x L (FP32)
+  uint64_t wait_ns;             // the pipeline waits' limit (a wait that runs out sets flags[0] bit 2)
   double* gram_part;            // per CTA: L x L
   double* sG_part;              // per CTA: L
   int* flags;
@@ -187,15 +188,20 @@ __device__ __forceinline__ uint64_t gtime_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+// The waits of the pipeline give up after the launch's wait limit (GrpArgs::wait_ns, half a
+// second unless the session says otherwise); the waits for a CTA's own copies in flight before
+// it leaves keep half a second whatever that limit is.
+constexpr uint64_t kOwnWaitNs = 500000000ull;
+
 // bounded poll of a global counter until it reaches target: short sleeps between polls (the
-// counters are written by other SMs), giving up after about half a second
-__device__ __forceinline__ bool wait_geq(const unsigned* p, unsigned target) {
+// counters are written by other SMs)
+__device__ __forceinline__ bool wait_geq(const unsigned* p, unsigned target, uint64_t limit_ns = kOwnWaitNs) {
   if (ld_acquire_u32(p) >= target) return true;
   const uint64_t t0 = gtime_ns();
   for (;;) {
     __nanosleep(64);
     if (ld_acquire_u32(p) >= target) return true;
-    if (gtime_ns() - t0 > 500000000ull) return false;
+    if (gtime_ns() - t0 > limit_ns) return false;
   }
 }
 // try_wait with a suspend-time hint: the thread sleeps in hardware until the phase completes
@@ -209,13 +215,13 @@ __device__ __forceinline__ bool mbar_try_sus(uint32_t a, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded: gives up after about half a second
-__device__ __forceinline__ bool mbar_wait_fast(uint32_t a, uint32_t parity) {
+// bounded: gives up after limit_ns
+__device__ __forceinline__ bool mbar_wait_fast(uint32_t a, uint32_t parity, uint64_t limit_ns = kOwnWaitNs) {
   if (mbar_try_sus(a, parity)) return true;
   const uint64_t t0 = gtime_ns();
   for (;;) {
     if (mbar_try_sus(a, parity)) return true;
-    if (gtime_ns() - t0 > 500000000ull) return false;
+    if (gtime_ns() - t0 > limit_ns) return false;
   }
 }
 __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
@@ -305,6 +311,9 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int NG = a.NG;
+  const uint64_t wl = a.wait_ns;
+#define PWAIT_MBAR(addr, par) mbar_wait_fast((addr), (par), wl)
+#define PWAIT_GEQ(ptr, target) wait_geq((ptr), (target), wl)
   const int nt = grp < a.ntiles ? static_cast<int>((a.ntiles - 1 - grp) / NG + 1) : 0;
   const int64_t f0 = static_cast<int64_t>(blk0) * 64;
   const int64_t fend = static_cast<int64_t>(blk1) * 64;
@@ -402,14 +411,14 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
         for (int b = 0; b < NB; ++b) {
           for (int hf = 0; hf < SPB; ++hf) {
             const uint32_t s = spos % a.ns1, k = spos / a.ns1;
-            if (k >= 1 && !dead && !mbar_wait_fast(bar(B_S1_EMPTY + s), (k - 1) & 1u)) dead = true;
+            if (k >= 1 && !dead && !PWAIT_MBAR(bar(B_S1_EMPTY + s), (k - 1) & 1u)) dead = true;
             mbar_expect_tx(bar(B_S1_FULL + s), SBYTES);
             tma_load_2d_hint(su32(base + lay.st1) + s * STG, tmap, static_cast<int32_t>(f0 + 64 * b + 32 * hf), y0,
                              bar(B_S1_FULL + s), drop);
             ++spos;
           }
           const uint32_t o = opos % OM_R, ko = opos / OM_R;
-          if (ko >= 1 && !dead && !mbar_wait_fast(bar(B_OM_EMPTY + o), (ko - 1) & 1u)) dead = true;
+          if (ko >= 1 && !dead && !PWAIT_MBAR(bar(B_OM_EMPTY + o), (ko - 1) & 1u)) dead = true;
           mbar_expect_tx(bar(B_OM_FULL + o), om_bytes);
           bulk_g2s_hint(su32(base + lay.om) + o * om_bytes, a.om16 + static_cast<int64_t>(blk0 + b) * L * 64,
                         om_bytes, bar(B_OM_FULL + o), keep);
@@ -437,15 +446,15 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
         const int slot = i % RING_R;
         const unsigned use = static_cast<unsigned>(i / RING_R);
         const int ri = i % IMG_R;
-        if (!dead && !mbar_wait_fast(bar(B_IMG_READY + ri), static_cast<uint32_t>(i / IMG_R) & 1u)) dead = true;
+        if (!dead && !PWAIT_MBAR(bar(B_IMG_READY + ri), static_cast<uint32_t>(i / IMG_R) & 1u)) dead = true;
         GRP_TRACE(i, 7);
         fence_proxy_async_global();   // the image (bulk writes of this CTA) before the bulk reads
         // G' of the tile: once every reducer of the group has published its rows
         auto load_g = [&]() {
-          if (!dead && !wait_geq(c_reduced(slot), static_cast<unsigned>(S) * (use + 1))) dead = true;
+          if (!dead && !PWAIT_GEQ(c_reduced(slot), static_cast<unsigned>(S) * (use + 1))) dead = true;
           GRP_TRACE(i, 8);
           fence_proxy_async_global();   // other CTAs' plain stores of G' before the bulk read
-          if (i >= 1 && !dead && !mbar_wait_fast(bar(B_GP_EMPTY), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
+          if (i >= 1 && !dead && !PWAIT_MBAR(bar(B_GP_EMPTY), static_cast<uint32_t>(i - 1) & 1u)) dead = true;
           mbar_expect_tx(bar(B_GP_FULL), gp_bytes);
           bulk_g2s_hint(su32(base + lay.gp), gbuf_g + static_cast<int64_t>(slot) * (gp_bytes / 2), gp_bytes,
                         bar(B_GP_FULL), drop);
@@ -457,7 +466,7 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
           for (int h = 0; h < 2; ++h) {
             if (issued == NS2) load_g();
             const uint32_t s = ppos % NS2, k = ppos / NS2;
-            if (k >= 1 && !dead && !mbar_wait_fast(bar(B_P2_EMPTY + s), (k - 1) & 1u)) dead = true;
+            if (k >= 1 && !dead && !PWAIT_MBAR(bar(B_P2_EMPTY + s), (k - 1) & 1u)) dead = true;
             mbar_expect_tx(bar(B_P2_FULL + s), P2U);
             const uint32_t dst = su32(base + lay.p2) + s * P2U;
             for (int e = 0; e < 2; ++e) {
@@ -473,7 +482,7 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
         if (issued <= NS2) load_g();
         GRP_TRACE(i, 9);
         // once G' has landed, count it as loaded: the reducers may then reuse the slot
-        if (!dead && !mbar_wait_fast(bar(B_GP_FULL), static_cast<uint32_t>(i) & 1u)) dead = true;
+        if (!dead && !PWAIT_MBAR(bar(B_GP_FULL), static_cast<uint32_t>(i) & 1u)) dead = true;
         fence_proxy_async_global();
         red_release_add(c_loaded(slot), 1u);
       }
@@ -491,12 +500,12 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
       for (int i = 0; i < nt; ++i) {
         const int d = i % ND1;
         const uint32_t d1 = tmem + static_cast<uint32_t>(d * L);
-        if (i >= ND1 && !dead && !mbar_wait_fast(bar(B_D1_EMPTY + d), static_cast<uint32_t>(i / ND1 - 1) & 1u)) dead = true;
+        if (i >= ND1 && !dead && !PWAIT_MBAR(bar(B_D1_EMPTY + d), static_cast<uint32_t>(i / ND1 - 1) & 1u)) dead = true;
         tc_fence_after();
         for (int b = 0; b < NB; ++b) {
           const uint32_t p = opos & 1u, o = opos % OM_R;
-          if (!dead && !mbar_wait_fast(bar(B_OP_FULL + p), (opos >> 1) & 1u)) dead = true;
-          if (!dead && !mbar_wait_fast(bar(B_OM_FULL + o), (opos / OM_R) & 1u)) dead = true;
+          if (!dead && !PWAIT_MBAR(bar(B_OP_FULL + p), (opos >> 1) & 1u)) dead = true;
+          if (!dead && !PWAIT_MBAR(bar(B_OM_FULL + o), (opos / OM_R) & 1u)) dead = true;
           tc_fence_after();
           if (!dead) {
             const uint64_t dA = sdesc(su32(base + lay.op) + p * BLK16, 16, 1024);
@@ -520,23 +529,23 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
       uint32_t ppos = 0, fuses = 0, drains = 0;
       tc_fence_after();
       for (int i = 0; i < nt; ++i) {
-        if (!dead && !mbar_wait_fast(bar(B_GP_FULL), static_cast<uint32_t>(i) & 1u)) dead = true;
+        if (!dead && !PWAIT_MBAR(bar(B_GP_FULL), static_cast<uint32_t>(i) & 1u)) dead = true;
         // direct mode: after a drain tile, H starts again from zero once the drain has read it
         const bool zero_h = !fresh && (i == 0 || drain_tile(i - 1));
         if (!fresh && i >= 1 && drain_tile(i - 1)) {
-          if (!dead && !mbar_wait_fast(bar(B_F_FREE), (drains - 1) & 1u)) dead = true;
+          if (!dead && !PWAIT_MBAR(bar(B_F_FREE), (drains - 1) & 1u)) dead = true;
         }
         tc_fence_after();
         for (int u = 0; u < nu; ++u) {
           const uint32_t fb = fresh ? fuses % NF : 0u;
           const uint32_t dst = fresh ? tF + fb * static_cast<uint32_t>(L) : tHrun + static_cast<uint32_t>(u * L);
           if (fresh && fuses >= static_cast<uint32_t>(NF) && !dead &&
-              !mbar_wait_fast(bar(B_F_FREE + fb), (fuses / NF - 1) & 1u))
+              !PWAIT_MBAR(bar(B_F_FREE + fb), (fuses / NF - 1) & 1u))
             dead = true;
           tc_fence_after();
           for (int h = 0; h < 2; ++h) {
             const uint32_t s = ppos % NS2;
-            if (!dead && !mbar_wait_fast(bar(B_P2_FULL + s), (ppos / NS2) & 1u)) dead = true;
+            if (!dead && !PWAIT_MBAR(bar(B_P2_FULL + s), (ppos / NS2) & 1u)) dead = true;
             tc_fence_after();
             if (!dead) {
               const uint64_t dA2 = sdesc(su32(base + lay.p2) + s * P2U, P2U / 2, 1024);   // MN-major: features x rows
@@ -584,8 +593,8 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
         const int slot = i % RING_R;
         const unsigned use = static_cast<unsigned>(i / RING_R);
         // the previous use of the slot has been reduced (the reducers read before they count)
-        if (use >= 1 && !dead && !wait_geq(c_reduced(slot), static_cast<unsigned>(S) * use)) dead = true;
-        if (!dead && !mbar_wait_fast(bar(B_D1_FULL + d), static_cast<uint32_t>(i / ND1) & 1u)) dead = true;
+        if (use >= 1 && !dead && !PWAIT_GEQ(c_reduced(slot), static_cast<unsigned>(S) * use)) dead = true;
+        if (!dead && !PWAIT_MBAR(bar(B_D1_FULL + d), static_cast<uint32_t>(i / ND1) & 1u)) dead = true;
         tc_fence_after();
         float* dstp = part_g + (static_cast<int64_t>(slot) * S + j) * L * GR_ROWS;
         const uint32_t d1 = tmem + static_cast<uint32_t>(d * L) + (static_cast<uint32_t>(q * 32) << 16);
@@ -645,7 +654,7 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
         for (int i = 0; i < nt; ++i) {
           for (int u = 0; u < nu; ++u) {
             const uint32_t fb = fuses % NF;
-            if (!dead && !mbar_wait_fast(bar(B_F_FULL + fb), (fuses / NF) & 1u)) dead = true;
+            if (!dead && !PWAIT_MBAR(bar(B_F_FULL + fb), (fuses / NF) & 1u)) dead = true;
             tc_fence_after();
             const uint32_t hb = tHrun + static_cast<uint32_t>(u * L) + lq;
             const uint32_t fbase = tF + fb * static_cast<uint32_t>(L) + lq;
@@ -687,7 +696,7 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
         uint32_t drains = 0;
         for (int i = 0; i < nt; ++i) {
           if (!drain_tile(i)) continue;
-          if (!dead && !mbar_wait_fast(bar(B_F_FULL), drains & 1u)) dead = true;
+          if (!dead && !PWAIT_MBAR(bar(B_F_FULL), drains & 1u)) dead = true;
           tc_fence_after();
           store_h(drains > 0);
           tc_fence_before();
@@ -723,8 +732,8 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
       const int64_t row0 = (tile - a.seg[sgi].tile0) * GR_ROWS;
       const int64_t mseg = a.seg[sgi].m;
       if (rt == 0) {
-        bool ok = dead || wait_geq(c_arrived(slot), static_cast<unsigned>(S) * (use + 1));
-        if (ok && use >= 1 && !dead) ok = wait_geq(c_loaded(slot), static_cast<unsigned>(S) * use);
+        bool ok = dead || PWAIT_GEQ(c_arrived(slot), static_cast<unsigned>(S) * (use + 1));
+        if (ok && use >= 1 && !dead) ok = PWAIT_GEQ(c_loaded(slot), static_cast<unsigned>(S) * use);
         red_go = ok ? 1u : 0u;
       }
       named_bar(2, RED_T);
@@ -875,9 +884,9 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
         uint16_t* img_t = img_cta + static_cast<int64_t>(ri) * a.nbmax * (BLK16 / 2);
         for (int b = 0; b < NB; ++b) {
           const uint32_t p = opos & 1u;
-          if (!dead && !mbar_wait_fast(bar(B_OP_FULL + p), (opos >> 1) & 1u)) dead = true;
+          if (!dead && !PWAIT_MBAR(bar(B_OP_FULL + p), (opos >> 1) & 1u)) dead = true;
           if (b == 0 && i >= IMG_R) {
-            if (!dead && !mbar_wait_fast(bar(B_IMG_FREE + ri), static_cast<uint32_t>(i / IMG_R - 1) & 1u)) dead = true;
+            if (!dead && !PWAIT_MBAR(bar(B_IMG_FREE + ri), static_cast<uint32_t>(i / IMG_R - 1) & 1u)) dead = true;
             fence_proxy_async_global();   // the slot's discards before the bulk writes of the new tile
           }
           if (!dead) bulk_s2g_hint(img_t + static_cast<int64_t>(b) * (BLK16 / 2), su32(base + lay.op) + p * BLK16,
@@ -908,7 +917,7 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
       const float xs = INP == IN_F8 ? a.seg[sgi].dscale * op_scale : op_scale;   // stored value -> scaled operand
       for (int b = 0; b < NB; ++b) {
         const uint32_t p = opos & 1u;
-        if (opos >= 2 && !dead && !mbar_wait_fast(bar(B_OP_EMPTY + p), ((opos >> 1) - 1) & 1u)) dead = true;
+        if (opos >= 2 && !dead && !PWAIT_MBAR(bar(B_OP_EMPTY + p), ((opos >> 1) - 1) & 1u)) dead = true;
         uint8_t* op = base + lay.op + p * BLK16;
         // (x - c) s = fma(x, s, -c s) rounds once like the subtraction does (s a power of two; for
         // FP8, x = code and s = block scale x s, exact because the code has 4 significant bits
@@ -930,7 +939,7 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
         };
         for (int hf = 0; hf < SPB; ++hf) {
           const uint32_t s = spos % a.ns1;
-          if (!dead && !mbar_wait_fast(bar(B_S1_FULL + s), (spos / a.ns1) & 1u)) dead = true;
+          if (!dead && !PWAIT_MBAR(bar(B_S1_FULL + s), (spos / a.ns1) & 1u)) dead = true;
           const uint8_t* stg = base + lay.st1 + s * STG;
           if constexpr (INP == IN_F32) {
             // 128-byte rows of 32 features: thread = (8-feature piece cq, rows rb + 32 k)
@@ -1017,6 +1026,8 @@ __global__ void __launch_bounds__(GRP_NT, 1) sketch_grp_kernel(const __grid_cons
       if (ct == 0) GRP_TRACE(i, 2);
     }
   }
+#undef PWAIT_MBAR
+#undef PWAIT_GEQ
   if (dead) atomicOr(a.flags, 2);
   tc_fence_before();
   __syncthreads();
@@ -1092,6 +1103,14 @@ __global__ void __launch_bounds__(GRR_T) gram_rows_kernel(const float* __restric
         out[c2 * L + c1] = val;
       }
   }
+}
+
+// the self-test of the bounded waits: a counter nothing writes, and the outcome
+__device__ unsigned g_never_written = 0;
+__device__ int g_selftest_result = 0;
+
+__global__ void wait_selftest_kernel(uint64_t limit_ns) {
+  if (threadIdx.x == 0) g_selftest_result = wait_geq(&g_never_written, 1u, limit_ns) ? 1 : 2;
 }
 
 thread_local char g_grp_reason[192] = "";
@@ -1218,6 +1237,17 @@ size_t grp_gbuf_elems(const GrpConfig& c, int L, int fmt) {
   return static_cast<size_t>(c.NG) * RING_R * (fmt == FMT_F16 ? 2 : 1) * 2 * L * 64;
 }
 size_t grp_cnt_elems(const GrpConfig& c) { return static_cast<size_t>(c.NG) * RING_R * 3; }
+
+cudaError_t grp_wait_selftest(uint64_t limit_ns, cudaStream_t st, bool* ran_out) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(limit_ns);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int r = 0;
+  e = cudaMemcpyFromSymbolAsync(&r, g_selftest_result, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  *ran_out = r == 2;
+  return e;
+}
 // G' rows of one launch when the Gram matrix is formed after it: the tiles of every block a
 // launch can hold (the batch closes at kTcPendingRows rows; a block has at most
 // max_block_rows rows and one ragged tile)
@@ -1294,6 +1324,7 @@ cudaError_t grp_pass(const State& s, const TcWork& w, const TcPending& pend, cud
   args.gram_part = w.gram_part;
   args.sG_part = w.sG_part;
   args.flags = s.flags;
+  args.wait_ns = w.wait_ns;
   args.trace = nullptr;
 #ifdef SPCA_GRP_TRACE
   static unsigned long long* dtrace = nullptr;

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -194,11 +195,37 @@ spca_status fail(spca_session* s, spca_status st, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(s, SPCA_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
+// Allocation-failure injection for tests of the error paths: with SPCA_FAIL_ALLOC_AT=N in the
+// environment, the N-th device allocation (from 0) of a spca_create call reports
+// cudaErrorMemoryAllocation without allocating. Armed per call, on the calling thread.
+thread_local int64_t t_fail_alloc_at = -1;
+thread_local int64_t t_alloc_count = 0;
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
+  if (t_fail_alloc_at >= 0 && t_alloc_count++ == t_fail_alloc_at) return cudaErrorMemoryAllocation;
   return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+struct AllocFailArm {   // arms the injection for one spca_create, disarms on every exit
+  AllocFailArm() {
+    const char* v = std::getenv("SPCA_FAIL_ALLOC_AT");
+    t_fail_alloc_at = (v && *v) ? std::atoll(v) : -1;
+    t_alloc_count = 0;
+  }
+  ~AllocFailArm() { t_fail_alloc_at = -1; }
+};
+
+// the grouped kernel's wait limit: SPCA_WAIT_LIMIT_MS (1 .. 60000), else half a second
+uint64_t wait_limit_ns() {
+  const char* v = std::getenv("SPCA_WAIT_LIMIT_MS");
+  if (!v || !*v) return 500000000ull;
+  long long ms = std::atoll(v);
+  if (ms < 1) ms = 1;
+  if (ms > 60000) ms = 60000;
+  return static_cast<uint64_t>(ms) * 1000000ull;
 }
 
 void free_all(spca_session* s) {
@@ -399,6 +426,7 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
   spca_session* s = nullptr;
   if (!out) return fail(nullptr, SPCA_E_INVALID, "out is NULL");
   *out = nullptr;
+  const AllocFailArm arm;
   if (n < 1 || k < 1 || p < 0) return fail(nullptr, SPCA_E_INVALID, "need n >= 1, k >= 1, p >= 0 (n=%lld k=%d p=%d)",
                                            (long long)n, k, p);
   const int64_t l = static_cast<int64_t>(k) + p;
@@ -479,6 +507,7 @@ spca_status spca_create(int64_t n, int32_t k, int32_t p, uint64_t seed, const sp
     const int fmt = t.fmt;
     t = tcw0;   // the configurations (the grouped kernel preferred, the others as fallbacks)
     t.fmt = fmt;
+    t.wait_ns = wait_limit_ns();
     CC(dalloc(&t.om16, size_t(tcz.npad) * L));
     CC(dalloc(&t.scale, 1));
     CC(dalloc(&t.scale_bits, 1));
@@ -793,6 +822,17 @@ spca_status spca_left_vectors_pass(spca_session* s, const void* rows, int64_t m,
   }
   CU(launch_u_pass(rows, dtype, scale, m, s->n, ld, s->shift, s->upass_W, s->L, s->k, s->upass_corr, gpart, gp_rows,
                    U, ldu, s->stream));
+  return SPCA_OK;
+}
+
+spca_status spca_wait_selftest(int64_t limit_ns, void* cuda_stream) {
+  if (limit_ns < 1 || limit_ns > 60000000000LL)
+    return fail(nullptr, SPCA_E_INVALID, "spca_wait_selftest: limit_ns must be in [1, 6e10]");
+  bool ran_out = false;
+  const cudaError_t e = grp_wait_selftest(static_cast<uint64_t>(limit_ns), static_cast<cudaStream_t>(cuda_stream),
+                                          &ran_out);
+  if (e != cudaSuccess) return fail(nullptr, SPCA_E_CUDA, "spca_wait_selftest: %s", cudaGetErrorString(e));
+  if (ran_out) return fail(nullptr, SPCA_E_TIMEOUT, "the bounded wait gave up after %lld ns", (long long)limit_ns);
   return SPCA_OK;
 }
 

@@ -139,6 +139,7 @@ struct TcWork {
   unsigned* cnt;         // grouped kernel: the groups' counters
   float* gfull;          // grouped kernel without in-kernel Gram: the launch's G' rows (tiles x 128 x L)
   int64_t gfull_rows;    // rows gfull holds
+  uint64_t wait_ns = 500000000ull;   // grouped kernel: limit of each pipeline wait
   int fmt;               // 0: BF16 operands; 1: FP16 operands on values scaled by *scale
   float* scale;          // device scalar: power-of-two operand scale (FP16 form)
   unsigned int* scale_bits;   // device scratch for the largest row norm
@@ -189,6 +190,9 @@ size_t grp_part_elems(const GrpConfig& c, int L);
 size_t grp_gbuf_elems(const GrpConfig& c, int L, int fmt);
 size_t grp_cnt_elems(const GrpConfig& c);
 size_t grp_gfull_rows(const GrpConfig& c, int64_t max_block_rows);
+// One thread polls a device counter that nothing writes with the pipeline's bounded wait;
+// *ran_out = true when the wait gave up after limit_ns (the expected outcome).
+cudaError_t grp_wait_selftest(uint64_t limit_ns, cudaStream_t st, bool* ran_out);
 cudaError_t grp_pass(const State& s, const TcWork& w, const TcPending& pend, cudaStream_t st, Prof* prof,
                      bool* used);
 const char* tc3_config_reason();

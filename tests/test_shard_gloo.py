@@ -6,6 +6,8 @@ session; ``shard.merge_across_ranks`` gathers the checkpoints on rank 0 in rank 
 adds them there. The merged accumulators must equal those of one process over all rows
 (the sketch is a sum over rows). The GPU merge itself (spca_merge with the shift rebase) is
 covered by tests/test_gpu_merge.py; here all ranks use one shift, so merging is addition.
+A rank that dies before the exchange (killed, no clean shutdown) makes the exchange fail on
+rank 0 within the process group's timeout instead of waiting for it forever.
 """
 import io
 import os
@@ -113,3 +115,49 @@ def test_sharded_accumulators_merge_to_one_pass(world):
     assert got["m"] == m
     for k in KEYS:
         np.testing.assert_allclose(got[k], getattr(whole, k), rtol=1e-12, atol=1e-10)
+
+
+def _worker_fail(rank, world, port, out):
+    """Rank 1 dies before the exchange step (a crash: no clean shutdown); rank 0 must see
+    an error from the exchange within the process group's timeout, not wait forever."""
+    import datetime
+    import sys
+    import time
+    sys.path.insert(0, ROOT)
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    import torch.distributed as dist
+    from paper_1704_07669_gb300 import shard as sh
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)
+    t0 = time.time()
+    try:
+        sh.merge_across_ranks(_FakeSession(_Acc()), scratch=_FakeSession(), merge=_add)
+        out.put(("no error", time.time() - t0))
+    except Exception as exc:   # noqa: BLE001 - the failure is the expected outcome
+        out.put((type(exc).__name__, time.time() - t0))
+    out.close()
+    out.join_thread()   # the result is sent before the hard exit
+    os._exit(0)
+
+
+class _Acc:
+    def __init__(self):
+        self.m = 1
+        for k in KEYS:
+            setattr(self, k, np.zeros(3))
+
+
+def test_a_rank_that_dies_before_the_exchange_is_detected():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_fail, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    what, dt = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert procs[1].exitcode == 3
+    assert what != "no error"
+    assert dt < 60.0
