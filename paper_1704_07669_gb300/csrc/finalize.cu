@@ -904,6 +904,112 @@ __device__ void blk_trinv_lower(const double* Lm, double* Linv, int d, int ld) {
   __syncthreads();
 }
 
+// The same factor and inverse, register-resident, for d(d+1)/2 <= blockDim.x * EPT: symmetric
+// Gaussian elimination without square roots. Step k subtracts m_ik = x_ik / x_kk times row k
+// from every row i > k of the trailing lower triangle (A = M D M^T, M unit lower triangular)
+// and applies the same row operations to Y (the identity first), which ends as M^-1; the
+// factor is M D^1/2, so its inverse is D^-1/2 M^-1 (row i scaled by x_ii^-1/2 at the end).
+// X's trailing part and Y's finished part share one lower-triangular array Z (entry (i, j)
+// is X's while j > k and Y's once j <= k: column k of X turns into column k of Y, -m_ik),
+// held in registers, EPT entries per thread at fixed places. A step needs column k of Z
+// (rows >= k) and row k of Y (columns < k): disjoint index ranges, so one vector u_k holds
+// both, which the owners of those entries leave in shared memory (two copies by parity) at
+// the end of the step before. Every thread loads all its operands first, then computes,
+// then stores, so that a step costs one load latency and one block barrier.
+// False, uniformly, if a pivot is <= tol.
+template <int EPT>
+__device__ bool blk_chol_inv32_reg(const float* X, float* Y, int d, int ld, float tol) {
+  __shared__ float piv[kMaxL];
+  __shared__ float uvec[2][kMaxL];   // u_k: column k of Z at indices >= k, row k of Y below k
+  const int nt = blockDim.x, tri = d * (d + 1) / 2;
+  float z[EPT];
+  int zi[EPT], zj[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = threadIdx.x + q * nt;
+    zi[q] = -1;
+    zj[q] = 0;
+    z[q] = 0.f;
+    if (e < tri) {   // e -> (i, j), j <= i, row by row
+      int i = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) - 1.f) * 0.5f);
+      while (i * (i + 1) / 2 > e) --i;
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      const int j = e - i * (i + 1) / 2;
+      zi[q] = i;
+      zj[q] = j;
+      z[q] = X[i * ld + j];
+      if (j == 0) uvec[0][i] = z[q];
+    }
+  }
+  __syncthreads();
+#ifdef SPCA_FIN_TRACE
+  long long tt[4] = {0, 0, 0, 0};
+  const long long tstart = clock64();
+#endif
+  for (int k = 0; k < d; ++k) {
+#ifdef SPCA_FIN_TRACE
+    const long long q0 = clock64();
+#endif
+    const float* u = uvec[k & 1];
+    float* un = uvec[(k + 1) & 1];
+    const float p = u[k];
+    if (!(p > tol)) return false;   // the same value in every thread
+    if (threadIdx.x == 0) piv[k] = p;
+    const float inv = 1.f / p;
+    float mi[EPT], rj[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {   // loads (u at zi > k is column k, at zj: column or row)
+      const bool act = zi[q] > k;
+      mi[q] = act ? u[zi[q]] : 0.f;
+      rj[q] = act ? u[zj[q]] : 0.f;
+    }
+#ifdef SPCA_FIN_TRACE
+    float chk = inv;
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) chk += mi[q] + rj[q];
+    if (chk == 123.456f) piv[0] = chk;
+    const long long q1 = clock64();
+#endif
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {   // the updates: column k of Y; X's trailing part and Y's rows
+      if (zi[q] > k) {
+        const float m = mi[q] * inv;
+        z[q] = zj[q] == k ? -m : fmaf(-m, rj[q], z[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {   // u_{k+1}: the next column (indices >= k + 1), the next row of Y
+      if (zi[q] > k && (zj[q] == k + 1 || (zi[q] == k + 1 && zj[q] <= k))) un[zj[q] == k + 1 ? zi[q] : zj[q]] = z[q];
+    }
+#ifdef SPCA_FIN_TRACE
+    const long long q2 = clock64();
+#endif
+    __syncthreads();
+#ifdef SPCA_FIN_TRACE
+    const long long q3 = clock64();
+    tt[0] += q1 - q0;
+    tt[1] += q2 - q1;
+    tt[2] += q3 - q2;
+#endif
+  }
+#ifdef SPCA_FIN_TRACE
+  if (threadIdx.x == 0 || threadIdx.x == 480)
+    printf("chol reg d=%d thr %d: total %lld (loads+div %lld, update+store %lld, barrier %lld)\n", d, threadIdx.x,
+           clock64() - tstart, tt[0], tt[1], tt[2]);
+#endif
+  const int nw = nt >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < d; i += nw)
+    for (int j = lane; j < d; j += 32) Y[i * ld + j] = 0.f;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int i = zi[q], j = zj[q];
+    if (i >= 0) Y[i * ld + j] = (i == j ? 1.f : z[q]) * rsqrtf(piv[i]);
+  }
+  __syncthreads();
+  return true;
+}
+
 // FP32 Cholesky of X (lower triangle, right-looking) and, alongside, Y = the inverse of the
 // factor: the row operations of the forward substitution L Y = I are applied to Y (the
 // identity first) step by step. Two block barriers per step. False, uniformly, if a pivot
@@ -1720,7 +1826,15 @@ __global__ void __launch_bounds__(POL_T) chol_inv_f32_kernel(const double* __res
   __syncthreads();
   dm = 0.f;
   for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) dm = fmaxf(dm, wmax[w]);
-  bool ok = rank_ok && dm > 0.f && isfinite(dm) && blk_chol_inv32(X, Yf, l, ld, static_cast<float>(tol_rel) * dm);
+  const float tol = static_cast<float>(tol_rel) * dm;
+  const int tri = l * (l + 1) / 2, cap = static_cast<int>(blockDim.x);
+  bool ok = rank_ok && dm > 0.f && isfinite(dm);
+  if (ok) {   // the register-resident elimination where the triangle fits the block's registers
+    if (tri <= 4 * cap) ok = blk_chol_inv32_reg<4>(X, Yf, l, ld, tol);
+    else if (tri <= 8 * cap) ok = blk_chol_inv32_reg<8>(X, Yf, l, ld, tol);
+    else if (tri <= 17 * cap) ok = blk_chol_inv32_reg<17>(X, Yf, l, ld, tol);
+    else ok = blk_chol_inv32(X, Yf, l, ld, tol);
+  }
   __syncthreads();
   for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
     const int i = e / L, j = e % L;
@@ -1966,13 +2080,22 @@ cudaError_t power_omega_run(const State& s, const FinalWork& f, int64_t m, cudaS
 // centring term matches the products it corrects; 0 without centring).
 __global__ void upass_w_kernel(const double* __restrict__ V, const double* __restrict__ sigma, int64_t n, int k, int L,
                                float* __restrict__ W) {
-  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < n * L;
+  __shared__ double inv[kMaxL];   // 1 / sigma_j once per block (FP64 divisions are slow here)
+  for (int j = threadIdx.x; j < L; j += blockDim.x) inv[j] = (j < k && sigma[j] > 0.0) ? 1.0 / sigma[j] : 0.0;
+  __syncthreads();
+  // a thread per (row c, 4 columns): V's columns read coalesced across threads, a float4 of W out
+  const int64_t nq = n * (L / 4);
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < nq;
        idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t c = idx / L;
-    const int j = static_cast<int>(idx - c * L);
-    float w = 0.f;
-    if (j < k && sigma[j] > 0.0) w = static_cast<float>(V[static_cast<int64_t>(j) * n + c] / sigma[j]);
-    W[idx] = w;
+    const int jq = static_cast<int>(idx / n);
+    const int64_t c = idx - static_cast<int64_t>(jq) * n;
+    float w[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int j = 4 * jq + t;
+      w[t] = j < k ? static_cast<float>(V[static_cast<int64_t>(j) * n + c] * inv[j]) : 0.f;
+    }
+    *reinterpret_cast<float4*>(W + c * L + 4 * jq) = make_float4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -1992,9 +2115,12 @@ __global__ void upass_corr_kernel(const float* __restrict__ W, const double* __r
   if (threadIdx.x == 0) corr[j] = m > 0 ? red[0] / static_cast<double>(m) : 0.0;
 }
 
-cudaError_t launch_upass_prep(const State& s, const double* V, const double* sigma, int k, int64_t m_center,
-                              float* W, double* corr, cudaStream_t st) {
-  upass_w_kernel<<<grid_for(s.n * s.L, 256), 256, 0, st>>>(V, sigma, s.n, k, s.L, W);
+cudaError_t launch_upass_w(const State& s, const double* V, const double* sigma, int k, float* W, cudaStream_t st) {
+  upass_w_kernel<<<grid_for(s.n * (s.L / 4), 256), 256, 0, st>>>(V, sigma, s.n, k, s.L, W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_upass_corr(const State& s, const float* W, int64_t m_center, double* corr, cudaStream_t st) {
   upass_corr_kernel<<<s.L, 256, 0, st>>>(W, s.colsum, m_center, s.n, s.L, corr);
   return cudaGetLastError();
 }

@@ -149,6 +149,7 @@ struct spca_session {
   float* upass_W = nullptr;       // n x L: V Sigma^-1 of the last finalize (FP32), for spca_left_vectors_pass
   double* upass_corr = nullptr;   // L: its centring term
   float* upass_gpart = nullptr;   // tensor-core sessions: split-K partials of the second pass (made on first use)
+  bool upass_corr_ready = false;  // upass_corr formed since the last finalize
 
   // host staging
   void* pinned[2] = {nullptr, nullptr};
@@ -727,7 +728,8 @@ spca_status spca_finalize(spca_session* s, double* sigma, double* V, int32_t out
   double* vd = out_on_device ? V : s->fin_V;
   CU(finalize_run(s->state(), s->fin, s->opt.center ? s->m : 0, s->k, sd, vd, s->stream, &s->prof, s->m,
                   s->opt.center != 0));
-  CU(launch_upass_prep(s->state(), vd, sd, s->k, s->opt.center ? s->m : 0, s->upass_W, s->upass_corr, s->stream));
+  CU(launch_upass_w(s->state(), vd, sd, s->k, s->upass_W, s->stream));
+  s->upass_corr_ready = false;
   if (!out_on_device) {
     CU(cudaMemcpyAsync(sigma, sd, sizeof(double) * s->k, cudaMemcpyDeviceToHost, s->stream));
     CU(cudaMemcpyAsync(V, vd, sizeof(double) * s->n * s->k, cudaMemcpyDeviceToHost, s->stream));
@@ -819,6 +821,10 @@ spca_status spca_left_vectors_pass(spca_session* s, const void* rows, int64_t m,
       }
     }
     gpart = s->upass_gpart;
+  }
+  if (!s->upass_corr_ready) {   // the centring term, once per finalize (the state is unchanged since)
+    CU(launch_upass_corr(s->state(), s->upass_W, s->opt.center ? s->m : 0, s->upass_corr, s->stream));
+    s->upass_corr_ready = true;
   }
   CU(launch_u_pass(rows, dtype, scale, m, s->n, ld, s->shift, s->upass_W, s->L, s->k, s->upass_corr, gpart, gp_rows,
                    U, ldu, s->stream));

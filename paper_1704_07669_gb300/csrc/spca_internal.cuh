@@ -234,8 +234,8 @@ cudaError_t power_omega_run(const State& s, const FinalWork& f, int64_t m, cudaS
 
 // the l x k map to U (and its centring term) from the last finalize's R^-T, eigenvectors and
 // column signs; m: the rows of the centring (0 when centering is off)
-cudaError_t launch_upass_prep(const State& s, const double* V, const double* sigma, int k, int64_t m_center,
-                              float* W, double* corr, cudaStream_t st);
+cudaError_t launch_upass_w(const State& s, const double* V, const double* sigma, int k, float* W, cudaStream_t st);
+cudaError_t launch_upass_corr(const State& s, const float* W, int64_t m_center, double* corr, cudaStream_t st);
 cudaError_t launch_u_pass(const void* rows, int dtype, float scale, int64_t m, int64_t n, int64_t ld,
                           const float* shift, const float* W, int L, int k, const double* corr, float* Gpart,
                           int64_t gp_rows, double* U, int64_t ldu, cudaStream_t st);
