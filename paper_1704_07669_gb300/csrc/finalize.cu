@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(256) bt_and_c_kernel(const double* __restrict_
   constexpr int G = 256 / 64;       // row groups; thread = (row group, column i mod 64)
   constexpr int RPT = BT_ROWS / G;  // rows per thread
   const int r = info[0];
+  const bool lower = info[1] == 0;   // T from the Cholesky route (the eigen route's T is full)
   const int tri = r * (r + 1) / 2;
   const bool whole = tcc >= l;      // all of T^T staged once
   double* out = Cpart + static_cast<int64_t>(blockIdx.x) * L * L;
@@ -110,7 +111,10 @@ __global__ void __launch_bounds__(256) bt_and_c_kernel(const double* __restrict_
         double acc[RPT];
 #pragma unroll
         for (int u = 0; u < RPT; ++u) acc[u] = 0.0;
-        for (int c = c0; c < c1; ++c) {
+        // the Cholesky route's T = R^-T is lower triangular (exact zeros above the diagonal):
+        // columns c > i add nothing
+        const int ce = (lower && c1 > i + 1) ? i + 1 : c1;
+        for (int c = c0; c < ce; ++c) {
           const double t = sT[(c - c0) * L + i];
 #pragma unroll
           for (int u = 0; u < RPT; ++u) acc[u] = fma(t, sH[(grp + G * u) * L + c], acc[u]);
@@ -373,9 +377,17 @@ __device__ __forceinline__ void jacobi_rotation(T app, T aqq, T apq, T& c, T& s)
 // FP32 rotation for the FP32 solve: the same formulas with the two divisions taken by the
 // fast reciprocal (|2 a_pq| is far from the range where it loses accuracy; an overflowing
 // theta gives t = 0, no rotation) and one Newton step on c.
+// sqrt.approx: t need not be exact (the next sweeps absorb a slightly wrong angle; c^2 + s^2 = 1
+// comes from the rsqrt and its Newton step below), and an infinite theta^2 gives t = 0
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ void jacobi_rotation32(float app, float aqq, float apq, float& c, float& s) {
   const float theta = __fdividef(aqq - app, 2.f * apq);
-  const float t = __fdividef(theta >= 0.f ? 1.f : -1.f, fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+  const float t = __fdividef(theta >= 0.f ? 1.f : -1.f, fabsf(theta) + sqrt_approx(fmaf(theta, theta, 1.f)));
   const float x = fmaf(t, t, 1.f);
   float y = rsqrtf(x);
   y = y * fmaf(-0.5f * x * y, y, 1.5f);
@@ -1307,8 +1319,8 @@ __device__ __forceinline__ float2 mixed_rotation(float2 app, float2 aqq, float a
   rotated = work;
   del = make_float2(0.f, 0.f);
   if (!work) return make_float2(1.f, 0.f);
-  const float theta = __fdiv_rn(gd.x, 2.f * apq);
-  const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+  const float theta = __fdividef(gd.x, 2.f * apq);
+  const float t = __fdividef(theta >= 0.f ? 1.f : -1.f, fabsf(theta) + sqrt_approx(fmaf(theta, theta, 1.f)));
   const float x = fmaf(t, t, 1.f);
   float y = rsqrtf(x);
   y = y * fmaf(-0.5f * x * y, y, 1.5f);
