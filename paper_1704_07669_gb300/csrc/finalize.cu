@@ -971,9 +971,8 @@ __device__ bool blk_chol_inv32_reg(const float* X, float* Y, int d, int ld, floa
     float mi[EPT], rj[EPT];
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {   // loads (u at zi > k is column k, at zj: column or row)
-      const bool act = zi[q] > k;
-      mi[q] = act ? u[zi[q]] : 0.f;
-      rj[q] = act ? u[zj[q]] : 0.f;
+      mi[q] = u[zi[q] > k ? zi[q] : k];
+      rj[q] = u[zj[q]];
     }
 #ifdef SPCA_FIN_TRACE
     float chk = inv;
@@ -991,7 +990,8 @@ __device__ bool blk_chol_inv32_reg(const float* X, float* Y, int d, int ld, floa
     }
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {   // u_{k+1}: the next column (indices >= k + 1), the next row of Y
-      if (zi[q] > k && (zj[q] == k + 1 || (zi[q] == k + 1 && zj[q] <= k))) un[zj[q] == k + 1 ? zi[q] : zj[q]] = z[q];
+      if (zj[q] == k + 1 && zi[q] > k) un[zi[q]] = z[q];
+      else if (zi[q] == k + 1 && zj[q] <= k) un[zj[q]] = z[q];
     }
 #ifdef SPCA_FIN_TRACE
     const long long q2 = clock64();
