@@ -378,39 +378,56 @@ def run_serving(spca, dev, seconds=3.0, loads=(0.25, 0.5, 0.75), seed=17040769 +
     mid = next((x for x in sweep if abs(x["load"] - 0.5) < 1e-9), sweep[0])
     out.update({k_: v for k_, v in mid.items() if k_ != "load"})
     out["load_sweep"] = sweep
-    out.update({"latency_note": "percentiles over each Poisson phase (plus one 256-row admission block per "
-                                "session before it) and the final finalize of every session",
+    out.update({"latency_note": "percentiles over each Poisson phase (sessions finalized, closed and replaced "
+                                "inside it), one 256-row admission block per session before it and the "
+                                "final finalize of every session",
                 "tc_sessions": int(sum(1 for i in range(S) if tensor_core_takes(spca, int(ns[i]), int(ls[i]))))})
     del pools
     return out
 
 
-def _serving_phase(spca, sat, mean_bytes, load, seconds, ns, ls, S, block, rng, pools):
-    """One Poisson phase of the serving measurement on a fresh server (all sessions admitted first)."""
+def _serving_phase(spca, sat, mean_bytes, load, seconds, ns, ls, S, block, rng, pools, churn_every=25, churned=8):
+    """One Poisson phase of the serving measurement on a fresh server (all sessions admitted
+    first). Sessions also come and go inside the timed window: every `churn_every`-th arrival
+    finalizes and closes one of the first `churned` sessions and opens a new session of the
+    same shape in its place; one session per such shape is reserved before the window, so
+    these admissions reset pooled sessions instead of allocating."""
     rate = load * sat * 1e9 / mean_bytes          # requests per second
     with spca.Server(max_block_rows=4096) as sv:
         ids = [sv.open(int(ns[i]), int(ls[i]) - 10, 10, 900 + i) for i in range(S)]
         for i in range(S):
             sv.wait(sv.update(ids[i], pools[i][:256]), 300.0)
+        for i in range(churned):
+            sv.wait(sv.reserve(int(ns[i]), int(ls[i]) - 10, 10, 1), 300.0)
         base = sv.stats()
         # Poisson arrivals at `load` of saturation
-        tickets = []
+        tickets, fins = [], []
         t_next = time.perf_counter()
         t_end = t_next + seconds
         nbytes = 0.0
+        n_req = n_churn = 0
         t0 = time.perf_counter()
         while t_next < t_end:
             while time.perf_counter() < t_next:
                 pass
-            i = int(rng.integers(0, S))
-            rows, b = block(i)
-            nbytes += b
-            tickets.append(sv.update(ids[i], rows))
+            n_req += 1
+            if n_req % churn_every == 0:
+                i = int(rng.integers(0, churned))
+                k = int(ls[i]) - 10
+                sig_h, V_h = np.zeros(k), np.zeros((k, int(ns[i])))
+                fins.append((sig_h, V_h, sv.finalize(ids[i], sig_h, V_h)))
+                sv.close_session(ids[i])
+                n_churn += 1
+                ids[i] = sv.open(int(ns[i]), k, 10, 5000 + n_churn)
+            else:
+                i = int(rng.integers(0, S))
+                rows, b = block(i)
+                nbytes += b
+                tickets.append(sv.update(ids[i], rows))
             t_next += rng.exponential(1.0 / rate)
         for t in tickets:
             sv.wait(t, 300.0)
         wall = time.perf_counter() - t0
-        fins = []
         for i in range(S):
             k = int(ls[i]) - 10
             sig_h, V_h = np.zeros(k), np.zeros((k, int(ns[i])))
@@ -423,6 +440,9 @@ def _serving_phase(spca, sat, mean_bytes, load, seconds, ns, ls, S, block, rng, 
             "updates": int(n_upd), "achieved_GBps": nbytes / wall / 1e9,
             "update_p50_ms": st["update_p50_ms"], "update_p99_ms": st["update_p99_ms"],
             "finalize_p50_ms": st["finalize_p50_ms"], "finalize_p99_ms": st["finalize_p99_ms"],
+            "sessions_replaced_in_window": n_churn,
+            "admissions_from_pool_in_window": int(st["admissions_from_pool"] - base["admissions_from_pool"]),
+            "sessions_created_in_window": int(st["sessions_created"] - base["sessions_created"]),
             "device_budget_bytes": st["device_bytes_budget"]}
 
 

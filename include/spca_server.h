@@ -13,7 +13,12 @@
  *    the row blocks one session has waiting are folded into one launch of the fused
  *    tensor-core pass,
  *  - records the latency of every update and finalize request (submission to completion)
- *    and reports p50/p99.
+ *    and reports p50/p99,
+ *  - keeps closed sessions, and sessions reserved ahead of time, in a pool with their device
+ *    and pinned memory: an admission of the same (n, k, p) and math form takes one and
+ *    resets its state for the new seed (as spca_reset), so it allocates nothing on the
+ *    worker while other sessions run. Pooled sessions count against the budget and are
+ *    freed, oldest first, when an admission of another shape needs their room.
  * A single worker thread owns all sessions and all CUDA work; the calls below only queue
  * requests and may come from any host thread. Rows must be device-resident FP32
  * (row-major, leading dimension ld); the caller keeps them valid and unmodified until the
@@ -51,7 +56,10 @@ typedef struct {
   double finalize_p50_ms, finalize_p99_ms;
   double rows_bytes;                             /* bytes of rows folded in so far */
   double active_seconds;                         /* wall time with at least one request in flight */
-  size_t device_bytes_in_use, device_bytes_budget;
+  size_t device_bytes_in_use, device_bytes_budget;   /* admitted sessions; the budget */
+  int64_t sessions_pooled;                       /* now */
+  int64_t admissions_from_pool, sessions_created;  /* so far (created: admissions and reserves) */
+  size_t device_bytes_pooled;                    /* now */
 } spca_server_stats;
 
 /* Fill *opt with the defaults. */
@@ -71,6 +79,18 @@ spca_status spca_server_create(const spca_server_options* opt, spca_server** out
 spca_status spca_server_open(spca_server* sv, int64_t n, int32_t k, int32_t p, uint64_t seed, int32_t* id);
 
 /*
+ * spca_server_reserve - queue the creation of `count` sessions of sizes (n, k, p) (math form
+ * chosen as for spca_server_open) into the pool, so that later opens of that shape are
+ * admitted without allocating. *ticket completes when they exist; its status is
+ * SPCA_E_NOMEM if the budget (admitted plus pooled sessions) cannot hold all of them (those
+ * made so far stay pooled) or the first failing spca_create's status.
+ * Errors: SPCA_E_INVALID (sizes, count < 1, NULL ticket), SPCA_E_NOMEM (one session alone
+ * exceeds the budget), SPCA_E_UNSUPPORTED (an explicit math form that does not fit),
+ * SPCA_E_STATE (the server is stopping).
+ */
+spca_status spca_server_reserve(spca_server* sv, int64_t n, int32_t k, int32_t p, int32_t count, uint64_t* ticket);
+
+/*
  * spca_server_update - queue m_i rows (device pointer, FP32, leading dimension ld >= n) for
  * session id; *ticket identifies the request. Errors: SPCA_E_INVALID.
  */
@@ -88,7 +108,8 @@ spca_status spca_server_finalize(spca_server* sv, int32_t id, double* sigma, dou
  * (SPCA_E_TIMEOUT if the wait timed out; the request itself goes on). */
 spca_status spca_server_wait(spca_server* sv, uint64_t ticket, double timeout_s);
 
-/* Close session id after its queued requests; its memory returns to the budget. */
+/* Close session id after its queued requests; the session goes to the pool (its memory stays
+ * allocated, counted as pooled) unless it had failed, in which case it is freed. */
 spca_status spca_server_close(spca_server* sv, int32_t id);
 
 /* Counters and latency percentiles so far. */

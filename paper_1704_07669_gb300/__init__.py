@@ -45,7 +45,9 @@ class ServerStats(ctypes.Structure):
                 ("update_p50_ms", ctypes.c_double), ("update_p99_ms", ctypes.c_double),
                 ("finalize_p50_ms", ctypes.c_double), ("finalize_p99_ms", ctypes.c_double),
                 ("rows_bytes", ctypes.c_double), ("active_seconds", ctypes.c_double),
-                ("device_bytes_in_use", ctypes.c_size_t), ("device_bytes_budget", ctypes.c_size_t)]
+                ("device_bytes_in_use", ctypes.c_size_t), ("device_bytes_budget", ctypes.c_size_t),
+                ("sessions_pooled", ctypes.c_int64), ("admissions_from_pool", ctypes.c_int64),
+                ("sessions_created", ctypes.c_int64), ("device_bytes_pooled", ctypes.c_size_t)]
 
 
 SPCA_SERVER_AUTO_MATH = -1
@@ -94,6 +96,7 @@ def lib():
             "spca_server_default_options": (None, [ctypes.POINTER(ServerOptions)]),
             "spca_server_create": (i32, [ctypes.POINTER(ServerOptions), ctypes.POINTER(vp)]),
             "spca_server_open": (i32, [vp, i64, i32, i32, u64, ctypes.POINTER(i32)]),
+            "spca_server_reserve": (i32, [vp, i64, i32, i32, i32, ctypes.POINTER(u64)]),
             "spca_server_update": (i32, [vp, i32, vp, i64, i64, ctypes.POINTER(u64)]),
             "spca_server_finalize": (i32, [vp, i32, vp, vp, ctypes.POINTER(u64)]),
             "spca_server_wait": (i32, [vp, u64, ctypes.c_double]),
@@ -460,6 +463,12 @@ class Server:
         _check_srv(lib().spca_server_open(self.handle, int(n), int(k), int(p), int(seed) & 0xFFFFFFFFFFFFFFFF,
                                           ctypes.byref(sid)))
         return sid.value
+
+    def reserve(self, n, k, p, count):
+        """Queue the creation of `count` pooled sessions of sizes (n, k, p); returns a ticket."""
+        t = ctypes.c_uint64(0)
+        _check_srv(lib().spca_server_reserve(self.handle, int(n), int(k), int(p), int(count), ctypes.byref(t)))
+        return t.value
 
     def update(self, sid, rows):
         """Queue a block of device-resident FP32 rows (a 2-D CUDA tensor); returns a ticket. The

@@ -1,7 +1,9 @@
 // The serving loop (include/spca_server.h): one worker thread owns the sessions and all CUDA
 // work; callers only queue requests. Each session runs on its own stream; the worker issues
 // whatever is queued for every admitted session, folds one session's waiting row blocks into
-// one launch of the pass, and polls events to complete requests.
+// one launch of the pass, and polls events to complete requests. Closed sessions (and those
+// reserved ahead of time) wait in a pool, keeping their device and pinned memory, so that an
+// admission of the same shape is a reset of their state instead of a round of allocations.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,7 +26,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-enum Kind { kOpen, kUpdate, kFinalize, kClose };
+enum Kind { kOpen, kUpdate, kFinalize, kClose, kReserve };
 
 struct Request {
   uint64_t ticket = 0;
@@ -34,6 +36,9 @@ struct Request {
   int64_t m = 0, ld = 0;
   double* sigma = nullptr;
   double* V = nullptr;
+  int64_t n = 0;                // reserve: shape, math, footprint and number of sessions
+  int k = 0, p = 0, math = 0, count = 0;
+  size_t bytes = 0;
   Clock::time_point t_submit;
 };
 
@@ -60,6 +65,49 @@ struct Slot {
   std::deque<Request> queue;    // not yet issued (worker)
   std::deque<Inflight> inflight;
 };
+
+// A session out of service: its handle and result buffers, kept for the next admission of
+// the same (n, k, p, math).
+struct Pooled {
+  int64_t n = 0;
+  int k = 0, p = 0, math = 0;
+  size_t bytes = 0;
+  spca_session* s = nullptr;
+  double* sig_dev = nullptr;
+  double* V_dev = nullptr;
+  double* res_host = nullptr;
+  int* flags_host = nullptr;
+
+  bool fits(const Slot& sl) const { return n == sl.n && k == sl.k && p == sl.p && math == sl.math; }
+};
+
+// Create the session and its result buffers; on failure, what was allocated stays in e.
+spca_status create_session(Pooled& e, uint64_t seed, int32_t max_block_rows) {
+  spca_options o;
+  spca_default_options(&o);
+  o.math = e.math;
+  o.max_block_rows = max_block_rows;
+  spca_status st = spca_create(e.n, e.k, e.p, seed, &o, &e.s);
+  const size_t vbytes = sizeof(double) * static_cast<size_t>(e.n) * e.k;
+  if (st == SPCA_OK && (cudaMalloc(&e.sig_dev, sizeof(double) * e.k) != cudaSuccess ||
+                        cudaMalloc(&e.V_dev, vbytes) != cudaSuccess ||
+                        cudaMallocHost(&e.res_host, sizeof(double) * e.k + vbytes) != cudaSuccess ||
+                        cudaMallocHost(&e.flags_host, sizeof(int)) != cudaSuccess)) {
+    cudaGetLastError();
+    st = SPCA_E_NOMEM;
+  }
+  return st;
+}
+
+void free_session(spca_session* s, double* sig_dev, double* V_dev, double* res_host, int* flags_host) {
+  if (s) spca_destroy(s);
+  if (sig_dev) cudaFree(sig_dev);
+  if (V_dev) cudaFree(V_dev);
+  if (res_host) cudaFreeHost(res_host);
+  if (flags_host) cudaFreeHost(flags_host);
+}
+
+void free_session(Pooled& e) { free_session(e.s, e.sig_dev, e.V_dev, e.res_host, e.flags_host); }
 
 struct TicketState {
   bool done = false;
@@ -94,16 +142,23 @@ struct spca_server {
   uint64_t next_ticket = 1;
   std::vector<double> lat_update, lat_finalize;
   int64_t updates_done = 0, finalizes_done = 0, admitted = 0, waiting = 0;
+  int64_t n_pooled = 0, from_pool = 0, created = 0;   // written by the worker under mu
+  size_t pooled_bytes = 0;
   double rows_bytes = 0.0, active_s = 0.0;
   bool stop = false;
   char worker_err[256] = "";       // text of the last failed request (guarded by mu)
   std::deque<int32_t> admission;   // worker
+  std::deque<Request> reserves;    // worker
+  std::vector<Pooled> pool;        // worker: oldest first
   std::vector<cudaEvent_t> events;  // worker: free events
   std::thread worker;
 
   void run();
   bool admit(int32_t id);
-  void release(Slot& sl);
+  void release(Slot& sl, bool to_pool);
+  spca_status reserve(const Request& r);
+  void to_pool(Pooled e);
+  void evict_oldest();
   void issue(int32_t id, std::vector<std::pair<uint64_t, spca_status>>& done);
   void complete(Slot& sl, Inflight& f, std::vector<std::pair<uint64_t, spca_status>>& done);
   cudaEvent_t event();
@@ -120,25 +175,61 @@ cudaEvent_t spca_server::event() {
   return e;
 }
 
+void spca_server::to_pool(Pooled e) {
+  pool.push_back(e);
+  std::lock_guard<std::mutex> lock(mu);
+  pooled_bytes += e.bytes;
+  ++n_pooled;
+}
+
+void spca_server::evict_oldest() {
+  Pooled e = pool.front();
+  pool.erase(pool.begin());
+  free_session(e);
+  std::lock_guard<std::mutex> lock(mu);
+  pooled_bytes -= e.bytes;
+  --n_pooled;
+}
+
 bool spca_server::admit(int32_t id) {
   Slot& sl = slots[static_cast<size_t>(id)];
-  if (in_use + sl.bytes > budget) return false;
-  spca_options o;
-  spca_default_options(&o);
-  o.math = sl.math;
-  o.max_block_rows = opt.max_block_rows;
-  spca_status st = spca_create(sl.n, sl.k, sl.p, sl.seed, &o, &sl.s);
-  const size_t vbytes = sizeof(double) * static_cast<size_t>(sl.n) * sl.k;
-  if (st == SPCA_OK && (cudaMalloc(&sl.sig_dev, sizeof(double) * sl.k) != cudaSuccess ||
-                        cudaMalloc(&sl.V_dev, vbytes) != cudaSuccess ||
-                        cudaMallocHost(&sl.res_host, sizeof(double) * sl.k + vbytes) != cudaSuccess ||
-                        cudaMallocHost(&sl.flags_host, sizeof(int)) != cudaSuccess)) {
-    cudaGetLastError();
-    st = SPCA_E_NOMEM;
+  Pooled e;
+  bool have = false;
+  // a pooled session of the same shape: no allocation, its state reset for the new seed
+  size_t j = 0;
+  while (j < pool.size() && !pool[j].fits(sl)) ++j;
+  if (j < pool.size()) {
+    e = pool[j];
+    pool.erase(pool.begin() + static_cast<std::ptrdiff_t>(j));
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      pooled_bytes -= e.bytes;
+      --n_pooled;
+    }
+    if (spca_reset(e.s, sl.seed) == SPCA_OK) {
+      have = true;
+    } else {
+      free_session(e);   // not handed out again; a new session is made below
+      e = Pooled();
+    }
   }
+  spca_status st = SPCA_OK;
+  if (!have) {
+    // room for a new session: pooled sessions of other shapes are freed first, oldest first
+    while (in_use + pooled_bytes + sl.bytes > budget && !pool.empty()) evict_oldest();
+    if (in_use + pooled_bytes + sl.bytes > budget) return false;
+    e.n = sl.n; e.k = sl.k; e.p = sl.p; e.math = sl.math; e.bytes = sl.bytes;
+    st = create_session(e, sl.seed, opt.max_block_rows);
+  }
+  sl.s = e.s;
+  sl.sig_dev = e.sig_dev;
+  sl.V_dev = e.V_dev;
+  sl.res_host = e.res_host;
+  sl.flags_host = e.flags_host;
   std::lock_guard<std::mutex> lock(mu);
   sl.admitted = true;
   in_use += sl.bytes;
+  ++(have ? from_pool : created);
   if (st != SPCA_OK) {
     sl.failed = true;
     sl.fail_status = st;
@@ -146,15 +237,39 @@ bool spca_server::admit(int32_t id) {
   return true;
 }
 
-void spca_server::release(Slot& sl) {
+// Sessions made ahead of time go straight to the pool; the budget bounds them as it bounds
+// admitted sessions (a reservation frees no pooled session of another shape).
+spca_status spca_server::reserve(const Request& r) {
+  for (int c = 0; c < r.count; ++c) {
+    if (in_use + pooled_bytes + r.bytes > budget) return SPCA_E_NOMEM;
+    Pooled e;
+    e.n = r.n; e.k = r.k; e.p = r.p; e.math = r.math; e.bytes = r.bytes;
+    const spca_status st = create_session(e, 0, opt.max_block_rows);
+    if (st != SPCA_OK) {
+      free_session(e);
+      return st;
+    }
+    to_pool(e);
+    std::lock_guard<std::mutex> lock(mu);
+    ++created;
+  }
+  return SPCA_OK;
+}
+
+// A closed session that is still usable goes back to the pool with its memory; a failed one,
+// and every session at shutdown, is freed.
+void spca_server::release(Slot& sl, bool pool_it) {
   for (Inflight& f : sl.inflight)
     if (f.ev) events.push_back(f.ev);
   sl.inflight.clear();
-  if (sl.s) spca_destroy(sl.s);
-  if (sl.sig_dev) cudaFree(sl.sig_dev);
-  if (sl.V_dev) cudaFree(sl.V_dev);
-  if (sl.res_host) cudaFreeHost(sl.res_host);
-  if (sl.flags_host) cudaFreeHost(sl.flags_host);
+  if (pool_it && sl.admitted && !sl.failed && sl.s) {
+    Pooled e;
+    e.n = sl.n; e.k = sl.k; e.p = sl.p; e.math = sl.math; e.bytes = sl.bytes;
+    e.s = sl.s; e.sig_dev = sl.sig_dev; e.V_dev = sl.V_dev; e.res_host = sl.res_host; e.flags_host = sl.flags_host;
+    to_pool(e);
+  } else {
+    free_session(sl.s, sl.sig_dev, sl.V_dev, sl.res_host, sl.flags_host);
+  }
   std::lock_guard<std::mutex> lock(mu);
   if (sl.admitted) in_use -= sl.bytes;
   sl = Slot();
@@ -188,7 +303,7 @@ void spca_server::issue(int32_t id, std::vector<std::pair<uint64_t, spca_status>
         if (!sl.inflight.empty()) break;
         done.emplace_back(r.ticket, SPCA_OK);
         sl.queue.pop_front();
-        release(sl);
+        release(sl, false);
         return;
       }
       done.emplace_back(r.ticket, sl.fail_status);
@@ -235,7 +350,7 @@ void spca_server::issue(int32_t id, std::vector<std::pair<uint64_t, spca_status>
     if (!sl.inflight.empty()) break;
     done.emplace_back(r.ticket, SPCA_OK);
     sl.queue.pop_front();
-    release(sl);
+    release(sl, true);
     return;
   }
   flush_batch();
@@ -286,6 +401,8 @@ void spca_server::run() {
         incoming.pop_front();
         if (r.kind == kOpen)
           admission.push_back(r.id);
+        else if (r.kind == kReserve)
+          reserves.push_back(r);
         else
           slots[static_cast<size_t>(r.id)].queue.push_back(r);
       }
@@ -306,13 +423,24 @@ void spca_server::run() {
       const Clock::time_point now = Clock::now();
       if (busy) active_s += std::chrono::duration<double>(now - last).count();
       last = now;
-      if (stop && !busy && admission.empty()) {
+      if (stop && !busy && admission.empty() && reserves.empty()) {
         bool queued = false;
         for (const Slot& sl : slots) queued = queued || !sl.queue.empty();
         if (!queued) break;
       }
     }
     std::vector<std::pair<uint64_t, spca_status>> done;
+    // reservations before the admissions that arrived with them
+    while (!reserves.empty()) {
+      done.emplace_back(reserves.front().ticket, reserve(reserves.front()));
+      reserves.pop_front();
+    }
+    // closes that can go now, so that their sessions are in the pool for these admissions
+    for (size_t i = 0; i < slots.size(); ++i) {
+      const Slot& sl = slots[i];
+      if (sl.admitted && sl.inflight.empty() && !sl.queue.empty() && sl.queue.front().kind == kClose)
+        issue(static_cast<int32_t>(i), done);
+    }
     // admission in arrival order
     while (!admission.empty() && admit(admission.front())) admission.pop_front();
     // issue
@@ -362,7 +490,8 @@ void spca_server::run() {
     if (!done.empty()) cv_done.notify_all();
   }
   for (Slot& sl : slots)
-    if (sl.used || sl.admitted) release(sl);
+    if (sl.used || sl.admitted) release(sl, false);
+  while (!pool.empty()) evict_oldest();
   for (cudaEvent_t e : events) cudaEventDestroy(e);
   events.clear();
 }
@@ -409,8 +538,8 @@ spca_status spca_server_create(const spca_server_options* opt, spca_server** out
   return SPCA_OK;
 }
 
-spca_status spca_server_open(spca_server* sv, int64_t n, int32_t k, int32_t p, uint64_t seed, int32_t* id) {
-  if (!sv || !id) return srv_fail(SPCA_E_INVALID, "NULL server or id");
+// The math form a session of these sizes gets and its device footprint with the result buffers.
+static spca_status session_shape(spca_server* sv, int64_t n, int32_t k, int32_t p, int* math_out, size_t* bytes_out) {
   if (n < 1 || k < 1 || p < 0 || k + p > 256 || k + p > n) return srv_fail(SPCA_E_INVALID, "bad sizes");
   int old = 0;
   cudaGetDevice(&old);
@@ -427,6 +556,17 @@ spca_status spca_server_open(spca_server* sv, int64_t n, int32_t k, int32_t p, u
   if (bytes == 0) return srv_fail(SPCA_E_UNSUPPORTED, "the tensor-core pass does not fit these sizes");
   bytes += sizeof(double) * (static_cast<size_t>(n) * k + k);   // result buffers
   if (bytes > sv->budget) return srv_fail(SPCA_E_NOMEM, "the session alone exceeds the device budget");
+  *math_out = math;
+  *bytes_out = bytes;
+  return SPCA_OK;
+}
+
+spca_status spca_server_open(spca_server* sv, int64_t n, int32_t k, int32_t p, uint64_t seed, int32_t* id) {
+  if (!sv || !id) return srv_fail(SPCA_E_INVALID, "NULL server or id");
+  int math = 0;
+  size_t bytes = 0;
+  const spca_status sst = session_shape(sv, n, k, p, &math, &bytes);
+  if (sst != SPCA_OK) return sst;
   std::lock_guard<std::mutex> lock(sv->mu);
   if (sv->stop) return srv_fail(SPCA_E_STATE, "server is stopping");
   for (size_t i = 0; i < sv->slots.size(); ++i) {
@@ -445,6 +585,25 @@ spca_status spca_server_open(spca_server* sv, int64_t n, int32_t k, int32_t p, u
     return SPCA_OK;
   }
   return srv_fail(SPCA_E_INVALID, "no free session slot");
+}
+
+spca_status spca_server_reserve(spca_server* sv, int64_t n, int32_t k, int32_t p, int32_t count, uint64_t* ticket) {
+  if (!sv || !ticket) return srv_fail(SPCA_E_INVALID, "NULL server or ticket");
+  if (count < 1) return srv_fail(SPCA_E_INVALID, "count < 1");
+  Request r;
+  r.kind = kReserve;
+  const spca_status sst = session_shape(sv, n, k, p, &r.math, &r.bytes);
+  if (sst != SPCA_OK) return sst;
+  r.n = n; r.k = k; r.p = p; r.count = count;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  if (sv->stop) return srv_fail(SPCA_E_STATE, "server is stopping");
+  r.ticket = sv->next_ticket++;
+  r.t_submit = Clock::now();
+  sv->tickets[r.ticket] = TicketState();
+  sv->incoming.push_back(r);
+  *ticket = r.ticket;
+  sv->cv_work.notify_one();
+  return SPCA_OK;
 }
 
 static spca_status queue_request(spca_server* sv, Request r, uint64_t* ticket) {
@@ -536,6 +695,10 @@ spca_status spca_server_get_stats(spca_server* sv, spca_server_stats* out) {
   out->active_seconds = sv->active_s;
   out->device_bytes_in_use = sv->in_use;
   out->device_bytes_budget = sv->budget;
+  out->sessions_pooled = sv->n_pooled;
+  out->admissions_from_pool = sv->from_pool;
+  out->sessions_created = sv->created;
+  out->device_bytes_pooled = sv->pooled_bytes;
   return SPCA_OK;
 }
 

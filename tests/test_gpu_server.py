@@ -3,7 +3,11 @@ blocks of uneven sizes arriving interleaved, admission against a device-memory b
 result must be the one the same session gives alone: bit for bit on the FP32 path (its
 kernels do not depend on how blocks are batched), within the tensor-core form's stated
 tolerance (1e-3 on sigma) where the batching of blocks into launches changes the order of
-FP32 accumulation."""
+FP32 accumulation. Closed and reserved sessions wait in the server's pool and are admitted
+again by a reset of their state; a reused session gives the result of a new one.
+"""
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -153,3 +157,71 @@ def test_rejects_bad_requests():
         with pytest.raises(spca.SpcaError) as ei:
             sv.update(sid, torch.zeros((4, 100), device=DEV))   # closed
         assert ei.value.status == 1
+
+
+def _wait_until(sv, key, value):
+    t0 = time.perf_counter()
+    while sv.stats()[key] != value:
+        assert time.perf_counter() - t0 < WAIT, (key, sv.stats()[key], value)
+        time.sleep(0.001)
+
+
+@pytest.mark.parametrize("math", ["fp32", "auto"])
+def test_pooled_sessions_are_reused_and_give_the_same_results(math):
+    # three sessions reserved ahead of time serve two waves of three opens each: no session is
+    # created after the reservation, and every result equals the same session run alone
+    n, k, p, rows = 3000, 20, 10, 2048
+    blocks = [(0, 700), (700, 1500), (1500, rows)]
+    datas = [session_data(n, k, p, 70 + i, rows) for i in range(6)]
+    kw = {} if math == "auto" else {"math": math}
+    got = []
+    with spca.Server(max_block_rows=4096, **kw) as sv:
+        sv.wait(sv.reserve(n, k, p, 3), WAIT)
+        st = sv.stats()
+        assert (st["sessions_pooled"], st["sessions_created"], st["device_bytes_in_use"]) == (3, 3, 0)
+        assert st["device_bytes_pooled"] > 0
+        for wave in range(2):
+            ids = [sv.open(n, k, p, 80 + 3 * wave + i) for i in range(3)]
+            fins = []
+            for i, sid in enumerate(ids):
+                for a, b in blocks:
+                    sv.update(sid, datas[3 * wave + i][a:b])
+                sig, V = np.zeros(k), np.zeros((k, n))
+                fins.append((sig, V, sv.finalize(sid, sig, V)))
+            for sig, V, t in fins:
+                sv.wait(t, WAIT)
+                got.append((sig, V.T.copy()))
+            for sid in ids:
+                sv.close_session(sid)
+            _wait_until(sv, "sessions_pooled", 3)
+        st = sv.stats()
+        assert (st["sessions_created"], st["admissions_from_pool"]) == (3, 6)
+    used = expected_math(n, k, p) if math == "auto" else math
+    for j, (sig, V) in enumerate(got):
+        s_alone, V_alone = alone(datas[j], k, p, 80 + j, blocks, used)
+        if used == "fp32":
+            assert np.array_equal(sig, s_alone) and np.array_equal(V, V_alone), j
+        else:
+            assert np.max(np.abs(sig - s_alone) / s_alone) <= 1e-3, j
+
+
+def test_an_admission_of_another_shape_frees_pooled_sessions():
+    n, k, p = 4000, 20, 10
+    with spca.Server(max_block_rows=4096) as probe:
+        probe.wait(probe.reserve(n, k, p, 1), WAIT)
+        footprint = probe.stats()["device_bytes_pooled"]
+    assert footprint > 0
+    data = session_data(n, 24, 6, 90, 1024)
+    with spca.Server(device_bytes=int(2.5 * footprint), max_block_rows=4096) as sv:
+        sv.wait(sv.reserve(n, k, p, 2), WAIT)
+        assert sv.stats()["sessions_pooled"] == 2
+        # same footprint (l = 30), another shape: the oldest pooled session makes room
+        sid = sv.open(n, 24, 6, 91)
+        sv.wait(sv.update(sid, data), WAIT)
+        st = sv.stats()
+        assert (st["sessions_pooled"], st["sessions_created"], st["admissions_from_pool"]) == (1, 3, 0)
+        assert st["device_bytes_in_use"] + st["device_bytes_pooled"] <= st["device_bytes_budget"]
+        with pytest.raises(spca.SpcaError) as ei:   # 2 of 2.5 footprints used: no room for a third
+            sv.wait(sv.reserve(n, k, p, 1), WAIT)
+        assert ei.value.status == 2
+        assert sv.stats()["sessions_pooled"] == 1
