@@ -135,7 +135,12 @@ def oracle_precision(A_dev, seed, results):
         rel = np.abs(sigma - ref["sigma"]) / ref["sigma"]
         out[math_name] = {"sigma_rel_max": float(rel.max()), "sigma_rel_lead10": float(rel[:10].max()),
                           "sin_theta_V10": float(O.max_principal_sine(V[:, :10], ref["V"][:, :10])),
+                          "every_sigma_within_1e-3": bool(rel.max() <= 1e-3),
                           "oracle_s": time.perf_counter() - t0}
+        if math_name == "bf16":
+            out[math_name]["note"] = ("BF16 operands round the shifted rows to 8 significant bits, which moves the "
+                                      "tail sigma by more than 1e-3 (an FP64 model with exact accumulation moves "
+                                      "them as much); the gate is sigma >= sigma_1/10 within 1e-3")
     return out
 
 
@@ -390,8 +395,9 @@ def _serving_phase(spca, sat, mean_bytes, load, seconds, ns, ls, S, block, rng, 
     """One Poisson phase of the serving measurement on a fresh server (all sessions admitted
     first). Sessions also come and go inside the timed window: every `churn_every`-th arrival
     finalizes and closes one of the first `churned` sessions and opens a new session of the
-    same shape in its place; one session per such shape is reserved before the window, so
-    these admissions reset pooled sessions instead of allocating."""
+    same shape in its place, fed a first 256-row block at once; one session per such shape is
+    reserved before the window, so these admissions reset pooled sessions instead of
+    allocating."""
     rate = load * sat * 1e9 / mean_bytes          # requests per second
     with spca.Server(max_block_rows=4096) as sv:
         ids = [sv.open(int(ns[i]), int(ls[i]) - 10, 10, 900 + i) for i in range(S)]
@@ -419,6 +425,8 @@ def _serving_phase(spca, sat, mean_bytes, load, seconds, ns, ls, S, block, rng, 
                 sv.close_session(ids[i])
                 n_churn += 1
                 ids[i] = sv.open(int(ns[i]), k, 10, 5000 + n_churn)
+                tickets.append(sv.update(ids[i], pools[i][:256]))   # its first rows, as at admission
+                nbytes += 4.0 * 256 * int(ns[i])
             else:
                 i = int(rng.integers(0, S))
                 rows, b = block(i)
