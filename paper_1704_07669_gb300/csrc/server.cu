@@ -49,7 +49,10 @@ struct Inflight {
 };
 
 struct Slot {
-  bool used = false;        // reserved by open (guarded by the server mutex)
+  bool used = false;        // open and not yet closed by the caller (guarded by the server mutex)
+  bool held = false;        // from open until the worker frees the slot (guarded by the server
+                            // mutex): a slot closed by the caller stays held while the worker
+                            // still has its requests, so open cannot hand it out again
   bool admitted = false;    // session created (worker)
   bool failed = false;
   spca_status fail_status = SPCA_OK;
@@ -490,7 +493,7 @@ void spca_server::run() {
     if (!done.empty()) cv_done.notify_all();
   }
   for (Slot& sl : slots)
-    if (sl.used || sl.admitted) release(sl, false);
+    if (sl.held || sl.admitted) release(sl, false);
   while (!pool.empty()) evict_oldest();
   for (cudaEvent_t e : events) cudaEventDestroy(e);
   events.clear();
@@ -571,9 +574,11 @@ spca_status spca_server_open(spca_server* sv, int64_t n, int32_t k, int32_t p, u
   if (sv->stop) return srv_fail(SPCA_E_STATE, "server is stopping");
   for (size_t i = 0; i < sv->slots.size(); ++i) {
     Slot& sl = sv->slots[i];
-    if (sl.used || sl.admitted) continue;
-    sl = Slot();
+    if (sl.used || sl.held) continue;
+    // a slot that is not held was reset by the worker (or never used): only its scalars are set
+    // here, the worker's queues are left alone
     sl.used = true;
+    sl.held = true;
     sl.n = n; sl.k = k; sl.p = p; sl.seed = seed; sl.math = math; sl.bytes = bytes;
     Request r;
     r.kind = kOpen;
