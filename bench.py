@@ -383,9 +383,9 @@ def run_serving(spca, dev, seconds=3.0, loads=(0.25, 0.5, 0.75), seed=17040769 +
     mid = next((x for x in sweep if abs(x["load"] - 0.5) < 1e-9), sweep[0])
     out.update({k_: v for k_, v in mid.items() if k_ != "load"})
     out["load_sweep"] = sweep
-    out.update({"latency_note": "percentiles over each Poisson phase (sessions finalized, closed and replaced "
-                                "inside it), one 256-row admission block per session before it and the "
-                                "final finalize of every session",
+    out.update({"latency_note": "percentiles over each Poisson phase (sessions closed and replaced inside it), "
+                                "one 256-row admission block per session before it and the final "
+                                "finalize of every session",
                 "tc_sessions": int(sum(1 for i in range(S) if tensor_core_takes(spca, int(ns[i]), int(ls[i]))))})
     del pools
     return out
@@ -394,10 +394,12 @@ def run_serving(spca, dev, seconds=3.0, loads=(0.25, 0.5, 0.75), seed=17040769 +
 def _serving_phase(spca, sat, mean_bytes, load, seconds, ns, ls, S, block, rng, pools, churn_every=25, churned=8):
     """One Poisson phase of the serving measurement on a fresh server (all sessions admitted
     first). Sessions also come and go inside the timed window: every `churn_every`-th arrival
-    finalizes and closes one of the first `churned` sessions and opens a new session of the
-    same shape in its place, fed a first 256-row block at once; one session per such shape is
-    reserved before the window, so these admissions reset pooled sessions instead of
-    allocating."""
+    closes one of the first `churned` sessions (its client leaves without a result) and opens a
+    new session of the same shape in its place, fed a first 256-row block at once; one session
+    per such shape is reserved before the window, so these admissions reset pooled sessions
+    instead of allocating. Finalisations run after the window (all sessions at once): inside it,
+    their single-block kernels would hold SMs that the cooperative tensor-core launches wait
+    for."""
     rate = load * sat * 1e9 / mean_bytes          # requests per second
     with spca.Server(max_block_rows=4096) as sv:
         ids = [sv.open(int(ns[i]), int(ls[i]) - 10, 10, 900 + i) for i in range(S)]
@@ -420,9 +422,7 @@ def _serving_phase(spca, sat, mean_bytes, load, seconds, ns, ls, S, block, rng, 
             if n_req % churn_every == 0:
                 i = int(rng.integers(0, churned))
                 k = int(ls[i]) - 10
-                sig_h, V_h = np.zeros(k), np.zeros((k, int(ns[i])))
-                fins.append((sig_h, V_h, sv.finalize(ids[i], sig_h, V_h)))
-                sv.close_session(ids[i])
+                sv.close_session(ids[i])   # the client leaves without a result
                 n_churn += 1
                 ids[i] = sv.open(int(ns[i]), k, 10, 5000 + n_churn)
                 tickets.append(sv.update(ids[i], pools[i][:256]))   # its first rows, as at admission
