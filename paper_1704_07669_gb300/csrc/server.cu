@@ -247,7 +247,9 @@ spca_status spca_server::reserve(const Request& r) {
     if (in_use + pooled_bytes + r.bytes > budget) return SPCA_E_NOMEM;
     Pooled e;
     e.n = r.n; e.k = r.k; e.p = r.p; e.math = r.math; e.bytes = r.bytes;
-    const spca_status st = create_session(e, 0, opt.max_block_rows);
+    spca_status st = create_session(e, 0, opt.max_block_rows);
+    // staging buffers that a first update would otherwise allocate on the worker
+    if (st == SPCA_OK) st = spca::session_prepare_staging(e.s);
     if (st != SPCA_OK) {
       free_session(e);
       return st;

@@ -605,6 +605,23 @@ spca_status ensure_staging(spca_session* s, size_t row_bytes) {
 
 }  // namespace
 
+extern "C++" {
+namespace spca {
+
+// Make the staging buffers now where FP32 device rows with leading dimension n go through
+// them (only the grouped kernel takes this session, and n x 4 bytes is not a multiple of 16, so
+// no tensor map describes the caller's rows): the first such update then allocates nothing.
+spca_status session_prepare_staging(spca_session* s) {
+  spca_status st = check_usable(s);
+  if (st != SPCA_OK) return st;
+  if (!(s->tc && s->tcw.use_grp && !s->tcw.cfg_ok) || (s->n * 4) % 16 == 0) return SPCA_OK;
+  CU(cudaSetDevice(s->device));
+  return ensure_staging(s, size_t(stage_ld(s->n, 4)) * 4);
+}
+
+}  // namespace spca
+}  // extern "C++"
+
 spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t ld, int32_t dtype,
                         const float* block_scale, int32_t rows_on_device, float* G_out) {
   spca_status st = check_usable(s);

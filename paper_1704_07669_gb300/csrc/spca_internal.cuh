@@ -250,6 +250,7 @@ cudaError_t launch_left_vectors(const State& s, const FinalWork& f, int k, const
 size_t session_footprint(int64_t n, int k, int p, int math, int64_t max_block_rows);   // 0: does not fit
 cudaStream_t session_stream(spca_session* s);
 spca_status session_flush(spca_session* s);
+spca_status session_prepare_staging(spca_session* s);
 spca_status session_finalize_async(spca_session* s, double* sigma_dev, double* V_dev, int* flags_host);
 spca_status session_flags_status(spca_session* s, int flags);
 int session_k(const spca_session* s);
