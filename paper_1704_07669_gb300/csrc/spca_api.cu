@@ -584,17 +584,31 @@ int64_t stage_ld(int64_t n, size_t es) {
   return ((n + q - 1) / q) * q;
 }
 
-// The two pinned host buffers and two device buffers of the staged paths (made once).
+// The two pinned host buffers and two device buffers of the staged paths (made once). An
+// allocation that fails leaves none of them behind, so a later call tries again.
 spca_status ensure_staging(spca_session* s, size_t row_bytes) {
-  if (s->pinned[0]) return SPCA_OK;
+  if (s->dstage[1]) return SPCA_OK;
   size_t want = kStageBytes;
   if (want < row_bytes) want = row_bytes;
   s->stage_bytes = want;
   for (int i = 0; i < 2; ++i) {
-    if (cudaMallocHost(&s->pinned[i], want) != cudaSuccess || cudaMalloc(&s->dstage[i], want) != cudaSuccess) {
+    void* ph = nullptr;
+    void* pd = nullptr;
+    if (cudaMallocHost(&ph, want) != cudaSuccess || cudaMalloc(&pd, want) != cudaSuccess) {
       cudaGetLastError();
+      if (ph) cudaFreeHost(ph);
+      for (int j = 0; j < i; ++j) {
+        cudaFreeHost(s->pinned[j]);
+        cudaFree(s->dstage[j]);
+        cudaEventDestroy(s->copied[j]);
+        cudaEventDestroy(s->consumed[j]);
+        s->pinned[j] = s->dstage[j] = nullptr;
+        s->copied[j] = s->consumed[j] = nullptr;
+      }
       return fail(s, SPCA_E_NOMEM, "staging allocation of %zu bytes failed", want);
     }
+    s->pinned[i] = ph;
+    s->dstage[i] = pd;
     CU(cudaEventCreateWithFlags(&s->copied[i], cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&s->consumed[i], cudaEventDisableTiming));
     CU(cudaEventRecord(s->consumed[i], s->stream));
