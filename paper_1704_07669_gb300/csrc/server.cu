@@ -416,9 +416,10 @@ void spca_server::run() {
         for (int32_t id : admission) {
           Slot& sl = slots[static_cast<size_t>(id)];
           for (const Request& r : sl.queue) {
-            TicketState& t = tickets[r.ticket];
-            t.done = true;
-            t.st = SPCA_E_STATE;
+            auto it = tickets.find(r.ticket);   // closes have no waiter and no entry
+            if (it == tickets.end()) continue;
+            it->second.done = true;
+            it->second.st = SPCA_E_STATE;
           }
           sl = Slot();
         }
@@ -477,9 +478,10 @@ void spca_server::run() {
       admitted = adm;
       waiting = static_cast<int64_t>(admission.size());
       for (auto& d : done) {
-        TicketState& t = tickets[d.first];
-        t.done = true;
-        t.st = d.second;
+        auto it = tickets.find(d.first);   // closes have no waiter and no entry
+        if (it == tickets.end()) continue;
+        it->second.done = true;
+        it->second.st = d.second;
       }
       for (auto& d : done) {
         if (d.second == SPCA_OK) continue;
