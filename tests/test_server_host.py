@@ -43,7 +43,8 @@ def fake(tmp_path_factory):
     src = os.path.join(ROOT, "paper_1704_07669_gb300", "csrc")
     cmd = ["g++", "-std=c++17", "-O1", "-g", "-fPIC", "-shared", f"-I{CUDA_INC}", f"-I{ROOT}/include", f"-I{src}",
            "-x", "c++", os.path.join(src, "server.cu"),
-           "-x", "c++", os.path.join(ROOT, "tests", "server_host", "fake_device.cpp"), "-o", out, "-lpthread"]
+           "-x", "c++", os.path.join(ROOT, "tests", "server_host", "fake_device.cpp"), "-o", out, "-lpthread",
+           "-Wl,-Bsymbolic"]   # its own stand-ins, even where the process has loaded the CUDA runtime
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     lib = ctypes.CDLL(out)
