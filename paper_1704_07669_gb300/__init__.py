@@ -141,6 +141,30 @@ def _wait_for_torch(*tensors):
             return
 
 
+def _unit_column_stride(x, what):
+    """Rows are read row-major with leading dimension ld: a view whose columns are not adjacent
+    would be read as if they were."""
+    if hasattr(x, "stride") and callable(x.stride):
+        ok = x.dim() == 2 and (x.stride(1) == 1 or x.shape[1] <= 1)
+    elif isinstance(x, np.ndarray):
+        ok = x.ndim == 2 and (x.strides[1] == x.itemsize or x.shape[1] <= 1)
+    else:
+        return
+    if not ok:
+        raise ValueError(f"{what} must be a 2-D row-major array with adjacent columns")
+
+
+def _float64_buffer(x, what):
+    """Result buffers are written as doubles; another dtype would be overrun."""
+    if x is None or not (hasattr(x, "dtype")):
+        return
+    if not str(x.dtype).endswith("float64"):
+        raise ValueError(f"{what} must hold float64 values, got {x.dtype}")
+    contiguous = x.is_contiguous() if hasattr(x, "is_contiguous") else x.flags["C_CONTIGUOUS"]
+    if not contiguous:
+        raise ValueError(f"{what} must be contiguous")
+
+
 def _dtype_code(x):
     name = str(getattr(x, "dtype", ""))
     if name.endswith("float32"):
@@ -170,6 +194,8 @@ def spca_create(n, k, p, seed, math=SPCA_MATH_FP32, center=1, max_block_rows=0, 
 
 
 def spca_update(handle, rows, m_i=None, ld=None, dtype=None, block_scale=None, rows_on_device=None, G_out=None):
+    if ld is None:
+        _unit_column_stride(rows, "rows")
     addr, on_dev = _ptr(rows)
     if m_i is None:
         m_i = rows.shape[0]
@@ -191,6 +217,8 @@ def spca_update(handle, rows, m_i=None, ld=None, dtype=None, block_scale=None, r
 
 def spca_finalize(handle, sigma, V, out_on_device=None):
     """Fill sigma (k doubles) and V (n x k doubles, column-major) - tensors or arrays."""
+    _float64_buffer(sigma, "sigma")
+    _float64_buffer(V, "V")
     sa, sdev = _ptr(sigma)
     va, vdev = _ptr(V)
     on = bool(sdev) if out_on_device is None else bool(out_on_device)
@@ -199,6 +227,7 @@ def spca_finalize(handle, sigma, V, out_on_device=None):
 
 def spca_left_vectors(handle, G, U, m=None, out_on_device=None):
     """Fill U (m x k doubles, column-major) from the kept sketch rows G (m x l FP32 CUDA tensor)."""
+    _float64_buffer(U, "U")
     ga, _ = _ptr(G)
     ua, udev = _ptr(U)
     if m is None:
@@ -210,6 +239,9 @@ def spca_left_vectors(handle, G, U, m=None, out_on_device=None):
 def spca_left_vectors_pass(handle, rows, U, block_scale=None):
     """U rows of the device rows `rows` (m x n, any storage dtype) by a second pass, into U: a
     CUDA float64 tensor of shape (k, m) (column-major m x k; ldu = its row stride)."""
+    _unit_column_stride(rows, "rows")
+    if not str(getattr(U, "dtype", "")).endswith("float64") or U.dim() != 2 or U.stride(1) != 1:
+        raise ValueError("spca_left_vectors_pass: U must be a 2-D float64 tensor with adjacent columns")
     addr, on_dev = _ptr(rows)
     ua, udev = _ptr(U)
     if not on_dev or not udev:
@@ -457,11 +489,13 @@ class Server:
         h = ctypes.c_void_p()
         _check_srv(lib().spca_server_create(ctypes.byref(opt), ctypes.byref(h)))
         self.handle = h.value
+        self._shapes = {}   # session id -> (n, k), for the size of the result buffers
 
     def open(self, n, k, p, seed):
         sid = ctypes.c_int32(-1)
         _check_srv(lib().spca_server_open(self.handle, int(n), int(k), int(p), int(seed) & 0xFFFFFFFFFFFFFFFF,
                                           ctypes.byref(sid)))
+        self._shapes[sid.value] = (int(n), int(k))
         return sid.value
 
     def reserve(self, n, k, p, count):
@@ -473,6 +507,9 @@ class Server:
     def update(self, sid, rows):
         """Queue a block of device-resident FP32 rows (a 2-D CUDA tensor); returns a ticket. The
         worker reads them on its own streams, after the work queued on torch's current stream."""
+        _unit_column_stride(rows, "rows")
+        if not str(rows.dtype).endswith("float32"):
+            raise ValueError(f"the serving loop takes FP32 rows, got {rows.dtype}")
         _wait_for_torch(rows)
         t = ctypes.c_uint64(0)
         _check_srv(lib().spca_server_update(self.handle, int(sid), _ptr(rows)[0], int(rows.shape[0]),
@@ -481,6 +518,11 @@ class Server:
 
     def finalize(self, sid, sigma, V):
         """Queue a finalisation into host numpy buffers sigma (k) and V (k x n, i.e. n x k column-major)."""
+        _float64_buffer(sigma, "sigma")
+        _float64_buffer(V, "V")
+        n, k = self._shapes.get(int(sid), (0, 0))
+        if sigma.size < k or V.size < n * k:
+            raise ValueError(f"sigma needs {k} and V {n * k} float64 values")
         t = ctypes.c_uint64(0)
         _check_srv(lib().spca_server_finalize(self.handle, int(sid), _ptr(sigma)[0], _ptr(V)[0], ctypes.byref(t)))
         return t.value

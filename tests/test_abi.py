@@ -96,3 +96,21 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(spca_build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         spca.lib()
+
+
+def test_binding_rejects_layouts_the_library_cannot_see():
+    """Checks the C ABI cannot make (it gets a pointer and a leading dimension): rows whose
+    columns are not adjacent, and result buffers that are not float64, are refused before any
+    library call (the handle below is never used)."""
+    import numpy as np
+    rows = np.zeros((8, 6), dtype=np.float32)
+    with pytest.raises(ValueError):
+        spca.spca_update(0, rows[:, ::2])                       # every other column
+    with pytest.raises(ValueError):
+        spca.spca_update(0, np.asfortranarray(rows))            # column-major
+    with pytest.raises(ValueError):
+        spca.spca_finalize(0, np.zeros(3, dtype=np.float32), np.zeros((3, 6)))
+    with pytest.raises(ValueError):
+        spca.spca_finalize(0, np.zeros(3), np.zeros((6, 3)).T)  # not contiguous
+    with pytest.raises(ValueError):
+        spca.spca_left_vectors(0, None, np.zeros((3, 8), dtype=np.float32))
