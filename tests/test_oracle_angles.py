@@ -1,4 +1,5 @@
-"""Pins of the oracle's subspace measure ``max_principal_sine``.
+"""Pins of the oracle's comparison measures: the subspace measure ``max_principal_sine``
+and, at the end, the relative Frobenius error ``rel_fro``.
 
 The sine of the largest principal angle between two k-dimensional subspaces is
 fixed by construction here: with V1 = [e_1 .. e_k] and the columns of V2 equal to
@@ -101,3 +102,30 @@ def test_planted_mistakes_are_caught(old, new):
     V1, V2 = _pair(30, th, 11)
     want = np.sin(0.6)
     assert abs(bad(V1, V2) - want) > 1e-3
+
+
+# ---------------------------------------------------------------- the relative Frobenius error
+
+def test_rel_fro_is_the_relative_frobenius_norm_of_the_difference():
+    """``rel_fro`` is the measure of every state comparison (H, Gram, sums, U): pinned to
+    values fixed by construction, so that a helper returning 0, a max-abs norm, or a
+    denominator taken from the wrong argument fails."""
+    ref = np.array([[3.0, 0.0], [0.0, 4.0]])            # ||ref||_F = 5
+    assert O.rel_fro(ref, ref) == 0.0
+    assert O.rel_fro(2.0 * ref, ref) == pytest.approx(1.0, rel=1e-15)
+    # one entry off by 1: ||diff||_F / ||ref||_F = 1 / 5
+    x = ref.copy()
+    x[0, 1] = 1.0
+    assert O.rel_fro(x, ref) == pytest.approx(0.2, rel=1e-15)
+    # Frobenius, not the largest entry: two entries off by 3 and 4 -> 5 / 5
+    y = ref.copy()
+    y[0, 1], y[1, 0] = 3.0, 4.0
+    assert O.rel_fro(y, ref) == pytest.approx(1.0, rel=1e-15)
+    # the denominator is the reference's norm: not symmetric in its arguments
+    assert O.rel_fro(ref, 2.0 * ref) == pytest.approx(0.5, rel=1e-15)
+    # scale invariance and shape independence (a flat view gives the same value)
+    rng = np.random.default_rng(0)
+    a, b = rng.standard_normal((7, 5)), rng.standard_normal((7, 5))
+    assert O.rel_fro(1e-30 * a, 1e-30 * b) == pytest.approx(O.rel_fro(a, b), rel=1e-12)
+    assert O.rel_fro(a.ravel(), b.ravel()) == pytest.approx(O.rel_fro(a, b), rel=1e-15)
+    assert O.rel_fro(a, b) == pytest.approx(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()), rel=1e-12)
