@@ -52,8 +52,8 @@ typedef struct {
 typedef struct {
   int64_t updates_done, finalizes_done;
   int64_t sessions_admitted, sessions_waiting;   /* now */
-  double update_p50_ms, update_p99_ms;           /* over all completed updates so far */
-  double finalize_p50_ms, finalize_p99_ms;
+  double update_p50_ms, update_p99_ms;           /* over the most recent 2^20 completed updates */
+  double finalize_p50_ms, finalize_p99_ms;       /* likewise for finalisations */
   double rows_bytes;                             /* bytes of rows folded in so far */
   double active_seconds;                         /* wall time with at least one request in flight */
   size_t device_bytes_in_use, device_bytes_budget;   /* admitted sessions; the budget */
@@ -105,7 +105,9 @@ spca_status spca_server_update(spca_server* sv, int32_t id, const float* rows, i
 spca_status spca_server_finalize(spca_server* sv, int32_t id, double* sigma, double* V, uint64_t* ticket);
 
 /* Wait until request `ticket` completes (timeout_s < 0: no limit) and return its status
- * (SPCA_E_TIMEOUT if the wait timed out; the request itself goes on). */
+ * (SPCA_E_TIMEOUT if the wait timed out; the request itself goes on). For a failed request,
+ * spca_server_last_error on the same thread then gives its own reason (with the message of
+ * the session that ran it). */
 spca_status spca_server_wait(spca_server* sv, uint64_t ticket, double timeout_s);
 
 /* Close session id after its queued requests; the session goes to the pool (its memory stays

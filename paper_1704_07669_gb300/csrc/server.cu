@@ -14,6 +14,7 @@
 #include <deque>
 #include <mutex>
 #include <new>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -115,9 +116,41 @@ void free_session(Pooled& e) { free_session(e.s, e.sig_dev, e.V_dev, e.res_host,
 struct TicketState {
   bool done = false;
   spca_status st = SPCA_OK;
+  std::string msg;   // what went wrong, for a failed request
 };
 
-double pct(std::vector<double> v, double q) {
+// A completed request: its ticket, status and (when it failed) the reason, taken from the
+// session that ran it at the time it failed.
+struct Done {
+  uint64_t ticket;
+  spca_status st;
+  std::string msg;
+};
+
+std::string reason(spca_session* s, spca_status st, const char* what) {
+  char buf[320];
+  const char* e = s ? spca_last_error(s) : "";
+  std::snprintf(buf, sizeof(buf), "%s (status %d)%s%s", what, static_cast<int>(st), e[0] ? ": " : "", e);
+  return buf;
+}
+
+// Latencies of the most recent kLatWindow completed requests of one kind (a ring, so a
+// long-running server holds a bounded record).
+constexpr size_t kLatWindow = size_t(1) << 20;
+struct LatRing {
+  std::vector<double> v;
+  size_t next = 0;
+  void add(double ms) {
+    if (v.size() < kLatWindow) {
+      v.push_back(ms);
+    } else {
+      v[next] = ms;
+      next = (next + 1) % kLatWindow;
+    }
+  }
+};
+
+double pct(std::vector<double>& v, double q) {   // reorders v
   if (v.empty()) return 0.0;
   const size_t i = static_cast<size_t>(q * static_cast<double>(v.size() - 1) + 0.5);
   std::nth_element(v.begin(), v.begin() + static_cast<std::ptrdiff_t>(i), v.end());
@@ -143,13 +176,12 @@ struct spca_server {
   std::vector<Slot> slots;
   std::unordered_map<uint64_t, TicketState> tickets;
   uint64_t next_ticket = 1;
-  std::vector<double> lat_update, lat_finalize;
+  LatRing lat_update, lat_finalize;
   int64_t updates_done = 0, finalizes_done = 0, admitted = 0, waiting = 0;
   int64_t n_pooled = 0, from_pool = 0, created = 0;   // written by the worker under mu
   size_t pooled_bytes = 0;
   double rows_bytes = 0.0, active_s = 0.0;
   bool stop = false;
-  char worker_err[256] = "";       // text of the last failed request (guarded by mu)
   std::deque<int32_t> admission;   // worker
   std::deque<Request> reserves;    // worker
   std::vector<Pooled> pool;        // worker: oldest first
@@ -162,8 +194,8 @@ struct spca_server {
   spca_status reserve(const Request& r);
   void to_pool(Pooled e);
   void evict_oldest();
-  void issue(int32_t id, std::vector<std::pair<uint64_t, spca_status>>& done);
-  void complete(Slot& sl, Inflight& f, std::vector<std::pair<uint64_t, spca_status>>& done);
+  void issue(int32_t id, std::vector<Done>& done);
+  void complete(Slot& sl, Inflight& f, std::vector<Done>& done);
   cudaEvent_t event();
 };
 
@@ -283,7 +315,7 @@ void spca_server::release(Slot& sl, bool pool_it) {
 // Issue what is queued for one admitted session, in order. Updates are folded into one
 // flushed batch; a finalisation waits until the previous one has completed (its result
 // buffers are per session); a close waits until nothing is in flight.
-void spca_server::issue(int32_t id, std::vector<std::pair<uint64_t, spca_status>>& done) {
+void spca_server::issue(int32_t id, std::vector<Done>& done) {
   Slot& sl = slots[static_cast<size_t>(id)];
   Inflight batch;
   batch.kind = kUpdate;
@@ -295,7 +327,9 @@ void spca_server::issue(int32_t id, std::vector<std::pair<uint64_t, spca_status>
       batch.ev = ev;
       sl.inflight.push_back(std::move(batch));
     } else {
-      for (Request& r : batch.reqs) done.emplace_back(r.ticket, st == SPCA_OK ? SPCA_E_CUDA : st);
+      const spca_status fs = st == SPCA_OK ? SPCA_E_CUDA : st;
+      const std::string why = reason(sl.s, fs, "launching the batched updates failed");
+      for (Request& r : batch.reqs) done.push_back({r.ticket, fs, why});
     }
     batch = Inflight();
     batch.kind = kUpdate;
@@ -306,19 +340,19 @@ void spca_server::issue(int32_t id, std::vector<std::pair<uint64_t, spca_status>
       if (r.kind == kClose) {
         flush_batch();
         if (!sl.inflight.empty()) break;
-        done.emplace_back(r.ticket, SPCA_OK);
+        done.push_back({r.ticket, SPCA_OK, std::string()});
         sl.queue.pop_front();
         release(sl, false);
         return;
       }
-      done.emplace_back(r.ticket, sl.fail_status);
+      done.push_back({r.ticket, sl.fail_status, reason(nullptr, sl.fail_status, "the session could not be created")});
       sl.queue.pop_front();
       continue;
     }
     if (r.kind == kUpdate) {
       const spca_status st = spca_update(sl.s, r.rows, r.m, r.ld, SPCA_F32, nullptr, 1, nullptr);
       if (st != SPCA_OK) {
-        done.emplace_back(r.ticket, st);
+        done.push_back({r.ticket, st, reason(sl.s, st, "update rejected")});
       } else {
         batch.reqs.push_back(r);
       }
@@ -346,14 +380,15 @@ void spca_server::issue(int32_t id, std::vector<std::pair<uint64_t, spca_status>
         f.reqs.push_back(r);
         sl.inflight.push_back(std::move(f));
       } else {
-        done.emplace_back(r.ticket, st == SPCA_OK ? SPCA_E_CUDA : st);
+        const spca_status fs = st == SPCA_OK ? SPCA_E_CUDA : st;
+        done.push_back({r.ticket, fs, reason(sl.s, fs, "finalisation could not be queued")});
       }
       sl.queue.pop_front();
       continue;
     }
     // close
     if (!sl.inflight.empty()) break;
-    done.emplace_back(r.ticket, SPCA_OK);
+    done.push_back({r.ticket, SPCA_OK, std::string()});
     sl.queue.pop_front();
     release(sl, true);
     return;
@@ -361,12 +396,12 @@ void spca_server::issue(int32_t id, std::vector<std::pair<uint64_t, spca_status>
   flush_batch();
 }
 
-void spca_server::complete(Slot& sl, Inflight& f, std::vector<std::pair<uint64_t, spca_status>>& done) {
+void spca_server::complete(Slot& sl, Inflight& f, std::vector<Done>& done) {
   const Clock::time_point now = Clock::now();
   if (f.kind == kUpdate) {
     std::lock_guard<std::mutex> lock(mu);
     for (const Request& r : f.reqs) {
-      lat_update.push_back(std::chrono::duration<double, std::milli>(now - r.t_submit).count());
+      lat_update.add(std::chrono::duration<double, std::milli>(now - r.t_submit).count());
       rows_bytes += 4.0 * static_cast<double>(r.m) * static_cast<double>(sl.n);
       ++updates_done;
     }
@@ -380,10 +415,10 @@ void spca_server::complete(Slot& sl, Inflight& f, std::vector<std::pair<uint64_t
         std::memcpy(r.V, sl.res_host + sl.k, sizeof(double) * static_cast<size_t>(sl.n) * sl.k);
       }
       std::lock_guard<std::mutex> lock(mu);
-      lat_finalize.push_back(std::chrono::duration<double, std::milli>(now - r.t_submit).count());
+      lat_finalize.add(std::chrono::duration<double, std::milli>(now - r.t_submit).count());
       ++finalizes_done;
     }
-    done.emplace_back(r.ticket, st);
+    done.push_back({r.ticket, st, st == SPCA_OK ? std::string() : reason(sl.s, st, "the finalisation failed")});
   }
 }
 
@@ -420,6 +455,7 @@ void spca_server::run() {
             if (it == tickets.end()) continue;
             it->second.done = true;
             it->second.st = SPCA_E_STATE;
+            it->second.msg = "the server stopped before the session was admitted";
           }
           sl = Slot();
         }
@@ -435,10 +471,12 @@ void spca_server::run() {
         if (!queued) break;
       }
     }
-    std::vector<std::pair<uint64_t, spca_status>> done;
+    std::vector<Done> done;
     // reservations before the admissions that arrived with them
     while (!reserves.empty()) {
-      done.emplace_back(reserves.front().ticket, reserve(reserves.front()));
+      const spca_status rs = reserve(reserves.front());
+      done.push_back({reserves.front().ticket, rs,
+                      rs == SPCA_OK ? std::string() : reason(nullptr, rs, "the reservation stopped short")});
       reserves.pop_front();
     }
     // closes that can go now, so that their sessions are in the pool for these admissions
@@ -460,7 +498,8 @@ void spca_server::run() {
         if (q == cudaErrorNotReady) break;
         if (q != cudaSuccess) {
           cudaGetLastError();
-          for (const Request& r : f.reqs) done.emplace_back(r.ticket, SPCA_E_CUDA);
+          for (const Request& r : f.reqs)
+            done.push_back({r.ticket, SPCA_E_CUDA, std::string("a CUDA error ended the request: ") + cudaGetErrorString(q)});
         } else {
           complete(sl, f, done);
         }
@@ -477,21 +516,12 @@ void spca_server::run() {
       for (const Slot& sl : slots) adm += sl.admitted ? 1 : 0;
       admitted = adm;
       waiting = static_cast<int64_t>(admission.size());
-      for (auto& d : done) {
-        auto it = tickets.find(d.first);   // closes have no waiter and no entry
+      for (Done& d : done) {
+        auto it = tickets.find(d.ticket);   // closes have no waiter and no entry
         if (it == tickets.end()) continue;
         it->second.done = true;
-        it->second.st = d.second;
-      }
-      for (auto& d : done) {
-        if (d.second == SPCA_OK) continue;
-        // the failing session's own message, if it has one
-        for (const Slot& sl : slots)
-          if (sl.s && spca_last_error(sl.s)[0]) {
-            std::snprintf(worker_err, sizeof(worker_err), "%s", spca_last_error(sl.s));
-            break;
-          }
-        if (!worker_err[0]) std::snprintf(worker_err, sizeof(worker_err), "request failed (status %d)", d.second);
+        it->second.st = d.st;
+        it->second.msg = std::move(d.msg);
       }
     }
     if (!done.empty()) cv_done.notify_all();
@@ -683,31 +713,37 @@ spca_status spca_server_wait(spca_server* sv, uint64_t ticket, double timeout_s)
     return srv_fail(SPCA_E_TIMEOUT, "request still running");
   }
   const spca_status st = sv->tickets[ticket].st;
+  if (st != SPCA_OK) srv_fail(st, sv->tickets[ticket].msg.empty() ? "request failed" : sv->tickets[ticket].msg.c_str());
   sv->tickets.erase(ticket);
-  if (st != SPCA_OK) srv_fail(st, sv->worker_err[0] ? sv->worker_err : "request failed");
   return st;
 }
 
 spca_status spca_server_get_stats(spca_server* sv, spca_server_stats* out) {
   if (!sv || !out) return srv_fail(SPCA_E_INVALID, "NULL server or out");
-  std::lock_guard<std::mutex> lock(sv->mu);
-  std::memset(out, 0, sizeof(*out));
-  out->updates_done = sv->updates_done;
-  out->finalizes_done = sv->finalizes_done;
-  out->sessions_admitted = sv->admitted;
-  out->sessions_waiting = sv->waiting;
-  out->update_p50_ms = pct(sv->lat_update, 0.50);
-  out->update_p99_ms = pct(sv->lat_update, 0.99);
-  out->finalize_p50_ms = pct(sv->lat_finalize, 0.50);
-  out->finalize_p99_ms = pct(sv->lat_finalize, 0.99);
-  out->rows_bytes = sv->rows_bytes;
-  out->active_seconds = sv->active_s;
-  out->device_bytes_in_use = sv->in_use;
-  out->device_bytes_budget = sv->budget;
-  out->sessions_pooled = sv->n_pooled;
-  out->admissions_from_pool = sv->from_pool;
-  out->sessions_created = sv->created;
-  out->device_bytes_pooled = sv->pooled_bytes;
+  std::vector<double> lu, lf;
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->updates_done = sv->updates_done;
+    out->finalizes_done = sv->finalizes_done;
+    out->sessions_admitted = sv->admitted;
+    out->sessions_waiting = sv->waiting;
+    out->rows_bytes = sv->rows_bytes;
+    out->active_seconds = sv->active_s;
+    out->device_bytes_in_use = sv->in_use;
+    out->device_bytes_budget = sv->budget;
+    out->sessions_pooled = sv->n_pooled;
+    out->admissions_from_pool = sv->from_pool;
+    out->sessions_created = sv->created;
+    out->device_bytes_pooled = sv->pooled_bytes;
+    lu = sv->lat_update.v;
+    lf = sv->lat_finalize.v;
+  }
+  // the selections run on the copies, outside the lock the worker takes
+  out->update_p50_ms = pct(lu, 0.50);
+  out->update_p99_ms = pct(lu, 0.99);
+  out->finalize_p50_ms = pct(lf, 0.50);
+  out->finalize_p99_ms = pct(lf, 0.99);
   return SPCA_OK;
 }
 

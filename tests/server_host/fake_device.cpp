@@ -14,6 +14,7 @@
 #include <atomic>
 #include <chrono>
 #include <cstdint>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -49,6 +50,7 @@ struct spca_session {
   uint64_t seed = 0;
   int64_t m = 0;
   uint64_t digest = 1469598103934665603ull;
+  char err[128] = "";
   CUstream_st stream;
 };
 
@@ -96,6 +98,8 @@ cudaError_t cudaGetDevice(int* device) {
 cudaError_t cudaSetDevice(int) { return cudaSuccess; }
 
 cudaError_t cudaGetLastError(void) { return cudaSuccess; }
+
+const char* cudaGetErrorString(cudaError_t e) { return e == cudaSuccess ? "no error" : "stand-in CUDA error"; }
 
 cudaError_t cudaMemGetInfo(size_t* free_bytes, size_t* total) {
   *free_bytes = size_t(64) << 30;
@@ -191,6 +195,11 @@ spca_status spca_reset(spca_session* s, uint64_t seed) {
 
 spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t ld, int32_t, const float*,
                         int32_t, float*) {
+  if (m_i == 97) {   // a block the stand-in refuses, to test how a failure is reported
+    std::snprintf(s->err, sizeof(s->err), "the stand-in refuses 97-row blocks (session seed %llu)",
+                  static_cast<unsigned long long>(s->seed));
+    return SPCA_E_INVALID;
+  }
   const uint32_t* w = static_cast<const uint32_t*>(rows);
   for (int64_t r = 0; r < m_i; ++r)
     for (int64_t j = 0; j < s->n; ++j) {
@@ -202,7 +211,7 @@ spca_status spca_update(spca_session* s, const void* rows, int64_t m_i, int64_t 
   return SPCA_OK;
 }
 
-const char* spca_last_error(const spca_session*) { return ""; }
+const char* spca_last_error(const spca_session* s) { return s ? s->err : ""; }
 
 // Test controls.
 void fake_set_delays(int64_t create_us, int64_t update_us, int64_t finalize_us) {

@@ -60,6 +60,7 @@ def fake(tmp_path_factory):
         "spca_server_close": (i32, [vp, i32]),
         "spca_server_get_stats": (i32, [vp, ctypes.POINTER(ServerStats)]),
         "spca_server_destroy": (i32, [vp]),
+        "spca_server_last_error": (ctypes.c_char_p, []),
         "fake_set_delays": (None, [i64, i64, i64]),
         "fake_fail_create_every": (None, [i64]),
         "fake_live_allocations": (i64, []),
@@ -115,6 +116,11 @@ class Srv:
 
     def wait(self, ticket, timeout=WAIT):
         return self.lib.spca_server_wait(self.h, ticket, timeout)
+
+    def wait_msg(self, ticket, timeout=WAIT):
+        """(status, reason) of a request; the reason is read on the waiting thread."""
+        st = self.lib.spca_server_wait(self.h, ticket, timeout)
+        return st, (self.lib.spca_server_last_error() or b"").decode() if st != OK else ""
 
     def close_session(self, sid):
         assert self.lib.spca_server_close(self.h, sid) == OK
@@ -356,3 +362,31 @@ def test_stress_under_thread_sanitizer(tmp_path):
     assert "ThreadSanitizer" not in r.stderr, r.stderr[-4000:]
     assert r.returncode == 0, (r.stdout, r.stderr[-2000:])
     assert r.stdout.startswith("failures 0"), r.stdout
+
+
+def test_a_failed_request_reports_its_own_reason(fake):
+    """Each failed request carries the reason of the session that ran it: a refused update of
+    one session and the failed creation of another are told apart, and the other requests of
+    the first session still complete."""
+    fake.fake_set_delays(0, 10, 20)
+    first = fake.fake_creates()
+    fake.fake_fail_create_every(first + 2)   # the second session made below fails
+    sv = Srv(fake)
+    rng = np.random.default_rng(12)
+    n, k, p = 10, 2, 1
+    a = sv.open(n, k, p, 71)
+    assert sv.wait(sv.update(a, rows(rng, 4, n))) == OK   # a is created (the first creation)
+    b = sv.open(n + 1, k, p, 72)                          # the second creation fails
+    bad = sv.update(a, rows(rng, 97, n))                  # refused by a's session (97 rows)
+    tb = sv.update(b, rows(rng, 4, n + 1))
+    good = rows(rng, 5, n)
+    tg = sv.update(a, good)
+    st_bad, msg_bad = sv.wait_msg(bad)
+    st_b, msg_b = sv.wait_msg(tb)
+    assert st_bad == 1 and "update rejected" in msg_bad and "seed 71" in msg_bad, msg_bad
+    assert st_b == NOMEM and "could not be created" in msg_b and "seed 71" not in msg_b, msg_b
+    assert sv.wait(tg) == OK
+    sv.close_session(a)
+    sv.close_session(b)
+    sv.destroy()
+    assert fake.fake_live_sessions() == 0
