@@ -104,7 +104,10 @@ spca_status spca_server_update(spca_server* sv, int32_t id, const float* rows, i
  */
 spca_status spca_server_finalize(spca_server* sv, int32_t id, double* sigma, double* V, uint64_t* ticket);
 
-/* Wait until request `ticket` completes (timeout_s < 0: no limit) and return its status
+/* The status of every request that returned a ticket is kept until spca_server_wait has read
+ * it: a caller that does not wait on its tickets should expect that record to grow.
+ *
+ * Wait until request `ticket` completes (timeout_s < 0: no limit) and return its status
  * (SPCA_E_TIMEOUT if the wait timed out; the request itself goes on). For a failed request,
  * spca_server_last_error on the same thread then gives its own reason (with the message of
  * the session that ran it). */
